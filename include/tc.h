@@ -1,0 +1,220 @@
+/*
+ * tc.h -- C ABI of the GB300 exact triangle counter (libtc.so).
+ *
+ * The library computes the exact number of triangles of an undirected simple
+ * graph with the cover-edge method of D. A. Bader, "Fast Triangle Counting"
+ * (arXiv 2309.09064), Algorithm 4 with the degree ordering of its Sec. II
+ * ("BaderD"):
+ *   1. BFS levels L over every component (Algorithm 4, BFS loop; each
+ *      component's root is its first vertex in the working order);
+ *   2. partition of E into horizontal edges E0 (L(u) == L(v)) and
+ *      level-spanning edges E1 (Algorithm 4, partition loop);
+ *   3. triangles inside G0 by the forward method on G0 oriented by the
+ *      working order (Algorithm 2, called from Algorithm 4);
+ *   4. triangles with one horizontal edge by intersecting the G1 lists of the
+ *      two endpoints of every horizontal edge (Algorithm 4, hashed loop);
+ *   5. T = (3) + (4), an exact 64-bit integer.
+ * Every step runs in hand-written CUDA kernels for sm_103a.
+ *
+ * Conventions
+ *   - Vertex ids are uint32_t in [0, n), n < 2^32 - 1.  Row offsets are
+ *     uint64_t.  A CSR is (row_ptr[n+1], col[row_ptr[n]]): symmetric, no
+ *     self-loops, no repeated entries, each row ascending.
+ *   - Pointers marked "host" are ordinary (ideally pinned) host memory;
+ *     "device" pointers are CUDA global memory of the context's device.
+ *   - Inputs are never written (the paper's read-only input convention,
+ *     Sec. III).  The library allocates its scratch memory itself (a
+ *     context-owned arena reused across calls and released by tc_destroy)
+ *     and never leaks it.
+ *   - Every function returns a tc_status.  The library never aborts, prints
+ *     or traps; on failure tc_last_error(ctx) gives a one-line message.
+ *   - A context is not thread-safe: one host thread at a time per context,
+ *     except tc_submit / tc_poll which are safe from any thread.
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum tc_status {
+    TC_OK = 0,
+    TC_ERR_INVALID = 1,   /* bad argument or malformed graph */
+    TC_ERR_OOM = 2,       /* device or host allocation failed */
+    TC_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+    TC_ERR_TIMEOUT = 4,   /* a bounded device wait gave up */
+    TC_ERR_BUSY = 5,      /* request queue full */
+    TC_NOT_READY = 6      /* tc_poll: result not ready yet */
+} tc_status;
+
+typedef struct tc_ctx tc_ctx;
+typedef struct tc_graph tc_graph;
+
+/* where a pointer lives */
+enum { TC_HOST = 0, TC_DEVICE = 1 };
+
+/* tc_graph_from_csr flags */
+enum {
+    TC_COPY = 0,       /* copy the arrays into library-owned device memory */
+    TC_BORROW = 1,     /* keep the caller's DEVICE pointers (must outlive the graph) */
+    TC_VALIDATE = 2    /* check symmetry, order, loops, repeats and bounds first */
+};
+
+/* vertex working order (Sec. II): which vertex is "smaller" in u < v */
+enum {
+    TC_ORDER_DEGREE = 0,  /* BaderD: decreasing degree, ties by ascending id (default) */
+    TC_ORDER_ID = 1       /* Bader: ascending vertex id */
+};
+
+typedef struct tc_options {
+    uint32_t order;        /* TC_ORDER_DEGREE or TC_ORDER_ID */
+    uint32_t flags;        /* reserved, 0 */
+    void *stream;          /* cudaStream_t to run on; NULL: the context creates its own */
+    uint32_t max_queue;    /* tc_submit queue capacity (0: 65536) */
+    uint32_t reserved[7];
+} tc_options;
+
+/* Per-call statistics (tc_count).  Counts are exact. */
+typedef struct tc_stats {
+    uint64_t n;                 /* vertices */
+    uint64_t m;                 /* undirected edges (row_ptr[n] / 2) */
+    uint64_t triangles;         /* T */
+    uint64_t t_same;            /* triangles wholly inside G0 (step 3) */
+    uint64_t t_cross;           /* triangles with one horizontal edge (step 4) */
+    uint64_t horizontal_edges;  /* |E0| */
+    uint64_t levels;            /* number of BFS levels (max L + 1) */
+    uint64_t components;        /* BFS roots (components, isolated vertices included) */
+    uint64_t probes;            /* elements probed in steps 3-4 */
+    uint64_t row2_slots;        /* total length of the compacted [G0 out | G1] rows */
+    uint64_t alg_bytes;         /* algorithmic bytes of the whole count (traffic model) */
+    uint64_t isect_bytes;       /* algorithmic bytes of the intersection stage alone */
+    float ms_total;             /* device time of the whole count */
+    float ms_levels;            /* degrees + BFS levels */
+    float ms_mark;              /* partition, orientation, compaction, planning */
+    float ms_isect;             /* intersections + reduction */
+    /* intersection classes: [0] warp, [1] block (shared table), [2] hub (global table) */
+    uint64_t class_rows[3];     /* hashed rows u (warp) or tasks (block, hub) */
+    uint64_t class_probes[3];   /* probed elements */
+    uint64_t class_bytes[3];    /* algorithmic bytes: hashed rows once + probed rows */
+    float ms_class[3];          /* device time of each class's kernel (0 if not launched) */
+    uint32_t launches;          /* kernels this call launched */
+    uint32_t reserved;
+} tc_stats;
+
+/*
+ * Launch-shape knobs of the intersection stage (Algorithm 4's hashed loop):
+ * rows are classed by the size s(u) of the hashed row of the first endpoint.
+ */
+typedef struct tc_tuning {
+    uint32_t warp_cap;         /* s(u) <= warp_cap: one warp per row, per-warp shared table (1..4096) */
+    uint32_t block_cap;        /* s(u) <= block_cap: one block per task, shared table (warp_cap..16384);
+                                  larger rows use block-private tables in global memory */
+    uint32_t task_work;        /* target probes per block task (large rows are split) */
+    uint32_t warps_per_block;  /* warp-class kernel block size in warps (1..32) */
+    uint32_t block_threads;    /* block-class kernel threads (64..1024, multiple of 32) */
+    uint32_t reserved[3];
+} tc_tuning;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`.  opt may be NULL (defaults). */
+tc_status tc_create(tc_ctx **out, int device, const tc_options *opt);
+/* Destroy a context: waits for its work, frees its arena and request slots. */
+tc_status tc_destroy(tc_ctx *ctx);
+/* One-line description of the last error on this context ("" if none). */
+const char *tc_last_error(const tc_ctx *ctx);
+/* Run subsequent work on `stream` (a cudaStream_t; NULL: the context's own). */
+tc_status tc_set_stream(tc_ctx *ctx, void *stream);
+/* Read / replace the context's tuning (TC_ERR_INVALID if out of range). */
+tc_status tc_get_tuning(const tc_ctx *ctx, tc_tuning *out);
+tc_status tc_set_tuning(tc_ctx *ctx, const tc_tuning *t);
+/* Bytes of device memory currently held by the context's arena. */
+tc_status tc_arena_bytes(const tc_ctx *ctx, uint64_t *bytes);
+
+/* ------------------------------------------------------------------- graphs */
+
+/*
+ * Build the CSR of the simple undirected graph spanned by n_tuples tuples
+ * (src[i], dst[i]): both directions are added, self-loops dropped, repeats
+ * removed and rows sorted (device radix sort).  src/dst are host or device
+ * arrays (`where`).  Ids >= n give TC_ERR_INVALID.  The graph owns its
+ * device arrays.
+ */
+tc_status tc_build_csr(tc_ctx *ctx, uint32_t n, uint64_t n_tuples, const uint32_t *src,
+                       const uint32_t *dst, int where, tc_graph **out);
+
+/*
+ * Wrap an existing CSR (row_ptr[n+1], col[row_ptr[n]]), host or device
+ * (`where`).  TC_COPY copies into library memory (host input is always
+ * copied); TC_BORROW keeps device pointers (caller keeps them alive and
+ * unchanged).  TC_VALIDATE runs the well-formedness check and returns
+ * TC_ERR_INVALID on the first violation.
+ */
+tc_status tc_graph_from_csr(tc_ctx *ctx, uint32_t n, const uint64_t *row_ptr, const uint32_t *col,
+                            int where, int flags, tc_graph **out);
+
+/* Device pointers and sizes of a graph (valid until tc_graph_free). */
+tc_status tc_graph_info(const tc_graph *g, uint32_t *n, uint64_t *slots, const uint64_t **d_row_ptr,
+                        const uint32_t **d_col);
+
+/*
+ * Copy a graph's CSR out: row_ptr gets n+1 offsets, col gets row_ptr[n] ids,
+ * into host or device buffers (`where`) the caller owns.
+ */
+tc_status tc_graph_copy_out(tc_ctx *ctx, const tc_graph *g, uint64_t *row_ptr, uint32_t *col, int where);
+
+/* Check a graph's CSR (symmetric, ascending rows, no loops, no repeats); *ok = 1 if well formed. */
+tc_status tc_validate(tc_ctx *ctx, const tc_graph *g, int *ok);
+
+/* Release a graph (and its device arrays unless borrowed). */
+tc_status tc_graph_free(tc_graph *g);
+
+/* ----------------------------------------------------------------- counting */
+
+/*
+ * Exact triangle count of g (Algorithm 4, steps 1-5 above).  *triangles gets
+ * T; stats (nullable) gets the breakdown.  Blocks until the result is on the
+ * host.
+ */
+tc_status tc_count(tc_ctx *ctx, const tc_graph *g, uint64_t *triangles, tc_stats *stats);
+
+/*
+ * Same as tc_count, and additionally writes the BFS level of every vertex to
+ * d_levels (device uint32_t[n], nullable) -- the L of Algorithm 4 under the
+ * context's working order.
+ */
+tc_status tc_count_levels(tc_ctx *ctx, const tc_graph *g, uint32_t *d_levels, uint64_t *triangles,
+                          tc_stats *stats);
+
+/*
+ * Count G independent graphs in one batched launch sequence; counts is a host
+ * uint64_t[G].  Every count equals tc_count on the same graph.
+ */
+tc_status tc_count_batch(tc_ctx *ctx, uint32_t G, const tc_graph *const *graphs, uint64_t *counts);
+
+/* ------------------------------------------------------------------ serving */
+
+/*
+ * Queue a count of g (which must stay alive until its ticket completes) and
+ * return at once with a ticket.  A server thread owned by the context admits
+ * queued requests while device memory allows, batches them, and overlaps
+ * their work on the device.  TC_ERR_BUSY if the queue is full.
+ */
+tc_status tc_submit(tc_ctx *ctx, const tc_graph *g, uint64_t *ticket);
+
+/*
+ * Non-blocking: TC_OK with *triangles set when the ticket is done (the ticket
+ * is then released), TC_NOT_READY while it is queued or running, another
+ * status if it failed or the ticket is unknown.
+ */
+tc_status tc_poll(tc_ctx *ctx, uint64_t ticket, uint64_t *triangles);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TC_H */

@@ -1,0 +1,404 @@
+// levels.cu -- degrees, canonical BFS roots and BFS levels (Algorithm 4, BFS loop).
+//
+// The paper's loop "for all v: if v unvisited, BFS(G, v)" takes vertices in the
+// working order, so every component's root is its first vertex in that order
+// (degree order: highest degree, then lowest id).  On the GPU:
+//   1. k_init computes degrees, gives isolated vertices level 0 (each is its
+//      own root) and finds the globally first non-isolated vertex;
+//   2. a direction-optimising frontier BFS (top-down with edge-balanced
+//      expansion, bottom-up when the frontier is large) levels its component;
+//   3. the vertices still unvisited form the other components: min-key
+//      hooking with pointer jumping finds each one's first vertex, and a
+//      multi-source BFS from those roots levels them.
+// BFS distances are unique given the roots, so L matches the serial
+// algorithm exactly whatever the thread schedule.
+#include "pipeline.cuh"
+
+namespace tc {
+namespace {
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long y = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        v = y < v ? y : v;
+    }
+    return v;
+}
+
+__global__ void k_init(uint32_t n, const uint64_t *__restrict__ rp, uint32_t *__restrict__ deg,
+                       uint32_t *__restrict__ L, Ctl *ctl, uint32_t order) {
+    __shared__ unsigned int s_iso;
+    __shared__ unsigned long long s_key;
+    if (threadIdx.x == 0) {
+        s_iso = 0;
+        s_key = ~0ull;
+    }
+    __syncthreads();
+    unsigned long long best = ~0ull;
+    unsigned iso = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        uint32_t d = (uint32_t)(rp[v + 1] - rp[v]);
+        deg[v] = d;
+        if (d == 0) {
+            L[v] = 0;
+            ++iso;
+        } else {
+            L[v] = kUnvisited;
+            unsigned long long k = order_key((uint32_t)v, d, order);
+            best = k < best ? k : best;
+        }
+    }
+    best = warp_min_u64(best);
+    iso = warp_sum(iso);
+    if (lane_id() == 0) {
+        atomicMin(&s_key, best);
+        atomicAdd(&s_iso, iso);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_key != ~0ull) atomicMin(&ctl->root_key, s_key);
+        if (s_iso) {
+            atomicAdd(&ctl->visited, s_iso);
+            atomicAdd(&ctl->components, s_iso);
+        }
+    }
+}
+
+// Seed the BFS with the globally first non-isolated vertex (if any).
+__global__ void k_seed(const uint32_t *__restrict__ deg, uint32_t *__restrict__ L, uint32_t *__restrict__ q,
+                       Ctl *ctl, int cur) {
+    unsigned long long key = ctl->root_key;
+    if (key == ~0ull) return;
+    uint32_t r = (uint32_t)(key & 0xFFFFFFFFull);
+    L[r] = 0;
+    q[0] = r;
+    ctl->fr_count[cur] = 1;
+    ctl->fr_edges[cur] = deg[r];
+    ctl->visited += 1;
+    ctl->visited_edges += deg[r];
+    ctl->components += 1;
+}
+
+__global__ void k_gather_deg(const uint32_t *__restrict__ q, uint32_t count, const uint32_t *__restrict__ deg,
+                             uint32_t *__restrict__ out) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) out[i] = deg[q[i]];
+}
+
+constexpr int kTdThreads = 256;
+constexpr int kTdItems = 8;
+constexpr uint64_t kTdTile = (uint64_t)kTdThreads * kTdItems;
+
+// Top-down step with edge-balanced expansion: the frontier's adjacency lists
+// are viewed as one concatenated list (fpref = exclusive prefix of frontier
+// degrees); each block takes tiles of kTdTile consecutive entries.
+__global__ void __launch_bounds__(kTdThreads) k_td(const uint32_t *__restrict__ q, uint32_t fcount,
+                                                   const unsigned long long *__restrict__ fpref,
+                                                   const uint64_t *__restrict__ rp, const uint32_t *__restrict__ col,
+                                                   const uint32_t *__restrict__ deg, uint32_t *__restrict__ L,
+                                                   uint32_t *__restrict__ qn, Ctl *ctl, uint32_t level, int nxt) {
+    __shared__ uint32_t s_lo, s_hi;
+    __shared__ unsigned long long s_edges;
+    const unsigned long long total = fpref[fcount];
+    unsigned long long edges = 0;
+    for (unsigned long long t0 = (unsigned long long)blockIdx.x * kTdTile; t0 < total;
+         t0 += (unsigned long long)gridDim.x * kTdTile) {
+        const unsigned long long t1 = t0 + kTdTile < total ? t0 + kTdTile : total;
+        if (threadIdx.x == 0) {
+            // frontier slots holding entries t0 and t1-1: largest i with fpref[i] <= x
+            uint32_t a = 0, b = fcount;
+            while (b - a > 1) {
+                uint32_t m = (a + b) >> 1;
+                if (fpref[m] <= t0) a = m; else b = m;
+            }
+            s_lo = a;
+            b = fcount;
+            while (b - a > 1) {
+                uint32_t m = (a + b) >> 1;
+                if (fpref[m] <= t1 - 1) a = m; else b = m;
+            }
+            s_hi = a;
+        }
+        __syncthreads();
+        const uint32_t lo = s_lo, hi = s_hi;
+        __syncthreads();
+#pragma unroll 1
+        for (int it = 0; it < kTdItems; ++it) {
+            const unsigned long long e = t0 + (unsigned long long)it * kTdThreads + threadIdx.x;
+            bool claim = false;
+            uint32_t w = 0;
+            if (e < t1) {
+                uint32_t a = lo, b = hi + 1;
+                while (b - a > 1) {
+                    uint32_t m = (a + b) >> 1;
+                    if (fpref[m] <= e) a = m; else b = m;
+                }
+                const uint32_t v = q[a];
+                w = col[rp[v] + (e - fpref[a])];
+                if (L[w] == kUnvisited && atomicCAS(&L[w], kUnvisited, level + 1) == kUnvisited) claim = true;
+            }
+            uint32_t slot = warp_append(claim, &ctl->fr_count[nxt]);
+            if (claim) {
+                qn[slot] = w;
+                edges += deg[w];
+            }
+        }
+    }
+    edges = warp_sum(edges);
+    if (threadIdx.x == 0) s_edges = 0;
+    __syncthreads();
+    if (lane_id() == 0 && edges) atomicAdd(&s_edges, edges);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_edges) atomicAdd(&ctl->fr_edges[nxt], s_edges);
+}
+
+// Bottom-up step: every unvisited vertex looks for a neighbour on `level`.
+__global__ void k_bu(uint32_t n, const uint64_t *__restrict__ rp, const uint32_t *__restrict__ col,
+                     const uint32_t *__restrict__ deg, uint32_t *__restrict__ L, uint32_t *__restrict__ qn, Ctl *ctl,
+                     uint32_t level, int nxt) {
+    __shared__ unsigned long long s_edges;
+    if (threadIdx.x == 0) s_edges = 0;
+    __syncthreads();
+    unsigned long long edges = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t n_round = ((uint64_t)n + 31) & ~uint64_t(31);
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_round; v += stride) {
+        bool found = false;
+        if (v < n && L[v] == kUnvisited) {
+            const uint64_t b = rp[v], e = rp[v + 1];
+            for (uint64_t j = b; j < e; ++j) {
+                if (L[col[j]] == level) {
+                    found = true;
+                    break;
+                }
+            }
+            if (found) L[v] = level + 1;
+        }
+        uint32_t slot = warp_append(found, &ctl->fr_count[nxt]);
+        if (found) {
+            qn[slot] = (uint32_t)v;
+            edges += deg[v];
+        }
+    }
+    edges = warp_sum(edges);
+    if (lane_id() == 0 && edges) atomicAdd(&s_edges, edges);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_edges) atomicAdd(&ctl->fr_edges[nxt], s_edges);
+}
+
+__global__ void k_collect_unvisited(uint32_t n, const uint32_t *__restrict__ L, uint32_t *__restrict__ R, Ctl *ctl) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t n_round = ((uint64_t)n + 31) & ~uint64_t(31);
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n_round; v += stride) {
+        bool un = v < n && L[v] == kUnvisited;
+        uint32_t slot = warp_append(un, &ctl->n_residual);
+        if (un) R[slot] = (uint32_t)v;
+    }
+}
+
+__global__ void k_cc_init(const uint32_t *__restrict__ R, uint32_t nr, uint32_t *__restrict__ parent) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += stride) parent[R[i]] = R[i];
+}
+
+// Follow parent pointers to the root.  Pointers always lead to a vertex with a
+// smaller key, so the walk ends; the bound only guards against a corrupted
+// array and raises the error flag.
+__device__ __forceinline__ uint32_t find_root(const uint32_t *parent, uint32_t x, uint32_t n, Ctl *ctl) {
+    for (uint32_t it = 0; it <= n; ++it) {
+        uint32_t p = parent[x];
+        if (p == x) return x;
+        x = p;
+    }
+    ctl->error = 2;
+    return x;
+}
+
+// Hooking: for every edge joining two trees, attach the root with the larger
+// working-order key under the root with the smaller one.
+__global__ void k_cc_hook(const uint32_t *__restrict__ R, uint32_t nr, uint32_t n, const uint64_t *__restrict__ rp,
+                          const uint32_t *__restrict__ col, const uint32_t *__restrict__ deg, uint32_t *parent,
+                          Ctl *ctl, uint32_t order) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    bool changed = false;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += stride) {
+        const uint32_t v = R[i];
+        for (uint64_t j = rp[v]; j < rp[v + 1]; ++j) {
+            const uint32_t w = col[j];
+            if (w < v) continue;  // each undirected edge once
+            uint32_t rv = find_root(parent, v, n, ctl), rw = find_root(parent, w, n, ctl);
+            if (rv == rw) continue;
+            unsigned long long kv = order_key(rv, deg[rv], order), kw = order_key(rw, deg[rw], order);
+            uint32_t hi = kv < kw ? rw : rv, lo = kv < kw ? rv : rw;
+            atomicCAS(&parent[hi], hi, lo);
+            changed = true;
+        }
+    }
+    if (__any_sync(0xFFFFFFFFu, changed) && lane_id() == 0) ctl->changed = 1;
+}
+
+__global__ void k_cc_compress(const uint32_t *__restrict__ R, uint32_t nr, uint32_t n, uint32_t *parent, Ctl *ctl) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += stride) {
+        const uint32_t v = R[i];
+        parent[v] = find_root(parent, v, n, ctl);
+    }
+}
+
+__global__ void k_cc_roots(const uint32_t *__restrict__ R, uint32_t nr, const uint32_t *__restrict__ parent,
+                           const uint32_t *__restrict__ deg, uint32_t *__restrict__ L, uint32_t *__restrict__ q,
+                           Ctl *ctl, int cur) {
+    __shared__ unsigned long long s_edges;
+    if (threadIdx.x == 0) s_edges = 0;
+    __syncthreads();
+    unsigned long long edges = 0;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const uint32_t nr_round = (nr + 31) & ~31u;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nr_round; i += stride) {
+        bool root = false;
+        uint32_t v = 0;
+        if (i < nr) {
+            v = R[i];
+            root = parent[v] == v;
+        }
+        uint32_t slot = warp_append(root, &ctl->fr_count[cur]);
+        if (root) {
+            L[v] = 0;
+            q[slot] = v;
+            edges += deg[v];
+        }
+    }
+    edges = warp_sum(edges);
+    if (lane_id() == 0 && edges) atomicAdd(&s_edges, edges);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_edges) atomicAdd(&ctl->fr_edges[cur], s_edges);
+}
+
+__global__ void k_count_roots(Ctl *ctl, int cur) {
+    ctl->components += ctl->fr_count[cur];
+    ctl->visited += ctl->fr_count[cur];
+    ctl->visited_edges += ctl->fr_edges[cur];
+}
+
+__global__ void k_reset_next(Ctl *ctl, int nxt) {
+    ctl->fr_count[nxt] = 0;
+    ctl->fr_edges[nxt] = 0;
+}
+
+__global__ void k_after_level(Ctl *ctl, int nxt, uint32_t level) {
+    ctl->visited += ctl->fr_count[nxt];
+    ctl->visited_edges += ctl->fr_edges[nxt];
+    if (ctl->fr_count[nxt]) ctl->max_level = level + 1 > ctl->max_level ? level + 1 : ctl->max_level;
+}
+
+unsigned grid_for(uint64_t work, unsigned threads, unsigned cap) {
+    uint64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+// Pull the control block to the host (synchronises the stream).
+static tc_status pull_ctl(tc_ctx *ctx) {
+    TC_CUDA(ctx, cudaMemcpyAsync(ctx->h_ctl, ctx->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
+    TC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return TC_OK;
+}
+
+// Level-synchronous BFS from the frontier in q[cur] (already levelled 0 ..
+// start_level).  Chooses top-down or bottom-up per level (Beamer et al.'s
+// edge/vertex heuristics).
+static tc_status bfs_loop(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t slots, uint32_t start_level,
+                          int *cur_io) {
+    cudaStream_t s = ctx->stream;
+    const unsigned cap = (unsigned)ctx->num_sms * 16u;
+    int cur = *cur_io;
+    uint32_t level = start_level;
+    bool bottom_up = false;
+    tc_status st = pull_ctl(ctx);
+    if (st != TC_OK) return st;
+    uint32_t fcount = ctx->h_ctl->fr_count[cur];
+    unsigned long long fedges = ctx->h_ctl->fr_edges[cur];
+    uint32_t prev_count = 0;
+    while (fcount > 0) {
+        const unsigned long long unexplored = slots - ctx->h_ctl->visited_edges;
+        if (!bottom_up && fedges > unexplored / 14 && fcount > 64) bottom_up = true;
+        else if (bottom_up && fcount < n / 24 && fcount < prev_count) bottom_up = false;
+        const int nxt = cur ^ 1;
+        uint32_t *q = cur ? b.q1 : b.q0;
+        uint32_t *qn = cur ? b.q0 : b.q1;
+        k_reset_next<<<1, 1, 0, s>>>(ctx->d_ctl, nxt);
+        note_launch(ctx, 2);  // reset + after-level bookkeeping
+        if (bottom_up) {
+            k_bu<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.rp, b.col, b.deg, b.L, qn, ctx->d_ctl, level, nxt);
+            note_launch(ctx);
+        } else if (fedges > 0) {
+            k_gather_deg<<<grid_for(fcount, 256, cap), 256, 0, s>>>(q, fcount, b.deg, b.fdeg);
+            note_launch(ctx, 2 + scan_u32_to_u64(b.fdeg, b.fpref, fcount, b.scan_tmp, s));
+            k_td<<<grid_for((fedges + kTdTile - 1) / kTdTile, 1, cap), kTdThreads, 0, s>>>(
+                q, fcount, reinterpret_cast<const unsigned long long *>(b.fpref), b.rp, b.col, b.deg, b.L, qn,
+                ctx->d_ctl, level, nxt);
+        }
+        k_after_level<<<1, 1, 0, s>>>(ctx->d_ctl, nxt, level);
+        TC_CUDA(ctx, cudaGetLastError());
+        st = pull_ctl(ctx);
+        if (st != TC_OK) return st;
+        prev_count = fcount;
+        fcount = ctx->h_ctl->fr_count[nxt];
+        fedges = ctx->h_ctl->fr_edges[nxt];
+        cur = nxt;
+        ++level;
+    }
+    *cur_io = cur;
+    return TC_OK;
+}
+
+tc_status compute_levels(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t slots) {
+    cudaStream_t s = ctx->stream;
+    const unsigned cap = (unsigned)ctx->num_sms * 16u;
+    if (n == 0) return TC_OK;
+    k_init<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.rp, b.deg, b.L, ctx->d_ctl, ctx->opt.order);
+    int cur = 0;
+    k_seed<<<1, 1, 0, s>>>(b.deg, b.L, b.q0, ctx->d_ctl, cur);
+    note_launch(ctx, 2);
+    TC_CUDA(ctx, cudaGetLastError());
+    tc_status st = bfs_loop(ctx, b, n, slots, 0, &cur);
+    if (st != TC_OK) return st;
+    if (ctx->h_ctl->visited >= n) return TC_OK;
+
+    // Remaining components: min-key roots by hooking, then a multi-source BFS.
+    k_collect_unvisited<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.L, b.R, ctx->d_ctl);
+    note_launch(ctx);
+    st = pull_ctl(ctx);
+    if (st != TC_OK) return st;
+    const uint32_t nr = ctx->h_ctl->n_residual;
+    if (nr == 0) return TC_OK;
+    k_cc_init<<<grid_for(nr, 256, cap), 256, 0, s>>>(b.R, nr, b.parent);
+    note_launch(ctx);
+    for (int round = 0;; ++round) {
+        TC_CUDA(ctx, cudaMemsetAsync(&ctx->d_ctl->changed, 0, sizeof(unsigned), s));
+        k_cc_hook<<<grid_for(nr, 256, cap), 256, 0, s>>>(b.R, nr, n, b.rp, b.col, b.deg, b.parent, ctx->d_ctl,
+                                                         ctx->opt.order);
+        k_cc_compress<<<grid_for(nr, 256, cap), 256, 0, s>>>(b.R, nr, n, b.parent, ctx->d_ctl);
+        note_launch(ctx, 2);
+        TC_CUDA(ctx, cudaGetLastError());
+        st = pull_ctl(ctx);
+        if (st != TC_OK) return st;
+        if (ctx->h_ctl->error) return set_error(ctx, TC_ERR_INVALID, "connected-components walk did not end");
+        if (!ctx->h_ctl->changed) break;
+        if (round > 64) return set_error(ctx, TC_ERR_TIMEOUT, "connected components did not converge");
+    }
+    cur = 0;
+    k_reset_next<<<1, 1, 0, s>>>(ctx->d_ctl, cur);
+    k_cc_roots<<<grid_for(nr, 256, cap), 256, 0, s>>>(b.R, nr, b.parent, b.deg, b.L, b.q0, ctx->d_ctl, cur);
+    k_count_roots<<<1, 1, 0, s>>>(ctx->d_ctl, cur);
+    note_launch(ctx, 3);
+    TC_CUDA(ctx, cudaGetLastError());
+    return bfs_loop(ctx, b, n, slots, 0, &cur);
+}
+
+}  // namespace tc

@@ -1,0 +1,179 @@
+// rows.cu -- partition of E into E0 / E1, orientation of E0 by the working
+// order, and compaction into one row per vertex (Algorithm 4, partition loop).
+//
+// For every vertex x the compacted row is  [ H(x) | G1(x) ]  with
+//   H(x)  = { y in N(x) : L(y) == L(x), x precedes y }   (G0, oriented)
+//   G1(x) = { y in N(x) : L(y) != L(x) }                 (level-spanning)
+// each part ascending (the CSR row order is kept).  Because L(u) == L(v) on a
+// horizontal edge u -> v, a common element w of row(u) and row(v) lies in
+// H(u) and H(v) when L(w) == L(u) (a triangle inside G0, counted once at its
+// first edge: Algorithm 2 on G0) and in G1(u) and G1(v) otherwise (a triangle
+// with exactly one horizontal edge: the hashed G1 loop of Algorithm 4).  So
+// one intersection per horizontal edge counts both kinds, and the position of
+// w in row(v) (below or above |H(v)|) tells which kind it is.
+#include "pipeline.cuh"
+
+namespace tc {
+namespace {
+
+__global__ void k_row_count(uint32_t n, const uint64_t *__restrict__ rp, const uint32_t *__restrict__ col,
+                            const uint32_t *__restrict__ deg, const uint32_t *__restrict__ L,
+                            uint32_t *__restrict__ hcnt, uint32_t *__restrict__ scnt, Ctl *ctl, uint32_t order) {
+    __shared__ unsigned long long s_e0;
+    if (threadIdx.x == 0) s_e0 = 0;
+    __syncthreads();
+    const unsigned lane = lane_id();
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long e0 = 0;
+    for (uint64_t x = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
+        const uint32_t dx = deg[x];
+        if (dx == 0) {
+            if (lane == 0) hcnt[x] = scnt[x] = 0;
+            continue;
+        }
+        const uint32_t lx = L[x];
+        const uint64_t b = rp[x];
+        uint32_t h = 0, g = 0;
+        for (uint32_t j = lane; j < dx; j += 32) {
+            const uint32_t y = col[b + j];
+            const uint32_t ly = L[y];
+            if (ly == lx) {
+                if (precedes((uint32_t)x, dx, y, deg[y], order)) ++h;
+            } else {
+                ++g;
+            }
+        }
+        h = warp_sum(h);
+        g = warp_sum(g);
+        if (lane == 0) {
+            hcnt[x] = h;
+            scnt[x] = h + g;
+            e0 += h;
+        }
+    }
+    if (lane == 0 && e0) atomicAdd(&s_e0, e0);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_e0) atomicAdd(&ctl->e0, s_e0);
+}
+
+__global__ void k_row_fill(uint32_t n, const uint64_t *__restrict__ rp, const uint32_t *__restrict__ col,
+                           const uint32_t *__restrict__ deg, const uint32_t *__restrict__ L,
+                           const uint32_t *__restrict__ hcnt, const uint64_t *__restrict__ off2,
+                           uint32_t *__restrict__ adj2, uint32_t order) {
+    const unsigned lane = lane_id();
+    const unsigned lt = (1u << lane) - 1u;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t x = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
+        const uint32_t dx = deg[x];
+        if (dx == 0) continue;
+        const uint32_t lx = L[x];
+        const uint64_t b = rp[x];
+        const uint64_t base = off2[x];
+        const uint32_t hx = hcnt[x];
+        uint32_t hp = 0, gp = 0;
+        for (uint32_t j0 = 0; j0 < dx; j0 += 32) {
+            const uint32_t j = j0 + lane;
+            bool isH = false, isG = false;
+            uint32_t y = 0;
+            if (j < dx) {
+                y = col[b + j];
+                const uint32_t ly = L[y];
+                if (ly == lx) isH = precedes((uint32_t)x, dx, y, deg[y], order);
+                else isG = true;
+            }
+            const unsigned mh = __ballot_sync(0xFFFFFFFFu, isH);
+            const unsigned mg = __ballot_sync(0xFFFFFFFFu, isG);
+            if (isH) adj2[base + hp + __popc(mh & lt)] = y;
+            if (isG) adj2[base + hx + gp + __popc(mg & lt)] = y;
+            hp += __popc(mh);
+            gp += __popc(mg);
+        }
+    }
+}
+
+// Rows with at least one oriented horizontal edge are the hashed side of the
+// intersections; split them by the size of their compacted row.
+__global__ void k_classify(uint32_t n, const uint32_t *__restrict__ hcnt, const uint32_t *__restrict__ scnt,
+                           uint32_t *__restrict__ wlist, uint32_t *__restrict__ blist, Ctl *ctl, uint32_t warp_cap) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t n_round = ((uint64_t)n + 31) & ~uint64_t(31);
+    unsigned my_max = 0;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_round; x += stride) {
+        bool active = x < n && hcnt[x] > 0;
+        uint32_t s = active ? scnt[x] : 0;
+        bool w = active && s <= warp_cap;
+        bool bl = active && s > warp_cap;
+        uint32_t sw = warp_append(w, &ctl->n_warp_u);
+        uint32_t sb = warp_append(bl, &ctl->n_block_u);
+        if (w) wlist[sw] = (uint32_t)x;
+        if (bl) {
+            blist[sb] = (uint32_t)x;
+            my_max = s > my_max ? s : my_max;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned y = __shfl_xor_sync(0xFFFFFFFFu, my_max, o);
+        my_max = y > my_max ? y : my_max;
+    }
+    if (lane_id() == 0 && my_max) atomicMax(&ctl->max_s2, my_max);
+}
+
+// Split each block-class row u into tasks of about `target` probes:
+// ntask = clamp(ceil(work(u) / max(task_work, 2 s(u))), 1, |H(u)|) where
+// work(u) = sum of s(v) over v in H(u).  A task takes a contiguous slice of H(u).
+__global__ void k_plan(const uint32_t *__restrict__ blist, const Ctl *__restrict__ ctl,
+                       const uint64_t *__restrict__ off2, const uint32_t *__restrict__ adj2,
+                       const uint32_t *__restrict__ hcnt, const uint32_t *__restrict__ scnt,
+                       uint32_t *__restrict__ ntask, uint32_t task_work) {
+    const unsigned lane = lane_id();
+    const uint32_t nb = ctl->n_block_u;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nb; i += warps) {
+        const uint32_t u = blist[i];
+        const uint64_t b = off2[u];
+        const uint32_t hu = hcnt[u];
+        unsigned long long work = 0;
+        for (uint32_t k = lane; k < hu; k += 32) work += scnt[adj2[b + k]];
+        work = warp_sum(work);
+        if (lane == 0) {
+            const unsigned long long su = scnt[u];
+            const unsigned long long target = 2 * su > task_work ? 2 * su : task_work;
+            unsigned long long nt = (work + target - 1) / target;
+            if (nt < 1) nt = 1;
+            if (nt > hu) nt = hu;
+            ntask[i] = (uint32_t)nt;
+        }
+    }
+}
+
+unsigned grid_for(uint64_t work, unsigned threads, unsigned cap) {
+    uint64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n) {
+    cudaStream_t s = ctx->stream;
+    const unsigned cap = (unsigned)ctx->num_sms * 16u;
+    const uint32_t order = ctx->opt.order;
+    if (n == 0) return TC_OK;
+    k_row_count<<<grid_for((uint64_t)n * 32, 256, cap), 256, 0, s>>>(n, b.rp, b.col, b.deg, b.L, b.hcnt, b.scnt,
+                                                                     ctx->d_ctl, order);
+    const uint32_t scan_launches = scan_u32_to_u64(b.scnt, b.off2, n, b.scan_tmp, s);
+    k_row_fill<<<grid_for((uint64_t)n * 32, 256, cap), 256, 0, s>>>(n, b.rp, b.col, b.deg, b.L, b.hcnt, b.off2,
+                                                                    b.adj2, order);
+    k_classify<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.hcnt, b.scnt, b.wlist, b.blist, ctx->d_ctl,
+                                                     ctx->tune.warp_cap);
+    // planning covers at most n block-class rows; the kernel reads the true count
+    k_plan<<<grid_for((uint64_t)n * 32, 256, cap), 256, 0, s>>>(b.blist, ctx->d_ctl, b.off2, b.adj2, b.hcnt, b.scnt,
+                                                                b.ntask, ctx->tune.task_work);
+    note_launch(ctx, 4 + scan_launches);
+    TC_CUDA(ctx, cudaGetLastError());
+    return TC_OK;
+}
+
+}  // namespace tc

@@ -1,0 +1,212 @@
+// tc_internal.cuh -- internal types and device helpers of libtc (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "tc.h"
+
+namespace tc {
+
+constexpr uint32_t kUnvisited = 0xFFFFFFFFu;
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+
+// ----------------------------------------------------------------------------- tuning
+// Class boundaries of the intersection stage by the size s(u) of the hashed
+// row [G0 out-list | G1 list] of the higher-ranked endpoint u.
+struct Tuning {
+    uint32_t warp_cap = 1024;        // s(u) <= warp_cap: one warp per u, per-warp smem table
+    uint32_t block_cap = 16384;      // s(u) <= block_cap: one block per task, smem table
+    uint32_t task_work = 65536;      // target probes per block task (heavy rows are split)
+    uint32_t warps_per_block = 8;    // warp-class kernel: warps per block
+    uint32_t block_threads = 512;    // block/hub-class kernel threads
+};
+
+// Control block in device memory: counters the kernels update and the host
+// reads back between launches.
+struct Ctl {
+    unsigned long long root_key;     // smallest working-order key among non-isolated vertices
+    unsigned long long t_same;       // triangles wholly inside G0
+    unsigned long long t_cross;      // triangles with one horizontal edge
+    unsigned long long e0;           // |E0|
+    unsigned long long probes;       // probed elements
+    unsigned long long cls_probes[3];   // per intersection class (warp, block, hub)
+    unsigned long long cls_build[3];    // hashed-row elements per class (each row once)
+    unsigned long long cls_rows[3];     // rows (warp) / tasks (block, hub) per class
+    unsigned long long fr_edges[2];  // sum of degrees of the frontier being built
+    unsigned long long visited_edges;
+    unsigned int fr_count[2];        // frontier sizes
+    unsigned int visited;            // vertices with a level
+    unsigned int max_level;
+    unsigned int components;         // BFS roots
+    unsigned int changed;            // CC hooking made progress
+    unsigned int n_residual;
+    unsigned int n_warp_u;           // warp-class rows
+    unsigned int n_block_u;          // block-class rows (incl. hubs)
+    unsigned int warp_next;          // dynamic scheduling counters
+    unsigned int block_next;
+    unsigned int error;              // nonzero: a device-side check failed
+    unsigned int max_s2;             // largest hashed row among block-class rows
+    unsigned int pad[5];
+};
+
+// ----------------------------------------------------------------------------- arena
+struct Arena {
+    char *base = nullptr;
+    size_t cap = 0;
+    size_t off = 0;
+    void reset() { off = 0; }
+    template <class T>
+    T *take(size_t count) {
+        size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+        if (off + bytes > cap) return nullptr;
+        T *p = reinterpret_cast<T *>(base + off);
+        off += bytes;
+        return p;
+    }
+};
+
+}  // namespace tc
+
+struct tc_graph {
+    tc_ctx *ctx;
+    uint32_t n;
+    uint64_t slots;    // row_ptr[n] = 2m
+    uint64_t *rp;      // device
+    uint32_t *col;     // device
+    uint32_t max_deg;
+    bool owned;
+};
+
+struct ServeState;  // serve.cu
+
+struct tc_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    tc_options opt{};
+    tc::Tuning tune{};
+    tc::Arena arena;
+    tc::Arena batch_arena;   // union CSR of tc_count_batch
+    tc::Ctl *d_ctl = nullptr;
+    tc::Ctl *h_ctl = nullptr;   // pinned
+    cudaEvent_t ev[8] = {};
+    uint32_t launches = 0;    // kernels launched by the current call
+    uint32_t isect_flags = 0; // which intersection kernels the last count launched (1 warp, 2 block, 4 hub)
+    std::string err;
+    ServeState *serve = nullptr;
+};
+
+namespace tc {
+
+// ----------------------------------------------------------------------------- host helpers
+tc_status set_error(tc_ctx *ctx, tc_status st, const std::string &msg);
+tc_status cuda_error(tc_ctx *ctx, cudaError_t e, const char *what);
+tc_status arena_reserve(tc_ctx *ctx, size_t bytes);
+
+// Launch bookkeeping: every kernel launch site calls this once per launch.
+inline void note_launch(tc_ctx *ctx, uint32_t k = 1) { ctx->launches += k; }
+
+#define TC_CUDA(ctx, call)                                   \
+    do {                                                     \
+        cudaError_t _e = (call);                             \
+        if (_e != cudaSuccess) return tc::cuda_error((ctx), _e, #call); \
+    } while (0)
+
+// Exclusive scan of `count` uint32 values into uint64 out[count + 1]
+// (out[count] = total).  tmp needs scan_tmp_elems(count) uint64 entries.
+// Returns the number of kernels launched.
+size_t scan_tmp_elems(uint64_t count);
+uint32_t scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t count, uint64_t *tmp, cudaStream_t s);
+// Same for uint64 inputs.
+uint32_t scan_u64(const uint64_t *in, uint64_t *out, uint64_t count, uint64_t *tmp, cudaStream_t s);
+
+// Pipeline entry (count.cu).  levels_out: device uint32[n] or nullptr.
+// group_of / n_groups / group_counts: optional per-group accumulation
+// (batched counting of a disjoint union): group_vertex_start is a device
+// uint32[n_groups + 1] of first vertex ids, group_counts a device uint64[n_groups].
+struct GroupSpec {
+    const uint32_t *vertex_start = nullptr;
+    uint32_t n_groups = 0;
+    unsigned long long *counts = nullptr;
+};
+struct GraphView {
+    uint32_t n = 0;
+    uint64_t slots = 0;
+    const uint64_t *rp = nullptr;
+    const uint32_t *col = nullptr;
+    uint32_t max_deg = 0;
+};
+tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, const GroupSpec &groups,
+                         uint64_t *triangles, tc_stats *stats);
+size_t pipeline_bytes(const tc_ctx *ctx, uint32_t n, uint64_t slots, uint32_t max_deg, bool own_levels,
+                      uint64_t *hub_slots, uint32_t *hub_blocks);
+
+// CSR construction / validation (csr.cu)
+tc_status build_csr_device(tc_ctx *ctx, uint32_t n, uint64_t t, const uint32_t *d_src,
+                           const uint32_t *d_dst, uint64_t **rp_out, uint32_t **col_out,
+                           uint64_t *slots_out);
+tc_status validate_csr_device(tc_ctx *ctx, uint32_t n, const uint64_t *rp, const uint32_t *col,
+                              uint64_t slots, int *ok);
+tc_status max_degree_device(tc_ctx *ctx, uint32_t n, const uint64_t *rp, uint32_t *max_deg);
+// Batched counting of G graphs as one disjoint union (batch.cu).
+tc_status count_batch(tc_ctx *ctx, uint32_t G, const tc_graph *const *graphs, uint64_t *counts);
+
+// Serving (serve.cu)
+void serve_shutdown(tc_ctx *ctx);
+
+// ----------------------------------------------------------------------------- device helpers
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// Working-order key: smaller key = earlier vertex.  Degree order (BaderD):
+// decreasing degree, ties by ascending id.  Id order (Bader): the id.
+__device__ __forceinline__ unsigned long long order_key(uint32_t v, uint32_t deg, uint32_t order) {
+    return order == TC_ORDER_DEGREE ? ((unsigned long long)(0xFFFFFFFFu - deg) << 32) | v
+                                    : (unsigned long long)v;
+}
+
+// x precedes y in the working order
+__device__ __forceinline__ bool precedes(uint32_t x, uint32_t dx, uint32_t y, uint32_t dy, uint32_t order) {
+    if (order == TC_ORDER_DEGREE) return dx > dy || (dx == dy && x < y);
+    return x < y;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+// Append `pred` items to a global list with one atomic per warp (all lanes of
+// the warp must call it).  Returns this lane's slot (valid where pred).
+__device__ __forceinline__ uint32_t warp_append(bool pred, unsigned int *counter) {
+    unsigned mask = __ballot_sync(0xFFFFFFFFu, pred);
+    uint32_t base = 0;
+    if (mask) {
+        unsigned leader = __ffs(mask) - 1;
+        if (lane_id() == leader) base = atomicAdd(counter, (unsigned)__popc(mask));
+        base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    }
+    return base + __popc(mask & ((1u << lane_id()) - 1u));
+}
+
+// Knuth multiplicative hashing: the top log2(table size) bits of w * 2654435761
+// (shift = 32 - log2(table size), table size >= 2).
+__device__ __forceinline__ uint32_t hash_slot(uint32_t w, uint32_t shift) {
+    return (w * 2654435761u) >> shift;
+}
+#endif
+
+}  // namespace tc

@@ -1,0 +1,56 @@
+"""C-ABI library checks that need no GPU: it loads, and it exports exactly the
+entry points include/tc.h declares (and the Python binding names them)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "tc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return set(re.findall(r"\b(tc_[a-z_]+)\s*\(", text))
+
+
+def test_header_declares_the_boundary_calls():
+    names = declared_functions()
+    for must in ("tc_build_csr", "tc_count", "tc_count_batch", "tc_submit", "tc_poll"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2309_09064_gb300 as tc
+    path = tc.library_path()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r" T (tc_[a-z_]+)$", out, flags=re.M))
+    assert declared_functions() == exported
+    assert set(tc.EXPORTED) == exported
+    for name in exported:
+        assert callable(getattr(tc, name))
+
+
+def test_binding_raises_without_a_device():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_2309_09064_gb300 as tc
+    with pytest.raises(tc.TcError):
+        tc.tc_create(0)
+
+
+def test_product_code_never_touches_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2309_09064_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "oracle.c" not in text and "liboracle" not in text, f
+
+
+def test_build_entry_point():
+    import __graft_entry__
+    __graft_entry__.build()
