@@ -13,12 +13,6 @@ __global__ void k_ctl_reset(Ctl *ctl) {
     if (threadIdx.x == 0) ctl->root_key = ~0ull;
 }
 
-uint64_t next_pow2(uint64_t x) {
-    uint64_t p = 64;
-    while (p < x) p <<= 1;
-    return p;
-}
-
 tc_status pull(tc_ctx *ctx) {
     TC_CUDA(ctx, cudaMemcpyAsync(ctx->h_ctl, ctx->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, ctx->stream));
     TC_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
@@ -30,21 +24,22 @@ tc_status pull(tc_ctx *ctx) {
 // Bytes of scratch for a graph with n vertices, `slots` CSR slots and the
 // given maximum degree.
 size_t pipeline_bytes(const tc_ctx *ctx, uint32_t n, uint64_t slots, uint32_t max_deg, bool own_levels,
-                      uint64_t *hub_slots, uint32_t *hub_blocks) {
+                      uint64_t *hub_words, uint32_t *hub_maps) {
     auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t n1 = (size_t)n + 1;
     size_t bytes = 0;
-    bytes += 11 * r(4 * n1);                       // deg q0 q1 fdeg R parent hcnt scnt wlist blist ntask
+    bytes += 14 * r(4 * n1);                       // deg q0 q1 fdeg R parent hcnt scnt rows[3] ntask[3]
     if (own_levels) bytes += r(4 * n1);            // L
-    bytes += 3 * r(8 * n1);                        // fpref off2 tpref
+    bytes += 5 * r(8 * n1);                        // fpref off2 tpref[3]
     bytes += r(4 * (slots + 1));                   // adj2
     bytes += r(8 * scan_tmp_elems(n1 + 1));        // scan tiles
-    *hub_slots = 0;
-    *hub_blocks = 0;
+    bytes += r(8 * (slots / 2 + 1));               // task pool: at most one task per oriented G0 edge
+    *hub_words = 0;
+    *hub_maps = 0;
     if (max_deg > ctx->tune.block_cap) {
-        *hub_slots = next_pow2(2ull * max_deg);
-        *hub_blocks = (uint32_t)ctx->num_sms;
-        bytes += r(4ull * *hub_slots * *hub_blocks);
+        *hub_words = ((((uint64_t)n + 31) / 32) + 31) & ~uint64_t(31);
+        *hub_maps = ctx->tune.hub_group;
+        bytes += r(4ull * *hub_words * *hub_maps);
     }
     return bytes + 4096;
 }
@@ -53,9 +48,9 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
                          uint64_t *triangles, tc_stats *stats) {
     const uint32_t n = g.n;
     cudaStream_t s = ctx->stream;
-    uint64_t hub_slots = 0;
-    uint32_t hub_blocks = 0;
-    const size_t need = pipeline_bytes(ctx, n, g.slots, g.max_deg, levels_out == nullptr, &hub_slots, &hub_blocks);
+    uint64_t hub_words = 0;
+    uint32_t hub_maps = 0;
+    const size_t need = pipeline_bytes(ctx, n, g.slots, g.max_deg, levels_out == nullptr, &hub_words, &hub_maps);
     tc_status st = arena_reserve(ctx, need);
     if (st != TC_OK) return st;
     Arena &a = ctx->arena;
@@ -73,25 +68,25 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     b.parent = a.take<uint32_t>(n1);
     b.hcnt = a.take<uint32_t>(n1);
     b.scnt = a.take<uint32_t>(n1);
-    b.wlist = a.take<uint32_t>(n1);
-    b.blist = a.take<uint32_t>(n1);
-    b.ntask = a.take<uint32_t>(n1);
+    bool ok = b.deg && b.L && b.q0 && b.q1 && b.fdeg && b.R && b.parent && b.hcnt && b.scnt;
+    for (int c = 0; c < 3; ++c) {
+        b.rows[c] = a.take<uint32_t>(n1);
+        b.ntask[c] = a.take<uint32_t>(n1);
+        b.tpref[c] = a.take<uint64_t>(n1);
+        ok = ok && b.rows[c] && b.ntask[c] && b.tpref[c];
+    }
     b.fpref = a.take<uint64_t>(n1);
     b.off2 = a.take<uint64_t>(n1);
-    b.tpref = a.take<uint64_t>(n1);
     b.adj2 = a.take<uint32_t>(g.slots + 1);
     b.scan_tmp = a.take<uint64_t>(scan_tmp_elems(n1 + 1));
-    b.hub_slots = hub_slots;
-    b.hub_blocks = hub_blocks;
-    if (hub_blocks) b.hub_tables = a.take<uint32_t>(hub_slots * hub_blocks);
+    b.task_cap = g.slots / 2 + 1;
+    b.task_pool = a.take<uint2>(b.task_cap);
+    b.hub_words = hub_words;
+    if (hub_maps) b.hub_bits = a.take<uint32_t>(hub_words * hub_maps);
     b.groups = groups;
-    if (!b.deg || !b.L || !b.q0 || !b.q1 || !b.fdeg || !b.R || !b.parent || !b.hcnt || !b.scnt || !b.wlist ||
-        !b.blist || !b.ntask || !b.fpref || !b.off2 || !b.tpref || !b.adj2 || !b.scan_tmp ||
-        (hub_blocks && !b.hub_tables))
-        return set_error(ctx, TC_ERR_OOM, "arena carve failed");
+    ok = ok && b.fpref && b.off2 && b.adj2 && b.scan_tmp && b.task_pool && (!hub_maps || b.hub_bits);
+    if (!ok) return set_error(ctx, TC_ERR_OOM, "arena carve failed");
 
-    ctx->launches = 0;
-    ctx->isect_flags = 0;
     k_ctl_reset<<<1, 128, 0, s>>>(ctx->d_ctl);
     note_launch(ctx);
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[0], s));
@@ -100,10 +95,14 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[1], s));
     st = build_rows(ctx, b, n);
     if (st != TC_OK) return st;
-    st = pull(ctx);
+    st = pull(ctx);  // row counts per class
     if (st != TC_OK) return st;
-    const uint32_t nb = ctx->h_ctl->n_block_u;
-    note_launch(ctx, scan_u32_to_u64(b.ntask, b.tpref, nb, b.scan_tmp, s));
+    st = plan_scans(ctx, b);
+    if (st != TC_OK) return st;
+    st = pull(ctx);  // task counts per class
+    if (st != TC_OK) return st;
+    st = emit_tasks(ctx, b);
+    if (st != TC_OK) return st;
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
     st = intersect(ctx, b, n);
     if (st != TC_OK) return st;

@@ -3,109 +3,190 @@
 // reduction of the counts into 64-bit totals.
 //
 // As in the paper's hashed loop, the row of u (the endpoint that comes first
-// in the working order, i.e. the higher-degree one under the degree order) is
-// put in a hash set once, and the rows of all its horizontal out-neighbours v
-// are probed against it: the cost per edge is the length of v's row, at most
-// min(d(u), d(v)).  Rows are split by the size s(u) of the hashed row:
-//   warp class   s(u) <= warp_cap : one warp per u, table in the warp's slice
-//                                   of shared memory;
-//   block class  s(u) <= block_cap: one block per task (a slice of u's
-//                                   out-edges), table in shared memory;
-//   hub class    larger           : one block per task, table in a
-//                                   block-private region of global memory.
-// Tables use open addressing with linear probing at load factor <= 1/2.
+// in the working order, the higher-degree one under the degree order) is put
+// in a set once, and the rows of its horizontal out-neighbours v are probed
+// against it; the cost per edge is |row(v)| <= min(d(u), d(v)).  Rows are
+// split by the size s(u) of the hashed row, and every row's out-edges are cut
+// into tasks of bounded probe work:
+//   warp class  s(u) <= warp_cap : one warp per task, open-addressing table in
+//                                  the warp's slice of shared memory;
+//   block class s(u) <= block_cap: one block per task, table in shared memory;
+//   hub class   larger           : hub rows are taken `hub_group` at a time,
+//                                  each gets an n-bit bitmap in global memory
+//                                  (L2-resident while its group runs) and all
+//                                  SMs probe the group's tasks against them.
+// Probing is flattened: the rows of a batch of v's are viewed as one list and
+// every lane keeps kUnroll independent loads in flight.
+#include <algorithm>
+
 #include "pipeline.cuh"
 
 namespace tc {
 namespace {
 
+constexpr int kUnroll = 8;                 // elements in flight per lane
+constexpr uint32_t kChunk = 32 * kUnroll;  // elements per warp step
+
 struct Acc {
     unsigned long long same = 0, cross = 0, probes = 0;
 };
 
-template <bool kShared>
-__device__ __forceinline__ uint32_t tab_load(const uint32_t *tab, uint32_t slot) {
-    if (kShared) return tab[slot];
-    return __ldcg(tab + slot);
+// ---------------------------------------------------------------------------- set representations
+
+struct SmemTable {  // open addressing, linear probing, load factor <= 1/2
+    uint32_t *tab;
+    uint32_t shift, mask;
+    __device__ __forceinline__ bool has(uint32_t w) const {
+        uint32_t slot = hash_slot(w, shift);
+        for (;;) {
+            const uint32_t k = tab[slot];
+            if (k == w) return true;
+            if (k == kEmpty) return false;
+            slot = (slot + 1) & mask;
+        }
+    }
+};
+
+struct GlobalBitmap {  // one bit per vertex id, read-only while probing
+    const uint32_t *bits;
+    __device__ __forceinline__ bool has(uint32_t w) const { return (__ldg(bits + (w >> 5)) >> (w & 31)) & 1u; }
+};
+
+__device__ __forceinline__ uint32_t table_size_for(uint32_t len) {
+    uint32_t ts = 64;
+    while (ts < 2 * len) ts <<= 1;
+    return ts;
 }
 
-// Insert the distinct ids row[0..len) with `nthreads` cooperating threads
-// (thread index `t`).
-__device__ __forceinline__ void table_insert(uint32_t *tab, uint32_t shift, uint32_t mask, const uint32_t *row,
-                                             uint32_t len, uint32_t t, uint32_t nthreads) {
+// Size a shared table for len ids and clear it (threads t of nthreads).
+__device__ __forceinline__ SmemTable clear_table(uint32_t *tab, uint32_t len, uint32_t t, uint32_t nthreads) {
+    const uint32_t ts = table_size_for(len);
+    SmemTable T{tab, (uint32_t)__clz(ts) + 1u, ts - 1u};
+    for (uint32_t j = t; j < ts; j += nthreads) tab[j] = kEmpty;
+    return T;
+}
+
+// Insert the distinct ids row[0..len) (after a barrier following clear_table).
+__device__ __forceinline__ void fill_table(const SmemTable &T, const uint32_t *__restrict__ row, uint32_t len,
+                                           uint32_t t, uint32_t nthreads) {
     for (uint32_t j = t; j < len; j += nthreads) {
         const uint32_t w = row[j];
-        uint32_t slot = hash_slot(w, shift);
-        while (atomicCAS(tab + slot, kEmpty, w) != kEmpty) slot = (slot + 1) & mask;
+        uint32_t slot = hash_slot(w, T.shift);
+        while (atomicCAS(T.tab + slot, kEmpty, w) != kEmpty) slot = (slot + 1) & T.mask;
     }
 }
 
-template <bool kShared>
-__device__ __forceinline__ bool table_has(const uint32_t *tab, uint32_t shift, uint32_t mask, uint32_t w) {
-    uint32_t slot = hash_slot(w, shift);
-    for (;;) {
-        const uint32_t k = tab_load<kShared>(tab, slot);
-        if (k == w) return true;
-        if (k == kEmpty) return false;
-        slot = (slot + 1) & mask;
-    }
-}
+// ---------------------------------------------------------------------------- flattened probing
 
-// Probe the rows of v = H(u)[k] for k in [k_lo, k_hi) with one warp.  Lanes
-// fetch the metadata of 32 out-neighbours at a time; then the warp walks each
-// row, lanes striding over its entries.  An entry at position j of row(v) is a
-// G0 triangle when j < |H(v)|, else a cross-level triangle.
-template <bool kShared>
-__device__ __forceinline__ void probe_slice(const uint32_t *tab, uint32_t shift, uint32_t mask,
-                                            const uint32_t *__restrict__ hrow, uint32_t k_lo, uint32_t k_hi,
-                                            uint32_t k_step, const uint64_t *__restrict__ off2,
-                                            const uint32_t *__restrict__ adj2, const uint32_t *__restrict__ hcnt,
-                                            Acc &acc) {
+// Probe the flattened list of `nv` rows described by pre[0..nv] (exclusive
+// prefix of lengths, pre[nv] = total), rb[] (row starts in adj2) and rh[]
+// (|H(v)|), all in shared memory.  The warp takes chunks c_begin,
+// c_begin + c_step, ... of kChunk elements.  An element at position j of
+// row(v) is a G0 triangle when j < |H(v)|, otherwise cross-level.
+template <class Set>
+__device__ __forceinline__ void probe_flat(const Set &set, const uint32_t *__restrict__ adj2,
+                                           const uint32_t *pre, const unsigned long long *rb, const uint32_t *rh,
+                                           uint32_t nv, uint32_t c_begin, uint32_t c_step, Acc &acc) {
     const unsigned lane = lane_id();
-    for (uint32_t k0 = k_lo; k0 < k_hi; k0 += k_step) {
-        const uint32_t k = k0 + lane;
-        uint64_t vb = 0;
-        uint32_t vs = 0, vh = 0;
-        if (k < k_hi && lane < k_step) {
-            const uint32_t v = hrow[k];
-            vb = off2[v];
-            vs = (uint32_t)(off2[v + 1] - vb);
-            vh = hcnt[v];
+    const uint32_t total = pre[nv];
+    for (uint32_t f0 = c_begin * kChunk; f0 < total; f0 += c_step * kChunk) {
+        // row holding this lane's first element: largest t with pre[t] <= f
+        const uint32_t f = f0 + lane;
+        uint32_t t = 0;
+        if (f < total) {
+            uint32_t a = 0, b = nv;
+            while (b - a > 1) {
+                const uint32_t m = (a + b) >> 1;
+                if (pre[m] <= f) a = m; else b = m;
+            }
+            t = a;
         }
-        const uint32_t cnt = min(32u, min(k_step, k_hi - k0));
-        for (uint32_t t = 0; t < cnt; ++t) {
-            const uint64_t b = __shfl_sync(0xFFFFFFFFu, vb, t);
-            const uint32_t len = __shfl_sync(0xFFFFFFFFu, vs, t);
-            const uint32_t hv = __shfl_sync(0xFFFFFFFFu, vh, t);
-            acc.probes += len;
-            for (uint32_t j = lane; j < len; j += 32) {
-                const uint32_t w = adj2[b + j];
-                if (table_has<kShared>(tab, shift, mask, w)) {
-                    if (j < hv) ++acc.same; else ++acc.cross;
+        uint32_t lo = pre[t], hi = pre[t + 1];
+        unsigned long long base = rb[t];
+        uint32_t hv = rh[t];
+        uint32_t w[kUnroll];
+        bool cls[kUnroll];
+        bool ok[kUnroll];
+#pragma unroll
+        for (int i = 0; i < kUnroll; ++i) {
+            const uint32_t fi = f0 + (uint32_t)i * 32u + lane;
+            ok[i] = fi < total;
+            w[i] = 0;
+            cls[i] = false;
+            if (ok[i]) {
+                while (fi >= hi) {  // advance to the row holding fi; fi < total = pre[nv] bounds t < nv
+                    ++t;
+                    lo = hi;
+                    hi = pre[t + 1];
+                    base = rb[t];
+                    hv = rh[t];
                 }
+                const uint32_t j = fi - lo;
+                w[i] = adj2[base + j];
+                cls[i] = j < hv;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kUnroll; ++i) {
+            if (ok[i] && set.has(w[i])) {
+                if (cls[i]) ++acc.same; else ++acc.cross;
             }
         }
     }
+    if (lane == 0 && c_begin == 0) acc.probes += total;
 }
 
-__device__ __forceinline__ uint32_t table_size_for(uint32_t len, uint32_t min_size) {
-    uint32_t ts = min_size;
-    while (ts < 2 * len) ts <<= 1;
-    return ts;
+// Block-wide exclusive scan of len[0..nv) into pre[0..nv]; all threads of the
+// block call it; ends with a barrier.
+__device__ __forceinline__ void block_scan_lengths(const uint32_t *len, uint32_t *pre, uint32_t nv) {
+    __shared__ uint32_t warp_tot[32];
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t per = (nv + blockDim.x - 1) / blockDim.x;  // items per thread (contiguous)
+    const uint32_t beg = threadIdx.x * per;
+    uint32_t sum = 0;
+    for (uint32_t i = 0; i < per; ++i)
+        if (beg + i < nv) sum += len[beg + i];
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= (unsigned)o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t t = lane < nwarps ? warp_tot[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+            if (lane >= (unsigned)o) t += y;
+        }
+        warp_tot[lane] = t;
+    }
+    __syncthreads();
+    uint32_t run = (warp ? warp_tot[warp - 1] : 0u) + x - sum;
+    for (uint32_t i = 0; i < per; ++i) {
+        if (beg + i < nv) {
+            pre[beg + i] = run;
+            run += len[beg + i];
+        }
+    }
+    if (threadIdx.x == 0) pre[nv] = warp_tot[nwarps - 1];
+    __syncthreads();
 }
 
 __device__ __forceinline__ uint32_t group_of(const GroupSpec &g, uint32_t u) {
     uint32_t a = 0, b = g.n_groups;
     while (b - a > 1) {
-        uint32_t m = (a + b) >> 1;
+        const uint32_t m = (a + b) >> 1;
         if (g.vertex_start[m] <= u) a = m; else b = m;
     }
     return a;
 }
 
 // Reduce a warp's counters into the control block (class c: 0 warp, 1 block, 2 hub).
-__device__ __forceinline__ void flush(Acc &acc, Ctl *ctl, int c, unsigned long long build_elems,
-                                      unsigned long long rows) {
+__device__ __forceinline__ void flush(const Acc &acc, Ctl *ctl, int c, unsigned long long build_elems,
+                                      unsigned long long tasks) {
     const unsigned long long s = warp_sum(acc.same), x = warp_sum(acc.cross), p = warp_sum(acc.probes);
     if (lane_id() == 0) {
         if (s) atomicAdd(&ctl->t_same, s);
@@ -115,176 +196,310 @@ __device__ __forceinline__ void flush(Acc &acc, Ctl *ctl, int c, unsigned long l
             atomicAdd(&ctl->cls_probes[c], p);
         }
         if (build_elems) atomicAdd(&ctl->cls_build[c], build_elems);
-        if (rows) atomicAdd(&ctl->cls_rows[c], rows);
+        if (tasks) atomicAdd(&ctl->cls_rows[c], tasks);
     }
 }
 
-// Warp class: one warp per row u, dynamically scheduled.
-__global__ void k_isect_warp(const uint32_t *__restrict__ wlist, const uint64_t *__restrict__ off2,
-                             const uint32_t *__restrict__ adj2, const uint32_t *__restrict__ hcnt, Ctl *ctl,
-                             uint32_t table_slots, GroupSpec groups) {
-    extern __shared__ uint32_t smem[];
-    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
-    uint32_t *tab = smem + (size_t)warp * table_slots;
-    const uint32_t nw = ctl->n_warp_u;
+// ---------------------------------------------------------------------------- warp class
+
+struct WarpMeta {
+    unsigned long long b[32];
+    uint32_t pre[33];
+    uint32_t h[32];
+    uint32_t pad[3];
+};
+
+__global__ void __launch_bounds__(1024) k_isect_warp(const uint2 *__restrict__ tasks, const uint32_t *__restrict__ rows,
+                                                    const uint32_t *__restrict__ ntask,
+                                                    const uint64_t *__restrict__ off2, const uint32_t *__restrict__ adj2,
+                                                    const uint32_t *__restrict__ hcnt, Ctl *ctl, uint32_t table_slots,
+                                                    GroupSpec groups) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    WarpMeta *meta = reinterpret_cast<WarpMeta *>(smem_raw) + warp;
+    uint32_t *tab = reinterpret_cast<uint32_t *>(smem_raw + sizeof(WarpMeta) * nwarps) + (size_t)warp * table_slots;
+    const unsigned long long ntasks = ctl->n_tasks[0];
     Acc acc;
-    unsigned long long build = 0, rows = 0;
+    unsigned long long build = 0, done = 0;
     for (;;) {
-        uint32_t i = 0;
-        if (lane == 0) i = atomicAdd(&ctl->warp_next, 1u);
-        i = __shfl_sync(0xFFFFFFFFu, i, 0);
-        if (i >= nw) break;
-        const uint32_t u = wlist[i];
+        unsigned long long k = 0;
+        if (lane == 0) k = atomicAdd(&ctl->task_next[0], 1u);
+        k = __shfl_sync(0xFFFFFFFFu, k, 0);
+        if (k >= ntasks) break;
+        const uint2 task = tasks[k];
+        const uint32_t u = rows[task.x], nt = ntask[task.x];
         const uint64_t ub = off2[u];
         const uint32_t su = (uint32_t)(off2[u + 1] - ub);
         const uint32_t hu = hcnt[u];
-        const uint32_t ts = table_size_for(su, 64);
-        const uint32_t shift = __clz(ts) + 1, mask = ts - 1;
-        for (uint32_t j = lane; j < ts; j += 32) tab[j] = kEmpty;
+        const uint32_t k_lo = (uint32_t)((uint64_t)task.y * hu / nt), k_hi = (uint32_t)((uint64_t)(task.y + 1) * hu / nt);
+        const SmemTable T = clear_table(tab, su, lane, 32);
         __syncwarp();
-        table_insert(tab, shift, mask, adj2 + ub, su, lane, 32);
+        fill_table(T, adj2 + ub, su, lane, 32);
         __syncwarp();
-        build += su;
-        ++rows;
+        if (task.y == 0) build += su;
+        ++done;
         const unsigned long long before = acc.same + acc.cross;
-        probe_slice<true>(tab, shift, mask, adj2 + ub, 0, hu, 32, off2, adj2, hcnt, acc);
+        for (uint32_t k0 = k_lo; k0 < k_hi; k0 += 32) {
+            const uint32_t kk = k0 + lane;
+            uint32_t len = 0, hv = 0;
+            unsigned long long b = 0;
+            if (kk < k_hi) {
+                const uint32_t v = adj2[ub + kk];
+                b = off2[v];
+                len = (uint32_t)(off2[v + 1] - b);
+                hv = hcnt[v];
+            }
+            uint32_t x = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                if (lane >= (unsigned)o) x += y;
+            }
+            meta->pre[lane + 1] = x;
+            if (lane == 0) meta->pre[0] = 0;
+            meta->b[lane] = b;
+            meta->h[lane] = hv;
+            __syncwarp();
+            const uint32_t nv = min(32u, k_hi - k0);
+            probe_flat(T, adj2, meta->pre, meta->b, meta->h, nv, 0, 1, acc);
+            __syncwarp();
+        }
         if (groups.n_groups) {
             const unsigned long long found = warp_sum(acc.same + acc.cross - before);
             if (lane == 0 && found) atomicAdd(&groups.counts[group_of(groups, u)], found);
         }
         __syncwarp();
     }
-    flush(acc, ctl, 0, lane == 0 ? build : 0, lane == 0 ? rows : 0);
+    flush(acc, ctl, 0, lane == 0 ? build : 0, lane == 0 ? done : 0);
 }
 
-// Block and hub classes: one block per task (u, slice t of nt).
-template <bool kShared>
-__global__ void k_isect_block(const uint32_t *__restrict__ blist, const uint32_t *__restrict__ ntask,
-                              const unsigned long long *__restrict__ tpref, const uint64_t *__restrict__ off2,
-                              const uint32_t *__restrict__ adj2, const uint32_t *__restrict__ hcnt, Ctl *ctl,
-                              uint32_t block_cap, uint32_t *hub_tables, uint64_t hub_slots, GroupSpec groups) {
-    extern __shared__ uint32_t smem[];
-    __shared__ uint32_t s_task[4];
+// ---------------------------------------------------------------------------- block and hub classes
+
+// Per-task shared metadata of up to max_v out-neighbours.
+struct SliceSmem {
+    unsigned long long *b;
+    uint32_t *h, *len, *pre;
+};
+
+__device__ __forceinline__ SliceSmem carve_slice(unsigned char *p, uint32_t max_v) {
+    SliceSmem s;
+    s.b = reinterpret_cast<unsigned long long *>(p);
+    s.h = reinterpret_cast<uint32_t *>(p + 8ull * max_v);
+    s.len = s.h + max_v;
+    s.pre = s.len + max_v;
+    return s;
+}
+
+__host__ __device__ constexpr size_t slice_smem_bytes(uint32_t max_v) { return 8ull * max_v + 12ull * max_v + 16; }
+
+// Load the metadata of v = hrow[k], k in [k_lo, k_hi), and scan the lengths.
+__device__ __forceinline__ uint32_t load_slice(const SliceSmem &S, const uint32_t *__restrict__ hrow, uint32_t k_lo,
+                                               uint32_t k_hi, const uint64_t *__restrict__ off2,
+                                               const uint32_t *__restrict__ hcnt) {
+    const uint32_t nv = k_hi - k_lo;
+    for (uint32_t i = threadIdx.x; i < nv; i += blockDim.x) {
+        const uint32_t v = hrow[k_lo + i];
+        const unsigned long long b = off2[v];
+        S.b[i] = b;
+        S.len[i] = (uint32_t)(off2[v + 1] - b);
+        S.h[i] = hcnt[v];
+    }
+    __syncthreads();
+    block_scan_lengths(S.len, S.pre, nv);
+    return nv;
+}
+
+// Thread 0 takes the next task index of class c; all threads see it.
+__device__ __forceinline__ bool next_task(Ctl *ctl, int c, unsigned long long first, unsigned long long last,
+                                          const uint2 *tasks, uint2 *s_task) {
+    if (threadIdx.x == 0) {
+        const unsigned long long k = first + atomicAdd(&ctl->task_next[c], 1u);
+        s_task[0] = k < last ? tasks[k] : make_uint2(0xFFFFFFFFu, 0u);
+    }
+    __syncthreads();
+    return s_task[0].x != 0xFFFFFFFFu;
+}
+
+__global__ void __launch_bounds__(1024) k_isect_block(const uint2 *__restrict__ tasks, const uint32_t *__restrict__ rows,
+                                                      const uint32_t *__restrict__ ntask,
+                                                      const uint64_t *__restrict__ off2,
+                                                      const uint32_t *__restrict__ adj2,
+                                                      const uint32_t *__restrict__ hcnt, Ctl *ctl, uint32_t max_v,
+                                                      GroupSpec groups) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint2 s_task[1];
     __shared__ unsigned long long s_found;
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const uint32_t nb = ctl->n_block_u;
-    const unsigned long long total = tpref[nb];
-    uint32_t *tab = kShared ? smem : hub_tables + (size_t)blockIdx.x * hub_slots;
+    const SliceSmem S = carve_slice(smem_raw, max_v);
+    uint32_t *tab = reinterpret_cast<uint32_t *>(smem_raw + ((slice_smem_bytes(max_v) + 15) & ~size_t(15)));
+    const unsigned long long ntasks = ctl->n_tasks[1];
     Acc acc;
-    unsigned long long build = 0, tasks = 0;
+    unsigned long long build = 0, done = 0;
     for (;;) {
+        if (threadIdx.x == 0) s_found = 0;
+        if (!next_task(ctl, 1, 0, ntasks, tasks, s_task)) break;
+        const uint2 task = s_task[0];
+        const uint32_t u = rows[task.x], nt = ntask[task.x];
+        const uint64_t ub = off2[u];
+        const uint32_t su = (uint32_t)(off2[u + 1] - ub);
+        const uint32_t hu = hcnt[u];
+        const uint32_t k_lo = (uint32_t)((uint64_t)task.y * hu / nt), k_hi = (uint32_t)((uint64_t)(task.y + 1) * hu / nt);
+        const SmemTable T = clear_table(tab, su, threadIdx.x, blockDim.x);
+        const uint32_t nv = load_slice(S, adj2 + ub, k_lo, k_hi, off2, hcnt);  // has barriers after the clear
+        fill_table(T, adj2 + ub, su, threadIdx.x, blockDim.x);
+        __syncthreads();
         if (threadIdx.x == 0) {
-            const unsigned long long k = atomicAdd(&ctl->block_next, 1u);
-            uint32_t i = 0xFFFFFFFFu;
-            if (k < total) {
-                uint32_t a = 0, b = nb;
-                while (b - a > 1) {
-                    uint32_t m = (a + b) >> 1;
-                    if (tpref[m] <= k) a = m; else b = m;
-                }
-                i = a;
-            }
-            s_task[0] = i;
-            s_task[1] = i != 0xFFFFFFFFu ? (uint32_t)(k - tpref[i]) : 0;
-            s_found = 0;
+            if (task.y == 0) build += su;
+            ++done;
+        }
+        const unsigned long long before = acc.same + acc.cross;
+        probe_flat(T, adj2, S.pre, S.b, S.h, nv, warp, nwarps, acc);
+        if (groups.n_groups) {
+            const unsigned long long found = warp_sum(acc.same + acc.cross - before);
+            if (lane == 0 && found) atomicAdd(&s_found, found);
         }
         __syncthreads();
-        const uint32_t i = s_task[0];
-        if (i == 0xFFFFFFFFu) break;
-        const uint32_t u = blist[i];
-        const uint32_t su = (uint32_t)(off2[u + 1] - off2[u]);
-        // this block class takes rows above or below block_cap, per instantiation
-        const bool mine = kShared ? su <= block_cap : su > block_cap;
-        if (mine) {
-            const uint32_t t = s_task[1], nt = ntask[i];
-            const uint64_t ub = off2[u];
-            const uint32_t hu = hcnt[u];
-            const uint32_t k_lo = (uint32_t)((uint64_t)t * hu / nt), k_hi = (uint32_t)((uint64_t)(t + 1) * hu / nt);
-            const uint32_t ts = table_size_for(su, 64);
-            const uint32_t shift = __clz(ts) + 1, mask = ts - 1;
-            for (uint32_t j = threadIdx.x; j < ts; j += blockDim.x) tab[j] = kEmpty;
-            if (!kShared) __threadfence_block();
-            __syncthreads();
-            table_insert(tab, shift, mask, adj2 + ub, su, threadIdx.x, blockDim.x);
-            if (!kShared) __threadfence_block();
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                if (t == 0) build += su;
-                ++tasks;
-            }
-            const unsigned long long before = acc.same + acc.cross;
-            // warps take 32-edge chunks of the slice in turn
-            for (uint32_t c0 = k_lo + warp * 32; c0 < k_hi; c0 += nwarps * 32)
-                probe_slice<kShared>(tab, shift, mask, adj2 + ub, c0, min(c0 + 32, k_hi), 32, off2, adj2, hcnt, acc);
-            if (groups.n_groups) {
-                const unsigned long long found = warp_sum(acc.same + acc.cross - before);
-                if (lane == 0 && found) atomicAdd(&s_found, found);
-            }
-        }
-        __syncthreads();
-        if (mine && groups.n_groups && threadIdx.x == 0 && s_found)
-            atomicAdd(&groups.counts[group_of(groups, u)], s_found);
+        if (groups.n_groups && threadIdx.x == 0 && s_found) atomicAdd(&groups.counts[group_of(groups, u)], s_found);
     }
-    flush(acc, ctl, kShared ? 1 : 2, threadIdx.x == 0 ? build : 0, threadIdx.x == 0 ? tasks : 0);
+    flush(acc, ctl, 1, threadIdx.x == 0 ? build : 0, threadIdx.x == 0 ? done : 0);
+}
+
+// Set the bits of hub rows rows[i0 .. i0+g) into bitmaps bits + r * words.
+__global__ void k_hub_set(const uint32_t *__restrict__ rows, uint32_t i0, uint32_t g,
+                          const uint64_t *__restrict__ off2, const uint32_t *__restrict__ adj2, uint32_t *bits,
+                          uint64_t words) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint32_t r = 0; r < g; ++r) {
+        const uint32_t u = rows[i0 + r];
+        const uint64_t b = off2[u], e = off2[u + 1];
+        uint32_t *bm = bits + (uint64_t)r * words;
+        for (uint64_t j = b + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < e; j += stride) {
+            const uint32_t w = adj2[j];
+            atomicOr(bm + (w >> 5), 1u << (w & 31));
+        }
+    }
+}
+
+// Probe the tasks [first, last) of the hub rows with row index in
+// [i0, i0 + hub_group) against their bitmaps.
+__global__ void __launch_bounds__(1024) k_isect_hub(const uint2 *__restrict__ tasks, unsigned long long first,
+                                                    unsigned long long last, const uint32_t *__restrict__ rows,
+                                                    const uint32_t *__restrict__ ntask, uint32_t i0,
+                                                    const uint64_t *__restrict__ off2, const uint32_t *__restrict__ adj2,
+                                                    const uint32_t *__restrict__ hcnt, Ctl *ctl, const uint32_t *bits,
+                                                    uint64_t words, uint32_t max_v, GroupSpec groups) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint2 s_task[1];
+    __shared__ unsigned long long s_found;
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const SliceSmem S = carve_slice(smem_raw, max_v);
+    Acc acc;
+    unsigned long long build = 0, done = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_found = 0;
+        if (!next_task(ctl, 2, first, last, tasks, s_task)) break;
+        const uint2 task = s_task[0];
+        const uint32_t u = rows[task.x], nt = ntask[task.x];
+        const uint64_t ub = off2[u];
+        const uint32_t hu = hcnt[u];
+        const uint32_t k_lo = (uint32_t)((uint64_t)task.y * hu / nt), k_hi = (uint32_t)((uint64_t)(task.y + 1) * hu / nt);
+        const GlobalBitmap B{bits + (uint64_t)(task.x - i0) * words};
+        const uint32_t nv = load_slice(S, adj2 + ub, k_lo, k_hi, off2, hcnt);
+        if (threadIdx.x == 0) {
+            if (task.y == 0) build += (uint32_t)(off2[u + 1] - ub);
+            ++done;
+        }
+        const unsigned long long before = acc.same + acc.cross;
+        probe_flat(B, adj2, S.pre, S.b, S.h, nv, warp, nwarps, acc);
+        if (groups.n_groups) {
+            const unsigned long long found = warp_sum(acc.same + acc.cross - before);
+            if (lane == 0 && found) atomicAdd(&s_found, found);
+        }
+        __syncthreads();
+        if (groups.n_groups && threadIdx.x == 0 && s_found) atomicAdd(&groups.counts[group_of(groups, u)], s_found);
+    }
+    flush(acc, ctl, 2, threadIdx.x == 0 ? build : 0, threadIdx.x == 0 ? done : 0);
+}
+
+uint32_t pow2_at_least(uint64_t x) {
+    uint32_t t = 64;
+    while (t < x) t <<= 1;
+    return t;
 }
 
 }  // namespace
 
+size_t warp_kernel_smem(const Tuning &tu) {
+    return (size_t)tu.warps_per_block * (sizeof(WarpMeta) + 4ull * pow2_at_least(2ull * tu.warp_cap));
+}
+size_t block_kernel_smem(const Tuning &tu) {
+    return ((slice_smem_bytes(tu.max_v) + 15) & ~size_t(15)) + 4ull * pow2_at_least(2ull * tu.block_cap);
+}
+size_t hub_kernel_smem(const Tuning &tu) { return slice_smem_bytes(tu.max_v); }
+
 tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
+    (void)n;
     cudaStream_t s = ctx->stream;
     const Tuning &tu = ctx->tune;
-    const Ctl &h = *ctx->h_ctl;  // pulled after build_rows
-    auto *tpref = reinterpret_cast<const unsigned long long *>(b.tpref);
+    const Ctl &h = *ctx->h_ctl;  // pulled after planning
     // ev[4..7] bracket the warp, block and hub kernels
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[4], s));
-    if (h.n_warp_u) {
-        const uint32_t slots = [&] {
-            uint32_t t = 64;
-            while (t < 2 * tu.warp_cap) t <<= 1;
-            return t;
-        }();
-        const size_t smem = (size_t)tu.warps_per_block * slots * sizeof(uint32_t);
+    if (h.n_tasks[0]) {
+        const uint32_t slots = pow2_at_least(2ull * tu.warp_cap);
+        const size_t smem = warp_kernel_smem(tu);
         TC_CUDA(ctx, cudaFuncSetAttribute(k_isect_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
         TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect_warp, 32 * tu.warps_per_block, smem));
         if (per_sm < 1) per_sm = 1;
-        unsigned grid = (unsigned)(ctx->num_sms * per_sm);
-        const unsigned need = (h.n_warp_u + tu.warps_per_block - 1) / tu.warps_per_block;
+        uint64_t grid = (uint64_t)ctx->num_sms * per_sm;
+        const uint64_t need = (h.n_tasks[0] + tu.warps_per_block - 1) / tu.warps_per_block;
         if (grid > need) grid = need;
-        k_isect_warp<<<grid, 32 * tu.warps_per_block, smem, s>>>(b.wlist, b.off2, b.adj2, b.hcnt, ctx->d_ctl, slots,
-                                                                  b.groups);
+        k_isect_warp<<<(unsigned)grid, 32 * tu.warps_per_block, smem, s>>>(b.tasks[0], b.rows[0], b.ntask[0], b.off2,
+                                                                            b.adj2, b.hcnt, ctx->d_ctl, slots, b.groups);
         note_launch(ctx);
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[5], s));
-    bool hub = false;
-    if (h.n_block_u) {
-        const uint32_t slots = [&] {
-            uint32_t t = 64;
-            while (t < 2 * tu.block_cap) t <<= 1;
-            return t;
-        }();
-        const size_t smem = (size_t)slots * sizeof(uint32_t);
-        TC_CUDA(ctx, cudaFuncSetAttribute(k_isect_block<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (h.n_tasks[1]) {
+        const size_t smem = block_kernel_smem(tu);
+        TC_CUDA(ctx, cudaFuncSetAttribute(k_isect_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
-        TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect_block<true>, tu.block_threads, smem));
+        TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect_block, tu.block_threads, smem));
         if (per_sm < 1) per_sm = 1;
-        k_isect_block<true><<<(unsigned)(ctx->num_sms * per_sm), tu.block_threads, smem, s>>>(
-            b.blist, b.ntask, tpref, b.off2, b.adj2, b.hcnt, ctx->d_ctl, tu.block_cap, nullptr, 0, b.groups);
+        uint64_t grid = (uint64_t)ctx->num_sms * per_sm;
+        if (grid > h.n_tasks[1]) grid = h.n_tasks[1];
+        k_isect_block<<<(unsigned)grid, tu.block_threads, smem, s>>>(b.tasks[1], b.rows[1], b.ntask[1], b.off2, b.adj2,
+                                                                     b.hcnt, ctx->d_ctl, tu.max_v, b.groups);
         note_launch(ctx);
-        hub = h.max_s2 > tu.block_cap;
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[6], s));
-    if (hub) {
-        {
-            TC_CUDA(ctx, cudaMemsetAsync(&ctx->d_ctl->block_next, 0, sizeof(unsigned), s));
-            k_isect_block<false><<<b.hub_blocks, tu.block_threads, 0, s>>>(
-                b.blist, b.ntask, tpref, b.off2, b.adj2, b.hcnt, ctx->d_ctl, tu.block_cap, b.hub_tables, b.hub_slots,
-                b.groups);
-            note_launch(ctx);
+    const uint32_t nh = h.n_rows[2];
+    if (nh) {
+        // task ranges of the hub rows: the host walks the groups
+        std::vector<unsigned long long> pref(nh + 1);
+        TC_CUDA(ctx, cudaMemcpyAsync(pref.data(), b.tpref[2], 8ull * (nh + 1), cudaMemcpyDeviceToHost, s));
+        TC_CUDA(ctx, cudaStreamSynchronize(s));
+        const size_t smem = hub_kernel_smem(tu);
+        TC_CUDA(ctx, cudaFuncSetAttribute(k_isect_hub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int per_sm = 0;
+        TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect_hub, tu.hub_threads, smem));
+        if (per_sm < 1) per_sm = 1;
+        for (uint32_t i0 = 0; i0 < nh; i0 += tu.hub_group) {
+            const uint32_t g = std::min<uint32_t>(tu.hub_group, nh - i0);
+            TC_CUDA(ctx, cudaMemsetAsync(b.hub_bits, 0, 4ull * b.hub_words * g, s));
+            TC_CUDA(ctx, cudaMemsetAsync(&ctx->d_ctl->task_next[2], 0, sizeof(unsigned), s));
+            k_hub_set<<<(unsigned)ctx->num_sms * 4u, 256, 0, s>>>(b.rows[2], i0, g, b.off2, b.adj2, b.hub_bits,
+                                                                 b.hub_words);
+            const unsigned long long first = pref[i0], last = pref[i0 + g];
+            uint64_t grid = (uint64_t)ctx->num_sms * per_sm;
+            if (grid > last - first) grid = last - first;
+            k_isect_hub<<<(unsigned)grid, tu.hub_threads, smem, s>>>(b.tasks[2], first, last, b.rows[2], b.ntask[2], i0,
+                                                                     b.off2, b.adj2, b.hcnt, ctx->d_ctl, b.hub_bits,
+                                                                     b.hub_words, tu.max_v, b.groups);
+            note_launch(ctx, 2);
         }
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[7], s));
-    ctx->isect_flags = (h.n_warp_u ? 1u : 0u) | (h.n_block_u ? 2u : 0u) | (hub ? 4u : 0u);
+    ctx->isect_flags = (h.n_tasks[0] ? 1u : 0u) | (h.n_tasks[1] ? 2u : 0u) | (nh ? 4u : 0u);
     TC_CUDA(ctx, cudaGetLastError());
     return TC_OK;
 }

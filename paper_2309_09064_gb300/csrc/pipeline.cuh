@@ -25,21 +25,27 @@ struct PipeBufs {
     uint32_t *scnt = nullptr;       // [n]   |G0 out-list(x)| + |G1(x)|
     uint64_t *off2 = nullptr;       // [n+1] offsets of the compacted rows
     uint32_t *adj2 = nullptr;       // [S]   rows [G0 out-list | G1 list], each part ascending
-    // intersection planning
-    uint32_t *wlist = nullptr;      // [n]   warp-class rows u
-    uint32_t *blist = nullptr;      // [n]   block-class rows u
-    uint32_t *ntask = nullptr;      // [n]   tasks per block-class row
-    uint64_t *tpref = nullptr;      // [n+1] exclusive prefix of ntask
-    uint32_t *hub_tables = nullptr; // global tables for rows too large for shared memory
-    uint64_t hub_slots = 0;         // slots per hub table
-    uint32_t hub_blocks = 0;        // number of hub tables
+    // intersection planning, per class c (0 warp, 1 block, 2 hub)
+    uint32_t *rows[3] = {};         // [n]   hashed rows u of class c
+    uint32_t *ntask[3] = {};        // [n]   tasks per row
+    uint64_t *tpref[3] = {};        // [n+1] exclusive prefix of ntask
+    uint2 *tasks[3] = {};           // {row index i, slice t} per task (carved after planning)
+    uint2 *task_pool = nullptr;     // capacity task_cap
+    uint64_t task_cap = 0;
+    uint32_t *hub_bits = nullptr;   // hub_group bitmaps of hub_words words each
+    uint64_t hub_words = 0;
     uint64_t *scan_tmp = nullptr;
     // batched counting of a disjoint union
     GroupSpec groups;
 };
 
 tc_status compute_levels(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t slots);
+// partition, orientation, compaction, classification and per-class task counts
 tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n);
+// scans of the per-class task counts (after the host has read the row counts)
+tc_status plan_scans(tc_ctx *ctx, const PipeBufs &b);
+// task emission (after the host knows the task totals)
+tc_status emit_tasks(tc_ctx *ctx, PipeBufs &b);
 tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n);
 
 }  // namespace tc

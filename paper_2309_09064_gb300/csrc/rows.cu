@@ -92,24 +92,27 @@ __global__ void k_row_fill(uint32_t n, const uint64_t *__restrict__ rp, const ui
 }
 
 // Rows with at least one oriented horizontal edge are the hashed side of the
-// intersections; split them by the size of their compacted row.
+// intersections; split them by the size s(u) of their compacted row:
+// class 0 (warp) s <= warp_cap, class 1 (block) s <= block_cap, class 2 (hub).
 __global__ void k_classify(uint32_t n, const uint32_t *__restrict__ hcnt, const uint32_t *__restrict__ scnt,
-                           uint32_t *__restrict__ wlist, uint32_t *__restrict__ blist, Ctl *ctl, uint32_t warp_cap) {
+                           uint32_t *__restrict__ r0, uint32_t *__restrict__ r1, uint32_t *__restrict__ r2, Ctl *ctl,
+                           uint32_t warp_cap, uint32_t block_cap) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t n_round = ((uint64_t)n + 31) & ~uint64_t(31);
     unsigned my_max = 0;
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_round; x += stride) {
-        bool active = x < n && hcnt[x] > 0;
-        uint32_t s = active ? scnt[x] : 0;
-        bool w = active && s <= warp_cap;
-        bool bl = active && s > warp_cap;
-        uint32_t sw = warp_append(w, &ctl->n_warp_u);
-        uint32_t sb = warp_append(bl, &ctl->n_block_u);
-        if (w) wlist[sw] = (uint32_t)x;
-        if (bl) {
-            blist[sb] = (uint32_t)x;
-            my_max = s > my_max ? s : my_max;
-        }
+        const bool active = x < n && hcnt[x] > 0;
+        const uint32_t s = active ? scnt[x] : 0;
+        const bool c0 = active && s <= warp_cap;
+        const bool c1 = active && s > warp_cap && s <= block_cap;
+        const bool c2 = active && s > block_cap;
+        const uint32_t p0 = warp_append(c0, &ctl->n_rows[0]);
+        const uint32_t p1 = warp_append(c1, &ctl->n_rows[1]);
+        const uint32_t p2 = warp_append(c2, &ctl->n_rows[2]);
+        if (c0) r0[p0] = (uint32_t)x;
+        if (c1) r1[p1] = (uint32_t)x;
+        if (c2) r2[p2] = (uint32_t)x;
+        if (c1 || c2) my_max = s > my_max ? s : my_max;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -119,18 +122,19 @@ __global__ void k_classify(uint32_t n, const uint32_t *__restrict__ hcnt, const 
     if (lane_id() == 0 && my_max) atomicMax(&ctl->max_s2, my_max);
 }
 
-// Split each block-class row u into tasks of about `target` probes:
-// ntask = clamp(ceil(work(u) / max(task_work, 2 s(u))), 1, |H(u)|) where
-// work(u) = sum of s(v) over v in H(u).  A task takes a contiguous slice of H(u).
-__global__ void k_plan(const uint32_t *__restrict__ blist, const Ctl *__restrict__ ctl,
+// Split every hashed row u of class c into tasks (contiguous slices of H(u))
+// of about `target` probes: work(u) = sum of s(v) over v in H(u),
+// ntask = ceil(work(u) / max(task_work, min_mult * s(u))), at least
+// ceil(|H(u)| / max_v) (shared-memory metadata of one task), at most |H(u)|.
+__global__ void k_plan(const uint32_t *__restrict__ rows, const unsigned int *__restrict__ n_rows,
                        const uint64_t *__restrict__ off2, const uint32_t *__restrict__ adj2,
                        const uint32_t *__restrict__ hcnt, const uint32_t *__restrict__ scnt,
-                       uint32_t *__restrict__ ntask, uint32_t task_work) {
+                       uint32_t *__restrict__ ntask, uint32_t task_work, uint32_t min_mult, uint32_t max_v) {
     const unsigned lane = lane_id();
-    const uint32_t nb = ctl->n_block_u;
+    const uint32_t nr = *n_rows;
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nb; i += warps) {
-        const uint32_t u = blist[i];
+    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nr; i += warps) {
+        const uint32_t u = rows[i];
         const uint64_t b = off2[u];
         const uint32_t hu = hcnt[u];
         unsigned long long work = 0;
@@ -138,12 +142,32 @@ __global__ void k_plan(const uint32_t *__restrict__ blist, const Ctl *__restrict
         work = warp_sum(work);
         if (lane == 0) {
             const unsigned long long su = scnt[u];
-            const unsigned long long target = 2 * su > task_work ? 2 * su : task_work;
+            const unsigned long long floor_t = (unsigned long long)min_mult * su;
+            const unsigned long long target = floor_t > task_work ? floor_t : task_work;
             unsigned long long nt = (work + target - 1) / target;
+            const unsigned long long by_v = (hu + max_v - 1) / max_v;
+            if (nt < by_v) nt = by_v;
             if (nt < 1) nt = 1;
             if (nt > hu) nt = hu;
             ntask[i] = (uint32_t)nt;
         }
+    }
+}
+
+__global__ void k_task_totals(Ctl *ctl, const unsigned long long *__restrict__ p0,
+                              const unsigned long long *__restrict__ p1, const unsigned long long *__restrict__ p2) {
+    ctl->n_tasks[0] = p0[ctl->n_rows[0]];
+    ctl->n_tasks[1] = p1[ctl->n_rows[1]];
+    ctl->n_tasks[2] = p2[ctl->n_rows[2]];
+}
+
+__global__ void k_emit(const uint32_t *__restrict__ ntask, const unsigned long long *__restrict__ tpref, uint32_t nr,
+                       uint2 *__restrict__ tasks) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += stride) {
+        const unsigned long long base = tpref[i];
+        const uint32_t nt = ntask[i];
+        for (uint32_t t = 0; t < nt; ++t) tasks[base + t] = make_uint2(i, t);
     }
 }
 
@@ -160,18 +184,60 @@ tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n) {
     cudaStream_t s = ctx->stream;
     const unsigned cap = (unsigned)ctx->num_sms * 16u;
     const uint32_t order = ctx->opt.order;
+    const Tuning &tu = ctx->tune;
     if (n == 0) return TC_OK;
     k_row_count<<<grid_for((uint64_t)n * 32, 256, cap), 256, 0, s>>>(n, b.rp, b.col, b.deg, b.L, b.hcnt, b.scnt,
                                                                      ctx->d_ctl, order);
-    const uint32_t scan_launches = scan_u32_to_u64(b.scnt, b.off2, n, b.scan_tmp, s);
+    uint32_t launches = 1 + scan_u32_to_u64(b.scnt, b.off2, n, b.scan_tmp, s);
     k_row_fill<<<grid_for((uint64_t)n * 32, 256, cap), 256, 0, s>>>(n, b.rp, b.col, b.deg, b.L, b.hcnt, b.off2,
                                                                     b.adj2, order);
-    k_classify<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.hcnt, b.scnt, b.wlist, b.blist, ctx->d_ctl,
-                                                     ctx->tune.warp_cap);
-    // planning covers at most n block-class rows; the kernel reads the true count
-    k_plan<<<grid_for((uint64_t)n * 32, 256, cap), 256, 0, s>>>(b.blist, ctx->d_ctl, b.off2, b.adj2, b.hcnt, b.scnt,
-                                                                b.ntask, ctx->tune.task_work);
-    note_launch(ctx, 4 + scan_launches);
+    k_classify<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.hcnt, b.scnt, b.rows[0], b.rows[1], b.rows[2], ctx->d_ctl,
+                                                     tu.warp_cap, tu.block_cap);
+    launches += 2;
+    const uint32_t work[3] = {tu.warp_task_work, tu.task_work, tu.hub_task_work};
+    const uint32_t mult[3] = {1, 2, 2};
+    const uint32_t maxv[3] = {0xFFFFFFFFu, tu.max_v, tu.max_v};
+    for (int c = 0; c < 3; ++c) {
+        k_plan<<<grid_for((uint64_t)n * 32, 256, cap), 256, 0, s>>>(b.rows[c], &ctx->d_ctl->n_rows[c], b.off2, b.adj2,
+                                                                    b.hcnt, b.scnt, b.ntask[c], work[c], mult[c],
+                                                                    maxv[c]);
+        ++launches;
+    }
+    note_launch(ctx, launches);
+    TC_CUDA(ctx, cudaGetLastError());
+    return TC_OK;
+}
+
+// After the host has read n_rows: scan the task counts, publish the totals.
+tc_status plan_scans(tc_ctx *ctx, const PipeBufs &b) {
+    cudaStream_t s = ctx->stream;
+    uint32_t launches = 1;
+    for (int c = 0; c < 3; ++c)
+        launches += scan_u32_to_u64(b.ntask[c], b.tpref[c], ctx->h_ctl->n_rows[c], b.scan_tmp, s);
+    k_task_totals<<<1, 1, 0, s>>>(ctx->d_ctl, reinterpret_cast<const unsigned long long *>(b.tpref[0]),
+                                  reinterpret_cast<const unsigned long long *>(b.tpref[1]),
+                                  reinterpret_cast<const unsigned long long *>(b.tpref[2]));
+    note_launch(ctx, launches);
+    TC_CUDA(ctx, cudaGetLastError());
+    return TC_OK;
+}
+
+tc_status emit_tasks(tc_ctx *ctx, PipeBufs &b) {
+    cudaStream_t s = ctx->stream;
+    const unsigned cap = (unsigned)ctx->num_sms * 16u;
+    uint64_t off = 0;
+    for (int c = 0; c < 3; ++c) {
+        b.tasks[c] = b.task_pool + off;
+        off += ctx->h_ctl->n_tasks[c];
+    }
+    if (off > b.task_cap) return set_error(ctx, TC_ERR_OOM, "task list exceeds its bound");
+    for (int c = 0; c < 3; ++c) {
+        const uint32_t nr = ctx->h_ctl->n_rows[c];
+        if (!nr) continue;
+        k_emit<<<grid_for(nr, 256, cap), 256, 0, s>>>(b.ntask[c], reinterpret_cast<const unsigned long long *>(b.tpref[c]),
+                                                     nr, b.tasks[c]);
+        note_launch(ctx);
+    }
     TC_CUDA(ctx, cudaGetLastError());
     return TC_OK;
 }

@@ -24,11 +24,16 @@ constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 // Class boundaries of the intersection stage by the size s(u) of the hashed
 // row [G0 out-list | G1 list] of the higher-ranked endpoint u.
 struct Tuning {
-    uint32_t warp_cap = 1024;        // s(u) <= warp_cap: one warp per u, per-warp smem table
-    uint32_t block_cap = 16384;      // s(u) <= block_cap: one block per task, smem table
-    uint32_t task_work = 65536;      // target probes per block task (heavy rows are split)
+    uint32_t warp_cap = 1024;        // s(u) <= warp_cap: warp tasks, per-warp smem table
+    uint32_t block_cap = 16384;      // s(u) <= block_cap: block tasks, smem table; larger: hub tasks
+    uint32_t task_work = 65536;      // target probes per block task (at least 2 s(u))
     uint32_t warps_per_block = 8;    // warp-class kernel: warps per block
-    uint32_t block_threads = 512;    // block/hub-class kernel threads
+    uint32_t block_threads = 1024;   // block-class kernel threads
+    uint32_t warp_task_work = 16384; // target probes per warp task
+    uint32_t hub_task_work = 131072; // target probes per hub task
+    uint32_t max_v = 2048;           // out-neighbours per block / hub task (shared-memory metadata)
+    uint32_t hub_group = 8;          // hub rows sharing one launch (one L2-resident bitmap each)
+    uint32_t hub_threads = 1024;     // hub kernel threads
 };
 
 // Control block in device memory: counters the kernels update and the host
@@ -50,12 +55,11 @@ struct Ctl {
     unsigned int components;         // BFS roots
     unsigned int changed;            // CC hooking made progress
     unsigned int n_residual;
-    unsigned int n_warp_u;           // warp-class rows
-    unsigned int n_block_u;          // block-class rows (incl. hubs)
-    unsigned int warp_next;          // dynamic scheduling counters
-    unsigned int block_next;
+    unsigned int n_rows[3];          // hashed rows per intersection class (warp, block, hub)
+    unsigned int task_next[3];       // dynamic scheduling counters per class
+    unsigned long long n_tasks[3];   // tasks per class
     unsigned int error;              // nonzero: a device-side check failed
-    unsigned int max_s2;             // largest hashed row among block-class rows
+    unsigned int max_s2;             // largest hashed row among block-class rows / max degree
     unsigned int pad[5];
 };
 
@@ -150,7 +154,7 @@ struct GraphView {
 tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, const GroupSpec &groups,
                          uint64_t *triangles, tc_stats *stats);
 size_t pipeline_bytes(const tc_ctx *ctx, uint32_t n, uint64_t slots, uint32_t max_deg, bool own_levels,
-                      uint64_t *hub_slots, uint32_t *hub_blocks);
+                      uint64_t *hub_words, uint32_t *hub_maps);
 
 // CSR construction / validation (csr.cu)
 tc_status build_csr_device(tc_ctx *ctx, uint32_t n, uint64_t t, const uint32_t *d_src,

@@ -54,3 +54,31 @@ def test_product_code_never_touches_the_oracle():
 def test_build_entry_point():
     import __graft_entry__
     __graft_entry__.build()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Offsets and sizes of tc_options / tc_tuning / tc_stats as gcc lays them
+    out from include/tc.h equal those of the ctypes mirrors in the binding."""
+    import ctypes
+    import paper_2309_09064_gb300 as tc
+    structs = {"tc_options": tc.tc_options, "tc_tuning": tc.tc_tuning, "tc_stats": tc.tc_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tc.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line.strip():
+            s, f, v = line.split()
+            got[(s, f)] = int(v)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
