@@ -37,6 +37,7 @@ import graphgen as gg  # noqa: E402
 
 WORKLOADS = {
     "rmat24": dict(kind="rmat", scale=24, edge_factor=16, seed=1),
+    "rmat22": dict(kind="rmat", scale=22, edge_factor=16, seed=1),
     "rmat20": dict(kind="rmat", scale=20, edge_factor=16, seed=1),
     "rmat10": dict(kind="rmat", scale=10, edge_factor=16, seed=1),
     "er20": dict(kind="er", n=1 << 20, m=1 << 24, seed=2),

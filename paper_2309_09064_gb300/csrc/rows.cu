@@ -16,6 +16,22 @@
 namespace tc {
 namespace {
 
+// Each lane owns one vertex x; rows of degree <= kSmallRow are handled by
+// their lane alone (sequential, in order), larger rows by the whole warp one
+// at a time (lanes stride over the row, ballots keep the order).
+constexpr uint32_t kSmallRow = 32;
+
+__device__ __forceinline__ bool is_h(uint32_t x, uint32_t dx, uint32_t lx, uint32_t y, const uint32_t *__restrict__ L,
+                                     const uint32_t *__restrict__ deg, uint32_t order, bool *is_g) {
+    const uint32_t ly = L[y];
+    if (ly != lx) {
+        *is_g = true;
+        return false;
+    }
+    *is_g = false;
+    return precedes(x, dx, y, deg[y], order);
+}
+
 __global__ void k_row_count(uint32_t n, const uint64_t *__restrict__ rp, const uint32_t *__restrict__ col,
                             const uint32_t *__restrict__ deg, const uint32_t *__restrict__ L,
                             uint32_t *__restrict__ hcnt, uint32_t *__restrict__ scnt, Ctl *ctl, uint32_t order) {
@@ -23,34 +39,50 @@ __global__ void k_row_count(uint32_t n, const uint64_t *__restrict__ rp, const u
     if (threadIdx.x == 0) s_e0 = 0;
     __syncthreads();
     const unsigned lane = lane_id();
-    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t n_round = ((uint64_t)n + 31) & ~uint64_t(31);
     unsigned long long e0 = 0;
-    for (uint64_t x = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
-        const uint32_t dx = deg[x];
-        if (dx == 0) {
-            if (lane == 0) hcnt[x] = scnt[x] = 0;
-            continue;
-        }
-        const uint32_t lx = L[x];
-        const uint64_t b = rp[x];
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_round; x += stride) {
+        const bool valid = x < n;
+        const uint32_t dx = valid ? deg[x] : 0;
+        const uint32_t lx = valid ? L[x] : 0;
+        const uint64_t b = valid ? rp[x] : 0;
         uint32_t h = 0, g = 0;
-        for (uint32_t j = lane; j < dx; j += 32) {
-            const uint32_t y = col[b + j];
-            const uint32_t ly = L[y];
-            if (ly == lx) {
-                if (precedes((uint32_t)x, dx, y, deg[y], order)) ++h;
-            } else {
-                ++g;
+        if (dx <= kSmallRow) {
+            for (uint32_t j = 0; j < dx; ++j) {
+                bool isg;
+                if (is_h((uint32_t)x, dx, lx, col[b + j], L, deg, order, &isg)) ++h;
+                g += isg;
             }
         }
-        h = warp_sum(h);
-        g = warp_sum(g);
-        if (lane == 0) {
+        unsigned big = __ballot_sync(0xFFFFFFFFu, dx > kSmallRow);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const uint32_t bx = (uint32_t)__shfl_sync(0xFFFFFFFFu, (unsigned long long)x, src);
+            const uint32_t bd = __shfl_sync(0xFFFFFFFFu, dx, src);
+            const uint32_t bl = __shfl_sync(0xFFFFFFFFu, lx, src);
+            const uint64_t bb = __shfl_sync(0xFFFFFFFFu, b, src);
+            uint32_t hh = 0, gg = 0;
+            for (uint32_t j = lane; j < bd; j += 32) {
+                bool isg;
+                if (is_h(bx, bd, bl, col[bb + j], L, deg, order, &isg)) ++hh;
+                gg += isg;
+            }
+            hh = warp_sum(hh);
+            gg = warp_sum(gg);
+            if ((int)lane == src) {
+                h = hh;
+                g = gg;
+            }
+        }
+        if (valid) {
             hcnt[x] = h;
             scnt[x] = h + g;
             e0 += h;
         }
     }
+    e0 = warp_sum(e0);
     if (lane == 0 && e0) atomicAdd(&s_e0, e0);
     __syncthreads();
     if (threadIdx.x == 0 && s_e0) atomicAdd(&ctl->e0, s_e0);
@@ -62,31 +94,50 @@ __global__ void k_row_fill(uint32_t n, const uint64_t *__restrict__ rp, const ui
                            uint32_t *__restrict__ adj2, uint32_t order) {
     const unsigned lane = lane_id();
     const unsigned lt = (1u << lane) - 1u;
-    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t x = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
-        const uint32_t dx = deg[x];
-        if (dx == 0) continue;
-        const uint32_t lx = L[x];
-        const uint64_t b = rp[x];
-        const uint64_t base = off2[x];
-        const uint32_t hx = hcnt[x];
-        uint32_t hp = 0, gp = 0;
-        for (uint32_t j0 = 0; j0 < dx; j0 += 32) {
-            const uint32_t j = j0 + lane;
-            bool isH = false, isG = false;
-            uint32_t y = 0;
-            if (j < dx) {
-                y = col[b + j];
-                const uint32_t ly = L[y];
-                if (ly == lx) isH = precedes((uint32_t)x, dx, y, deg[y], order);
-                else isG = true;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t n_round = ((uint64_t)n + 31) & ~uint64_t(31);
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_round; x += stride) {
+        const bool valid = x < n;
+        const uint32_t dx = valid ? deg[x] : 0;
+        const uint32_t lx = valid ? L[x] : 0;
+        const uint64_t b = valid ? rp[x] : 0;
+        const uint64_t base = valid && dx ? off2[x] : 0;
+        const uint32_t hx = valid && dx ? hcnt[x] : 0;
+        if (dx <= kSmallRow) {
+            uint32_t hp = 0, gp = 0;
+            for (uint32_t j = 0; j < dx; ++j) {
+                const uint32_t y = col[b + j];
+                bool isg;
+                if (is_h((uint32_t)x, dx, lx, y, L, deg, order, &isg)) adj2[base + hp++] = y;
+                else if (isg) adj2[base + hx + gp++] = y;
             }
-            const unsigned mh = __ballot_sync(0xFFFFFFFFu, isH);
-            const unsigned mg = __ballot_sync(0xFFFFFFFFu, isG);
-            if (isH) adj2[base + hp + __popc(mh & lt)] = y;
-            if (isG) adj2[base + hx + gp + __popc(mg & lt)] = y;
-            hp += __popc(mh);
-            gp += __popc(mg);
+        }
+        unsigned big = __ballot_sync(0xFFFFFFFFu, dx > kSmallRow);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const uint32_t bx = (uint32_t)__shfl_sync(0xFFFFFFFFu, (unsigned long long)x, src);
+            const uint32_t bd = __shfl_sync(0xFFFFFFFFu, dx, src);
+            const uint32_t bl = __shfl_sync(0xFFFFFFFFu, lx, src);
+            const uint64_t bb = __shfl_sync(0xFFFFFFFFu, b, src);
+            const uint64_t bbase = __shfl_sync(0xFFFFFFFFu, base, src);
+            const uint32_t bh = __shfl_sync(0xFFFFFFFFu, hx, src);
+            uint32_t hp = 0, gp = 0;
+            for (uint32_t j0 = 0; j0 < bd; j0 += 32) {
+                const uint32_t j = j0 + lane;
+                bool isH = false, isG = false;
+                uint32_t y = 0;
+                if (j < bd) {
+                    y = col[bb + j];
+                    isH = is_h(bx, bd, bl, y, L, deg, order, &isG);
+                }
+                const unsigned mh = __ballot_sync(0xFFFFFFFFu, isH);
+                const unsigned mg = __ballot_sync(0xFFFFFFFFu, isG);
+                if (isH) adj2[bbase + hp + __popc(mh & lt)] = y;
+                if (isG) adj2[bbase + bh + gp + __popc(mg & lt)] = y;
+                hp += __popc(mh);
+                gp += __popc(mg);
+            }
         }
     }
 }
@@ -186,11 +237,9 @@ tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n) {
     const uint32_t order = ctx->opt.order;
     const Tuning &tu = ctx->tune;
     if (n == 0) return TC_OK;
-    k_row_count<<<grid_for((uint64_t)n * 32, 256, cap), 256, 0, s>>>(n, b.rp, b.col, b.deg, b.L, b.hcnt, b.scnt,
-                                                                     ctx->d_ctl, order);
+    k_row_count<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.rp, b.col, b.deg, b.L, b.hcnt, b.scnt, ctx->d_ctl, order);
     uint32_t launches = 1 + scan_u32_to_u64(b.scnt, b.off2, n, b.scan_tmp, s);
-    k_row_fill<<<grid_for((uint64_t)n * 32, 256, cap), 256, 0, s>>>(n, b.rp, b.col, b.deg, b.L, b.hcnt, b.off2,
-                                                                    b.adj2, order);
+    k_row_fill<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.rp, b.col, b.deg, b.L, b.hcnt, b.off2, b.adj2, order);
     k_classify<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.hcnt, b.scnt, b.rows[0], b.rows[1], b.rows[2], ctx->d_ctl,
                                                      tu.warp_cap, tu.block_cap);
     launches += 2;
