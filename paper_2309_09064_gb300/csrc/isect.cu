@@ -19,7 +19,7 @@
 //                                  so that only prefilter-positive probes read
 //                                  the bitmap.
 // Within a task, warps take out-neighbour rows dynamically and walk each row
-// with every lane holding kUnroll independent loads.  A block keeps its table
+// with every lane holding several independent loads.  A block keeps its table
 // (or prefilter) when its next task belongs to the same row.
 #include <algorithm>
 
@@ -28,8 +28,8 @@
 namespace tc {
 namespace {
 
-constexpr int kUnroll = 4;                // row elements in flight per lane
-constexpr uint32_t kStep = 32 * kUnroll;  // row elements per warp step
+constexpr int kUnrollTable = 4;  // row elements in flight per lane, shared-table classes
+constexpr int kUnrollHub = 8;    // row elements in flight per lane, hub class
 constexpr uint32_t kFilterLog2 = 20;      // hub prefilter: 2^20 bits (128 KB)
 
 struct Acc {
@@ -46,15 +46,6 @@ struct Acc {
 struct BucketTable {
     uint4 *bk;
     uint32_t shift, mask;  // home bucket = hash >> shift; mask = buckets - 1
-    __device__ __forceinline__ bool has(uint32_t w) const {
-        uint32_t b = hash_slot(w, shift);
-        for (;;) {
-            const uint4 q = bk[b];
-            if (q.x == w || q.y == w || q.z == w || q.w == w) return true;
-            if (q.w == kEmpty) return false;
-            b = (b + 1) & mask;
-        }
-    }
 };
 
 // Buckets for len keys: at most `cap` buckets, at least len / 2 (load factor
@@ -96,35 +87,83 @@ __device__ __forceinline__ uint32_t filter_bit(uint32_t w) { return (w * 0x85EBC
 struct HubSet {
     const uint32_t *filter;  // shared
     const uint32_t *bits;    // global, read-only while probing
-    __device__ __forceinline__ bool has(uint32_t w) const {
-        const uint32_t f = filter_bit(w);
-        if (!((filter[f >> 5] >> (f & 31)) & 1u)) return false;
-        return (__ldg(bits + (w >> 5)) >> (w & 31)) & 1u;
-    }
 };
 
 // ---------------------------------------------------------------------------- probing one row
 
 // Probe row(v) = adj2[b .. b+len) with one warp; position j < hv is the G0
 // part (a triangle inside G0), the rest the G1 part (a cross-level triangle).
-template <class Set>
-__device__ __forceinline__ void probe_row(const Set &set, const uint32_t *__restrict__ adj2, unsigned long long b,
-                                          uint32_t len, uint32_t hv, Acc &acc) {
+// Each lane first issues all its element loads (kUnrollTable or kUnrollHub), then all first lookups,
+// then resolves them, so independent memory operations overlap.
+__device__ __forceinline__ void count_hit(bool hit, uint32_t j, uint32_t hv, Acc &acc) {
+    if (hit) {
+        if (j < hv) ++acc.same; else ++acc.cross;
+    }
+}
+
+__device__ __forceinline__ void probe_row(const BucketTable &T, const uint32_t *__restrict__ adj2,
+                                          unsigned long long b, uint32_t len, uint32_t hv, Acc &acc) {
     const unsigned lane = lane_id();
     const uint32_t *row = adj2 + b;
-    for (uint32_t j0 = 0; j0 < len; j0 += kStep) {
-        uint32_t w[kUnroll];
+    for (uint32_t j0 = 0; j0 < len; j0 += 32u * kUnrollTable) {
+        uint32_t w[kUnrollTable];
 #pragma unroll
-        for (int i = 0; i < kUnroll; ++i) {
+        for (int i = 0; i < kUnrollTable; ++i) {
             const uint32_t j = j0 + (uint32_t)i * 32u + lane;
             w[i] = j < len ? row[j] : kEmpty;
         }
+        uint4 q[kUnrollTable];
+        uint32_t home[kUnrollTable];
 #pragma unroll
-        for (int i = 0; i < kUnroll; ++i) {
+        for (int i = 0; i < kUnrollTable; ++i) {
+            home[i] = hash_slot(w[i], T.shift);
+            q[i] = T.bk[home[i]];
+        }
+#pragma unroll
+        for (int i = 0; i < kUnrollTable; ++i) {
             const uint32_t j = j0 + (uint32_t)i * 32u + lane;
-            if (w[i] != kEmpty && set.has(w[i])) {
-                if (j < hv) ++acc.same; else ++acc.cross;
+            bool hit = q[i].x == w[i] || q[i].y == w[i] || q[i].z == w[i] || q[i].w == w[i];
+            if (!hit && q[i].w != kEmpty && w[i] != kEmpty) {  // bucket full: continue the probe sequence
+                uint32_t bb = home[i];
+                for (;;) {
+                    bb = (bb + 1) & T.mask;
+                    const uint4 r = T.bk[bb];
+                    if (r.x == w[i] || r.y == w[i] || r.z == w[i] || r.w == w[i]) {
+                        hit = true;
+                        break;
+                    }
+                    if (r.w == kEmpty) break;
+                }
             }
+            count_hit(hit && w[i] != kEmpty, j, hv, acc);
+        }
+    }
+}
+
+__device__ __forceinline__ void probe_row(const HubSet &H, const uint32_t *__restrict__ adj2, unsigned long long b,
+                                          uint32_t len, uint32_t hv, Acc &acc) {
+    const unsigned lane = lane_id();
+    const uint32_t *row = adj2 + b;
+    for (uint32_t j0 = 0; j0 < len; j0 += 32u * kUnrollHub) {
+        uint32_t w[kUnrollHub];
+#pragma unroll
+        for (int i = 0; i < kUnrollHub; ++i) {
+            const uint32_t j = j0 + (uint32_t)i * 32u + lane;
+            w[i] = j < len ? row[j] : kEmpty;
+        }
+        bool pos[kUnrollHub];
+#pragma unroll
+        for (int i = 0; i < kUnrollHub; ++i) {
+            const uint32_t f = filter_bit(w[i]);
+            pos[i] = w[i] != kEmpty && ((H.filter[f >> 5] >> (f & 31)) & 1u);
+        }
+        uint32_t word[kUnrollHub];
+#pragma unroll
+        for (int i = 0; i < kUnrollHub; ++i) word[i] = pos[i] ? __ldg(H.bits + (w[i] >> 5)) : 0u;
+#pragma unroll
+        for (int i = 0; i < kUnrollHub; ++i) {
+            const uint32_t j = j0 + (uint32_t)i * 32u + lane;
+            count_hit(pos[i] && ((word[i] >> (w[i] & 31)) & 1u), j, hv, acc);
         }
     }
 }
@@ -271,15 +310,23 @@ struct TaskSmem {
     unsigned int next;
     unsigned int pad;
     unsigned long long found;
+    unsigned long long chunk_pos, chunk_end;  // this block's current run of consecutive tasks
 };
 
-// Thread 0 takes the next task index of class c in [first, last); all threads see it.
+// Thread 0 takes the next task of class c in [first, last): blocks grab runs
+// of `chunk` consecutive tasks, so the tasks of one row mostly stay on one
+// block and its table is built once.  All threads see the task.
 __device__ __forceinline__ bool next_task(Ctl *ctl, int c, unsigned long long first, unsigned long long last,
-                                          const uint2 *tasks, TaskSmem *ts) {
+                                          unsigned long long chunk, const uint2 *tasks, TaskSmem *ts) {
     __syncthreads();  // everyone is done with the previous task
     if (threadIdx.x == 0) {
-        const unsigned long long k = first + atomicAdd(&ctl->task_next[c], 1u);
-        ts->task = k < last ? tasks[k] : make_uint2(0xFFFFFFFFu, 0u);
+        if (ts->chunk_pos >= ts->chunk_end) {
+            const unsigned long long k = first + (unsigned long long)atomicAdd(&ctl->task_next[c], 1u) * chunk;
+            ts->chunk_pos = k;
+            ts->chunk_end = k + chunk < last ? k + chunk : last;
+        }
+        const unsigned long long k = ts->chunk_pos++;
+        ts->task = k < ts->chunk_end ? tasks[k] : make_uint2(0xFFFFFFFFu, 0u);
         ts->next = 0;
         ts->found = 0;
     }
@@ -287,12 +334,20 @@ __device__ __forceinline__ bool next_task(Ctl *ctl, int c, unsigned long long fi
     return ts->task.x != 0xFFFFFFFFu;
 }
 
+__device__ __forceinline__ void init_task_smem(TaskSmem *ts) {
+    if (threadIdx.x == 0) {
+        ts->chunk_pos = 0;
+        ts->chunk_end = 0;
+    }
+}
+
 __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict__ tasks, const uint32_t *__restrict__ rows,
                                                       const uint32_t *__restrict__ ntask,
                                                       const uint64_t *__restrict__ off2,
                                                       const uint32_t *__restrict__ adj2,
                                                       const uint32_t *__restrict__ hcnt, Ctl *ctl, uint32_t max_v,
-                                                      uint32_t table_buckets, GroupSpec groups) {
+                                                      uint32_t table_buckets, unsigned long long chunk,
+                                                      GroupSpec groups) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TaskSmem ts;
     const unsigned lane = lane_id();
@@ -303,7 +358,8 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
     unsigned long long build = 0, done = 0;
     uint32_t cur_row = 0xFFFFFFFFu;
     BucketTable T{bk, 0, 0};
-    while (next_task(ctl, 1, 0, ntasks, tasks, &ts)) {
+    init_task_smem(&ts);
+    while (next_task(ctl, 1, 0, ntasks, chunk, tasks, &ts)) {
         const uint2 task = ts.task;
         const uint32_t u = rows[task.x], nt = ntask[task.x];
         const uint64_t ub = off2[u];
@@ -358,7 +414,8 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
                                                     const uint32_t *__restrict__ ntask, uint32_t i0,
                                                     const uint64_t *__restrict__ off2, const uint32_t *__restrict__ adj2,
                                                     const uint32_t *__restrict__ hcnt, Ctl *ctl, const uint32_t *bits,
-                                                    uint64_t words, uint32_t max_v, GroupSpec groups) {
+                                                    uint64_t words, uint32_t max_v, unsigned long long chunk,
+                                                    GroupSpec groups) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TaskSmem ts;
     const unsigned lane = lane_id();
@@ -368,7 +425,8 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
     Acc acc;
     unsigned long long build = 0, done = 0;
     uint32_t cur_row = 0xFFFFFFFFu;
-    while (next_task(ctl, 2, first, last, tasks, &ts)) {
+    init_task_smem(&ts);
+    while (next_task(ctl, 2, first, last, chunk, tasks, &ts)) {
         const uint2 task = ts.task;
         const uint32_t u = rows[task.x], nt = ntask[task.x];
         const uint64_t ub = off2[u];
@@ -449,9 +507,10 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         if (per_sm < 1) per_sm = 1;
         uint64_t grid = (uint64_t)ctx->num_sms * per_sm;
         if (grid > h.n_tasks[1]) grid = h.n_tasks[1];
+        const unsigned long long chunk = std::max<unsigned long long>(1, h.n_tasks[1] / (grid * 8));
         k_isect_block<<<(unsigned)grid, tu.block_threads, smem, s>>>(b.tasks[1], b.rows[1], b.ntask[1], b.off2, b.adj2,
                                                                      b.hcnt, ctx->d_ctl, tu.max_v,
-                                                                     block_table_buckets(tu), b.groups);
+                                                                     block_table_buckets(tu), chunk, b.groups);
         note_launch(ctx);
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[6], s));
@@ -475,9 +534,10 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
             const unsigned long long first = pref[i0], last = pref[i0 + g];
             uint64_t grid = (uint64_t)ctx->num_sms * per_sm;
             if (grid > last - first) grid = last - first;
+            const unsigned long long chunk = std::max<unsigned long long>(1, (last - first) / (grid * 4));
             k_isect_hub<<<(unsigned)grid, tu.hub_threads, smem, s>>>(b.tasks[2], first, last, b.rows[2], b.ntask[2], i0,
                                                                      b.off2, b.adj2, b.hcnt, ctx->d_ctl, b.hub_bits,
-                                                                     b.hub_words, tu.max_v, b.groups);
+                                                                     b.hub_words, tu.max_v, chunk, b.groups);
             note_launch(ctx, 2);
         }
     }
