@@ -196,6 +196,30 @@ tc_status tc_count_levels(tc_ctx *ctx, const tc_graph *g, uint32_t *d_levels, ui
  */
 tc_status tc_count_batch(tc_ctx *ctx, uint32_t G, const tc_graph *const *graphs, uint64_t *counts);
 
+/*
+ * Exact count of one small graph that allocates nothing (no counterpart in
+ * the paper; an interface for callers that cannot allocate device memory when
+ * they count, e.g. code running inside another allocator or a process whose
+ * memory pool already owns the whole device).  Same method and same results
+ * as tc_count, run by one thread block with all scratch in a fixed array of
+ * device memory declared in the library (about 5.8 MB, held by every GPU
+ * that loads the library until exit).
+ *   d_row_ptr, d_col: device CSR (well formed, as for TC_BORROW), n <= 65536
+ *     vertices, slots = row_ptr[n] <= 1048576 (TC_ERR_INVALID beyond that);
+ *   order: TC_ORDER_DEGREE or TC_ORDER_ID;
+ *   d_out: device uint64_t[4], written when the stream reaches the kernel:
+ *     [0] = T, [1] = triangles inside G0, [2] = cross-level triangles,
+ *     [3] = 0 (1 if the device saw row_ptr[n] beyond the limit; nothing else
+ *     is then written);
+ *   stream: cudaStream_t (NULL: the legacy default stream).
+ * Asynchronous: returns after the launch.  Every call shares the one array, so
+ * calls that overlap on the GPU (other streams or threads) race; serialise
+ * them.  The first call on a device looks up the array's device address; make
+ * it before any stream capture.
+ */
+tc_status tc_count_noalloc(const uint64_t *d_row_ptr, const uint32_t *d_col, uint32_t n, uint64_t slots,
+                           uint32_t order, uint64_t *d_out, void *stream);
+
 /* ------------------------------------------------------------------ serving */
 
 /*

@@ -21,7 +21,7 @@ __all__ = [
     "TC_ORDER_DEGREE", "TC_ORDER_ID", "tc_create", "tc_destroy", "tc_last_error", "tc_set_stream",
     "tc_arena_bytes", "tc_build_csr", "tc_graph_from_csr", "tc_graph_info", "tc_graph_copy_out",
     "tc_validate", "tc_graph_free", "tc_count", "tc_count_levels", "tc_count_batch", "tc_submit", "tc_poll",
-    "tc_get_tuning", "tc_set_tuning", "library_path", "EXPORTED",
+    "tc_get_tuning", "tc_set_tuning", "tc_count_noalloc", "library_path", "EXPORTED",
 ]
 
 TC_OK, TC_ERR_INVALID, TC_ERR_OOM, TC_ERR_CUDA, TC_ERR_TIMEOUT, TC_ERR_BUSY, TC_NOT_READY = range(7)
@@ -35,7 +35,7 @@ _STATUS = {0: "TC_OK", 1: "TC_ERR_INVALID", 2: "TC_ERR_OOM", 3: "TC_ERR_CUDA", 4
 EXPORTED = ["tc_create", "tc_destroy", "tc_last_error", "tc_set_stream", "tc_get_tuning", "tc_set_tuning",
             "tc_arena_bytes", "tc_build_csr",
             "tc_graph_from_csr", "tc_graph_info", "tc_graph_copy_out", "tc_validate", "tc_graph_free",
-            "tc_count", "tc_count_levels", "tc_count_batch", "tc_submit", "tc_poll"]
+            "tc_count", "tc_count_levels", "tc_count_batch", "tc_submit", "tc_poll", "tc_count_noalloc"]
 
 
 class TcError(RuntimeError):
@@ -103,6 +103,7 @@ def _load():
         "tc_count_batch": ([V, U32, P(V), P(U64)], I),
         "tc_submit": ([V, V, P(U64)], I),
         "tc_poll": ([V, U64, P(U64)], I),
+        "tc_count_noalloc": ([V, V, U32, U64, U32, V, V], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -276,6 +277,22 @@ def tc_count_batch(ctx, graphs):
     out = np.zeros(max(G, 1), dtype=np.uint64)
     _check(ctx, _lib.tc_count_batch(ctx, G, arr, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
     return out[:G]
+
+
+def tc_count_noalloc(row_ptr, col, n: int, slots: int, out, order: int = TC_ORDER_DEGREE, stream=None):
+    """Count a small device CSR without any allocation by the library.
+
+    For callers that cannot allocate device memory at the point of the count.
+    row_ptr / col / out are device buffers (CUDA tensors or addresses); out
+    receives [T, T inside G0, T cross-level, limit flag] as uint64 when the
+    stream reaches the kernel.  Asynchronous; raises TcError on bad sizes.
+    """
+    pr, wr = _ptr(row_ptr)
+    pc, wc = _ptr(col)
+    po, wo = _ptr(out)
+    if TC_HOST in (wr, wc, wo):
+        raise ValueError("tc_count_noalloc takes device buffers only")
+    _check(None, _lib.tc_count_noalloc(pr, pc, n, slots, order, po, _stream_handle(stream)))
 
 
 def tc_submit(ctx, g) -> int:
