@@ -91,7 +91,8 @@ struct HubSet {
 
 // ---------------------------------------------------------------------------- probing one row
 
-// Probe row(v) = adj2[b .. b+len) with one warp; position j < hv is the G0
+// Probe positions [j_lo, len) of row(v) = adj2[b .. b+len) with one warp;
+// position j < hv is the G0
 // part (a triangle inside G0), the rest the G1 part (a cross-level triangle).
 // Each lane first issues all its element loads (kUnrollTable or kUnrollHub), then all first lookups,
 // then resolves them, so independent memory operations overlap.
@@ -102,10 +103,10 @@ __device__ __forceinline__ void count_hit(bool hit, uint32_t j, uint32_t hv, Acc
 }
 
 __device__ __forceinline__ void probe_row(const BucketTable &T, const uint32_t *__restrict__ adj2,
-                                          unsigned long long b, uint32_t len, uint32_t hv, Acc &acc) {
+                                          unsigned long long b, uint32_t j_lo, uint32_t len, uint32_t hv, Acc &acc) {
     const unsigned lane = lane_id();
     const uint32_t *row = adj2 + b;
-    for (uint32_t j0 = 0; j0 < len; j0 += 32u * kUnrollTable) {
+    for (uint32_t j0 = j_lo; j0 < len; j0 += 32u * kUnrollTable) {
         uint32_t w[kUnrollTable];
 #pragma unroll
         for (int i = 0; i < kUnrollTable; ++i) {
@@ -141,10 +142,10 @@ __device__ __forceinline__ void probe_row(const BucketTable &T, const uint32_t *
 }
 
 __device__ __forceinline__ void probe_row(const HubSet &H, const uint32_t *__restrict__ adj2, unsigned long long b,
-                                          uint32_t len, uint32_t hv, Acc &acc) {
+                                          uint32_t j_lo, uint32_t len, uint32_t hv, Acc &acc) {
     const unsigned lane = lane_id();
     const uint32_t *row = adj2 + b;
-    for (uint32_t j0 = 0; j0 < len; j0 += 32u * kUnrollHub) {
+    for (uint32_t j0 = j_lo; j0 < len; j0 += 32u * kUnrollHub) {
         uint32_t w[kUnrollHub];
 #pragma unroll
         for (int i = 0; i < kUnrollHub; ++i) {
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(1024) k_isect_warp(const uint2 *__restrict__ t
                 const unsigned long long bt = __shfl_sync(0xFFFFFFFFu, b, t);
                 const uint32_t lt = __shfl_sync(0xFFFFFFFFu, len, t);
                 const uint32_t ht = __shfl_sync(0xFFFFFFFFu, hv, t);
-                probe_row(T, adj2, bt, lt, ht, acc);
+                probe_row(T, adj2, bt, 0, lt, ht, acc);
             }
         }
         if (groups.n_groups) {
@@ -260,10 +261,15 @@ __global__ void __launch_bounds__(1024) k_isect_warp(const uint2 *__restrict__ t
 
 // ---------------------------------------------------------------------------- block and hub classes
 
-// Per-task shared metadata of up to max_v out-neighbour rows.
+// Per-task shared metadata of up to max_v out-neighbour rows.  Rows are cut
+// into segments of kSeg positions; seg[i] is the exclusive prefix of segment
+// counts, so warps can take segments one at a time and no long row holds up
+// the block.
+constexpr uint32_t kSeg = 512;
+
 struct SliceSmem {
     unsigned long long *b;
-    uint32_t *len, *h;
+    uint32_t *len, *h, *seg;
 };
 
 __device__ __forceinline__ SliceSmem carve_slice(unsigned char *p, uint32_t max_v) {
@@ -271,10 +277,50 @@ __device__ __forceinline__ SliceSmem carve_slice(unsigned char *p, uint32_t max_
     s.b = reinterpret_cast<unsigned long long *>(p);
     s.len = reinterpret_cast<uint32_t *>(p + 8ull * max_v);
     s.h = s.len + max_v;
+    s.seg = s.h + max_v;
     return s;
 }
 
-__host__ __device__ constexpr size_t slice_smem_bytes(uint32_t max_v) { return (16ull * max_v + 15) & ~15ull; }
+__host__ __device__ constexpr size_t slice_smem_bytes(uint32_t max_v) { return (20ull * max_v + 4 + 15) & ~15ull; }
+
+// Block-wide exclusive scan of the segment counts of rows 0..nv-1 into
+// seg[0..nv]; all threads of the block call it; ends with a barrier.
+__device__ __forceinline__ void scan_segments(const uint32_t *len, uint32_t *seg, uint32_t nv) {
+    __shared__ uint32_t warp_tot[32];
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const uint32_t per = (nv + blockDim.x - 1) / blockDim.x;  // rows per thread (contiguous)
+    const uint32_t beg = threadIdx.x * per;
+    uint32_t sum = 0;
+    for (uint32_t i = 0; i < per; ++i)
+        if (beg + i < nv) sum += (len[beg + i] + kSeg - 1) / kSeg;
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= (unsigned)o) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t t = lane < nwarps ? warp_tot[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+            if (lane >= (unsigned)o) t += y;
+        }
+        warp_tot[lane] = t;
+    }
+    __syncthreads();
+    uint32_t run = (warp ? warp_tot[warp - 1] : 0u) + x - sum;
+    for (uint32_t i = 0; i < per; ++i) {
+        if (beg + i < nv) {
+            seg[beg + i] = run;
+            run += (len[beg + i] + kSeg - 1) / kSeg;
+        }
+    }
+    if (threadIdx.x == 0) seg[nv] = warp_tot[nwarps - 1];
+    __syncthreads();
+}
 
 // Load the metadata of v = hrow[k], k in [k_lo, k_hi) (no barrier).
 __device__ __forceinline__ void load_slice(const SliceSmem &S, const uint32_t *__restrict__ hrow, uint32_t k_lo,
@@ -289,19 +335,27 @@ __device__ __forceinline__ void load_slice(const SliceSmem &S, const uint32_t *_
     }
 }
 
-// Warps take rows of the slice one at a time (shared counter) and probe them.
+// Warps take row segments of the slice one at a time (shared counter).
 template <class Set>
 __device__ __forceinline__ void probe_slice(const Set &set, const SliceSmem &S, uint32_t nv,
                                             const uint32_t *__restrict__ adj2, unsigned int *next, Acc &acc) {
     const unsigned lane = lane_id();
+    const uint32_t total = S.seg[nv];
     for (;;) {
-        uint32_t i = 0;
-        if (lane == 0) i = atomicAdd(next, 1u);
-        i = __shfl_sync(0xFFFFFFFFu, i, 0);
-        if (i >= nv) break;
-        const uint32_t len = S.len[i];
-        if (lane == 0) acc.probes += len;
-        probe_row(set, adj2, S.b[i], len, S.h[i], acc);
+        uint32_t g = 0;
+        if (lane == 0) g = atomicAdd(next, 1u);
+        g = __shfl_sync(0xFFFFFFFFu, g, 0);
+        if (g >= total) break;
+        uint32_t a = 0, e = nv;  // row of segment g: largest t with seg[t] <= g
+        while (e - a > 1) {
+            const uint32_t m = (a + e) >> 1;
+            if (S.seg[m] <= g) a = m; else e = m;
+        }
+        const uint32_t len = S.len[a];
+        const uint32_t j_lo = (g - S.seg[a]) * kSeg;
+        const uint32_t j_hi = min(len, j_lo + kSeg);
+        if (lane == 0) acc.probes += j_hi - j_lo;
+        probe_row(set, adj2, S.b[a], j_lo, j_hi, S.h[a], acc);
     }
 }
 
@@ -370,6 +424,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
         if (rebuild) T = clear_table(bk, su, table_buckets, threadIdx.x, blockDim.x);
         load_slice(S, adj2 + ub, k_lo, k_hi, off2, hcnt);
         __syncthreads();
+        scan_segments(S.len, S.seg, k_hi - k_lo);
         if (rebuild) {
             fill_table(T, adj2 + ub, su, threadIdx.x, blockDim.x);
             __syncthreads();
@@ -438,6 +493,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
             for (uint32_t j = threadIdx.x; j < kFilterWords; j += blockDim.x) filter[j] = 0u;
         load_slice(S, adj2 + ub, k_lo, k_hi, off2, hcnt);
         __syncthreads();
+        scan_segments(S.len, S.seg, k_hi - k_lo);
         if (rebuild) {
             for (uint32_t j = threadIdx.x; j < su; j += blockDim.x) {
                 const uint32_t f = filter_bit(adj2[ub + j]);
