@@ -28,7 +28,7 @@
 namespace tc {
 namespace {
 
-constexpr int kUnrollTable = 4;  // row elements in flight per lane, shared-table classes
+constexpr int kUnrollTable = 8;  // row elements in flight per lane, shared-table classes
 constexpr int kUnrollHub = 8;    // row elements in flight per lane, hub class
 constexpr uint32_t kFilterLog2 = 20;      // hub prefilter: 2^20 bits (128 KB)
 
@@ -96,9 +96,47 @@ struct HubSet {
 // part (a triangle inside G0), the rest the G1 part (a cross-level triangle).
 // Each lane first issues all its element loads (kUnrollTable or kUnrollHub), then all first lookups,
 // then resolves them, so independent memory operations overlap.
-__device__ __forceinline__ void count_hit(bool hit, uint32_t j, uint32_t hv, Acc &acc) {
-    if (hit) {
-        if (j < hv) ++acc.same; else ++acc.cross;
+// Per-row-step hit counters stay 32-bit in registers; probe_row adds them to
+// the 64-bit accumulators once per call.
+struct Hits {
+    uint32_t all = 0, same = 0;
+    __device__ __forceinline__ void add(bool hit, uint32_t j, uint32_t hv) {
+        all += hit;
+        same += hit && j < hv;
+    }
+    __device__ __forceinline__ void flush(Acc &acc) const {
+        acc.same += same;
+        acc.cross += all - same;
+    }
+};
+
+// Probe one element batch against the bucket table: first buckets for all,
+// then the rare continuation for lanes whose home bucket was full.
+template <int N>
+__device__ __forceinline__ void lookup_batch(const BucketTable &T, const uint32_t (&w)[N], bool (&hit)[N]) {
+    uint4 q[N];
+    uint32_t home[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        home[i] = hash_slot(w[i], T.shift);
+        q[i] = T.bk[home[i]];
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        hit[i] = q[i].x == w[i] || q[i].y == w[i] || q[i].z == w[i] || q[i].w == w[i];
+        if (!hit[i] && q[i].w != kEmpty && w[i] != kEmpty) {  // bucket full: continue the probe sequence
+            uint32_t bb = home[i];
+            for (;;) {
+                bb = (bb + 1) & T.mask;
+                const uint4 r = T.bk[bb];
+                if (r.x == w[i] || r.y == w[i] || r.z == w[i] || r.w == w[i]) {
+                    hit[i] = true;
+                    break;
+                }
+                if (r.w == kEmpty) break;
+            }
+        }
+        hit[i] = hit[i] && w[i] != kEmpty;
     }
 }
 
@@ -106,6 +144,7 @@ __device__ __forceinline__ void probe_row(const BucketTable &T, const uint32_t *
                                           unsigned long long b, uint32_t j_lo, uint32_t len, uint32_t hv, Acc &acc) {
     const unsigned lane = lane_id();
     const uint32_t *row = adj2 + b;
+    Hits hits;
     for (uint32_t j0 = j_lo; j0 < len; j0 += 32u * kUnrollTable) {
         uint32_t w[kUnrollTable];
 #pragma unroll
@@ -113,38 +152,26 @@ __device__ __forceinline__ void probe_row(const BucketTable &T, const uint32_t *
             const uint32_t j = j0 + (uint32_t)i * 32u + lane;
             w[i] = j < len ? row[j] : kEmpty;
         }
-        uint4 q[kUnrollTable];
-        uint32_t home[kUnrollTable];
 #pragma unroll
-        for (int i = 0; i < kUnrollTable; ++i) {
-            home[i] = hash_slot(w[i], T.shift);
-            q[i] = T.bk[home[i]];
-        }
+        for (int half = 0; half < kUnrollTable; half += kUnrollTable / 2) {
+            uint32_t ww[kUnrollTable / 2];
+            bool hit[kUnrollTable / 2];
 #pragma unroll
-        for (int i = 0; i < kUnrollTable; ++i) {
-            const uint32_t j = j0 + (uint32_t)i * 32u + lane;
-            bool hit = q[i].x == w[i] || q[i].y == w[i] || q[i].z == w[i] || q[i].w == w[i];
-            if (!hit && q[i].w != kEmpty && w[i] != kEmpty) {  // bucket full: continue the probe sequence
-                uint32_t bb = home[i];
-                for (;;) {
-                    bb = (bb + 1) & T.mask;
-                    const uint4 r = T.bk[bb];
-                    if (r.x == w[i] || r.y == w[i] || r.z == w[i] || r.w == w[i]) {
-                        hit = true;
-                        break;
-                    }
-                    if (r.w == kEmpty) break;
-                }
-            }
-            count_hit(hit && w[i] != kEmpty, j, hv, acc);
+            for (int i = 0; i < kUnrollTable / 2; ++i) ww[i] = w[half + i];
+            lookup_batch(T, ww, hit);
+#pragma unroll
+            for (int i = 0; i < kUnrollTable / 2; ++i)
+                hits.add(hit[i], j0 + (uint32_t)(half + i) * 32u + lane, hv);
         }
     }
+    hits.flush(acc);
 }
 
 __device__ __forceinline__ void probe_row(const HubSet &H, const uint32_t *__restrict__ adj2, unsigned long long b,
                                           uint32_t j_lo, uint32_t len, uint32_t hv, Acc &acc) {
     const unsigned lane = lane_id();
     const uint32_t *row = adj2 + b;
+    Hits hits;
     for (uint32_t j0 = j_lo; j0 < len; j0 += 32u * kUnrollHub) {
         uint32_t w[kUnrollHub];
 #pragma unroll
@@ -162,11 +189,10 @@ __device__ __forceinline__ void probe_row(const HubSet &H, const uint32_t *__res
 #pragma unroll
         for (int i = 0; i < kUnrollHub; ++i) word[i] = pos[i] ? __ldg(H.bits + (w[i] >> 5)) : 0u;
 #pragma unroll
-        for (int i = 0; i < kUnrollHub; ++i) {
-            const uint32_t j = j0 + (uint32_t)i * 32u + lane;
-            count_hit(pos[i] && ((word[i] >> (w[i] & 31)) & 1u), j, hv, acc);
-        }
+        for (int i = 0; i < kUnrollHub; ++i)
+            hits.add(pos[i] && ((word[i] >> (w[i] & 31)) & 1u), j0 + (uint32_t)i * 32u + lane, hv);
     }
+    hits.flush(acc);
 }
 
 __device__ __forceinline__ uint32_t group_of(const GroupSpec &g, uint32_t u) {

@@ -12,6 +12,8 @@
 //      multi-source BFS from those roots levels them.
 // BFS distances are unique given the roots, so L matches the serial
 // algorithm exactly whatever the thread schedule.
+#include <algorithm>
+
 #include "pipeline.cuh"
 
 namespace tc {
@@ -293,12 +295,114 @@ __global__ void k_after_level(Ctl *ctl, int nxt, uint32_t level) {
     if (ctl->fr_count[nxt]) ctl->max_level = level + 1 > ctl->max_level ? level + 1 : ctl->max_level;
 }
 
+// Grid-wide barrier for the persistent BFS (all blocks are co-resident: the
+// kernel is launched cooperatively).  Sense by generation counter; the wait
+// gives up after ~2 s of clock time, raises the error flag and returns false.
+__device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned nblocks) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = &ctl->bar_gen;
+        const unsigned g = *gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(&ctl->bar_count, 1u) == nblocks - 1) {
+            ctl->bar_count = 0;
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g) {
+                if (clock64() - t0 > 4000000000ll) {  // ~2 s at 2 GHz
+                    ctl->error = 4;
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Persistent top-down BFS for small frontiers (high-diameter graphs): one
+// launch runs level after level, warp per frontier vertex, one grid barrier
+// per level, until the frontier is empty or exceeds (max_f, max_e); then the
+// host takes over again.  Counter slots rotate mod 3 (level L reads slot s,
+// writes s+1, and s+2 is cleared for level L+1); queues alternate.
+__global__ void __launch_bounds__(512) k_bfs_persist(uint32_t *__restrict__ q0, uint32_t *__restrict__ q1,
+                                                     const uint64_t *__restrict__ rp,
+                                                     const uint32_t *__restrict__ col,
+                                                     const uint32_t *__restrict__ deg, uint32_t *L, Ctl *ctl,
+                                                     uint32_t slot, uint32_t queue, uint32_t level, uint32_t max_f,
+                                                     unsigned long long max_e) {
+    const unsigned lane = lane_id();
+    const unsigned gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+    volatile unsigned *vcount = ctl->fr_count;
+    volatile unsigned long long *vedges = ctl->fr_edges;
+    for (;;) {
+        const uint32_t fcount = vcount[slot];
+        const unsigned long long fedges = vedges[slot];
+        if (fcount == 0 || fcount > max_f || fedges > max_e) break;
+        const uint32_t s1 = slot == 2 ? 0 : slot + 1, s2 = s1 == 2 ? 0 : s1 + 1;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ctl->fr_count[s2] = 0;
+            ctl->fr_edges[s2] = 0;
+        }
+        const uint32_t *q = queue ? q1 : q0;
+        uint32_t *qn = queue ? q0 : q1;
+        unsigned long long edges = 0;
+        for (uint32_t i = gwarp; i < fcount; i += nwarps) {
+            const uint32_t v = q[i];
+            const uint64_t b = rp[v], e = rp[v + 1];
+            for (uint64_t j0 = b; j0 < e; j0 += 32) {
+                const uint64_t j = j0 + lane;
+                bool claim = false;
+                uint32_t w = 0;
+                if (j < e) {
+                    w = col[j];
+                    claim = L[w] == kUnvisited && atomicCAS(&L[w], kUnvisited, level + 1) == kUnvisited;
+                }
+                const uint32_t pos = warp_append(claim, &ctl->fr_count[s1]);
+                if (claim) {
+                    qn[pos] = w;
+                    edges += deg[w];
+                }
+            }
+        }
+        edges = warp_sum(edges);
+        if (lane == 0 && edges) atomicAdd(&ctl->fr_edges[s1], edges);
+        if (!grid_barrier(ctl, gridDim.x)) return;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const uint32_t c = vcount[s1];
+            ctl->visited += c;
+            ctl->visited_edges += vedges[s1];
+            if (c) ctl->max_level = level + 1 > ctl->max_level ? level + 1 : ctl->max_level;
+        }
+        slot = s1;
+        queue ^= 1u;
+        ++level;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->p_slot = slot;
+        ctl->p_queue = queue;
+        ctl->p_level = level;
+    }
+}
+
 unsigned grid_for(uint64_t work, unsigned threads, unsigned cap) {
     uint64_t b = (work + threads - 1) / threads;
     if (b < 1) b = 1;
     if (b > cap) b = cap;
     return (unsigned)b;
 }
+
+constexpr uint32_t kPersistMaxF = 32768;          // frontier vertices
+constexpr unsigned long long kPersistMaxE = 65536;  // frontier edges
 
 }  // namespace
 
@@ -309,51 +413,81 @@ static tc_status pull_ctl(tc_ctx *ctx) {
     return TC_OK;
 }
 
-// Level-synchronous BFS from the frontier in q[cur] (already levelled 0 ..
-// start_level).  Chooses top-down or bottom-up per level (Beamer et al.'s
-// edge/vertex heuristics).
+// Level-synchronous BFS from the frontier in queue `queue`, counter slot
+// `slot` (levels 0 .. start_level already assigned).  Per level the host
+// chooses top-down (edge-balanced) or bottom-up (Beamer et al.'s edge/vertex
+// heuristics); runs of small frontiers go to the persistent kernel.
 static tc_status bfs_loop(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t slots, uint32_t start_level,
-                          int *cur_io) {
+                          uint32_t slot, uint32_t queue) {
     cudaStream_t s = ctx->stream;
     const unsigned cap = (unsigned)ctx->num_sms * 16u;
-    int cur = *cur_io;
     uint32_t level = start_level;
     bool bottom_up = false;
     tc_status st = pull_ctl(ctx);
     if (st != TC_OK) return st;
-    uint32_t fcount = ctx->h_ctl->fr_count[cur];
-    unsigned long long fedges = ctx->h_ctl->fr_edges[cur];
+    uint32_t fcount = ctx->h_ctl->fr_count[slot];
+    unsigned long long fedges = ctx->h_ctl->fr_edges[slot];
     uint32_t prev_count = 0;
+    int persist_blocks = -1;
     while (fcount > 0) {
         const unsigned long long unexplored = slots - ctx->h_ctl->visited_edges;
         if (!bottom_up && fedges > unexplored / 14 && fcount > 64) bottom_up = true;
         else if (bottom_up && fcount < n / 24 && fcount < prev_count) bottom_up = false;
-        const int nxt = cur ^ 1;
-        uint32_t *q = cur ? b.q1 : b.q0;
-        uint32_t *qn = cur ? b.q0 : b.q1;
-        k_reset_next<<<1, 1, 0, s>>>(ctx->d_ctl, nxt);
+        const uint32_t nxt = slot == 2 ? 0 : slot + 1;
+        if (!bottom_up && fcount <= kPersistMaxF && fedges <= kPersistMaxE) {
+            if (persist_blocks < 0) {
+                int per_sm = 0;
+                TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs_persist, 512, 0));
+                persist_blocks = std::max(1, std::min(per_sm, 2)) * ctx->num_sms;
+            }
+            k_reset_next<<<1, 1, 0, s>>>(ctx->d_ctl, (int)nxt);
+            uint32_t *q0 = b.q0, *q1 = b.q1;
+            const uint64_t *rp = b.rp;
+            const uint32_t *col = b.col, *deg = b.deg;
+            uint32_t *L = b.L;
+            Ctl *ctl = ctx->d_ctl;
+            uint32_t a_slot = slot, a_queue = queue, a_level = level, a_max_f = kPersistMaxF;
+            unsigned long long a_max_e = kPersistMaxE;
+            void *args[] = {&q0, &q1, &rp, &col, &deg, &L, &ctl, &a_slot, &a_queue, &a_level, &a_max_f, &a_max_e};
+            TC_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_bfs_persist, dim3(persist_blocks), dim3(512), args,
+                                                     0, s));
+            note_launch(ctx, 2);
+            st = pull_ctl(ctx);
+            if (st != TC_OK) return st;
+            if (ctx->h_ctl->error == 4) return set_error(ctx, TC_ERR_TIMEOUT, "persistent BFS barrier timed out");
+            slot = ctx->h_ctl->p_slot;
+            queue = ctx->h_ctl->p_queue;
+            level = ctx->h_ctl->p_level;
+            prev_count = fcount;
+            fcount = ctx->h_ctl->fr_count[slot];
+            fedges = ctx->h_ctl->fr_edges[slot];
+            continue;  // the frontier is empty or too large for the persistent kernel
+        }
+        uint32_t *q = queue ? b.q1 : b.q0;
+        uint32_t *qn = queue ? b.q0 : b.q1;
+        k_reset_next<<<1, 1, 0, s>>>(ctx->d_ctl, (int)nxt);
         note_launch(ctx, 2);  // reset + after-level bookkeeping
         if (bottom_up) {
-            k_bu<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.rp, b.col, b.deg, b.L, qn, ctx->d_ctl, level, nxt);
+            k_bu<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.rp, b.col, b.deg, b.L, qn, ctx->d_ctl, level, (int)nxt);
             note_launch(ctx);
         } else if (fedges > 0) {
             k_gather_deg<<<grid_for(fcount, 256, cap), 256, 0, s>>>(q, fcount, b.deg, b.fdeg);
             note_launch(ctx, 2 + scan_u32_to_u64(b.fdeg, b.fpref, fcount, b.scan_tmp, s));
             k_td<<<grid_for((fedges + kTdTile - 1) / kTdTile, 1, cap), kTdThreads, 0, s>>>(
                 q, fcount, reinterpret_cast<const unsigned long long *>(b.fpref), b.rp, b.col, b.deg, b.L, qn,
-                ctx->d_ctl, level, nxt);
+                ctx->d_ctl, level, (int)nxt);
         }
-        k_after_level<<<1, 1, 0, s>>>(ctx->d_ctl, nxt, level);
+        k_after_level<<<1, 1, 0, s>>>(ctx->d_ctl, (int)nxt, level);
         TC_CUDA(ctx, cudaGetLastError());
         st = pull_ctl(ctx);
         if (st != TC_OK) return st;
         prev_count = fcount;
         fcount = ctx->h_ctl->fr_count[nxt];
         fedges = ctx->h_ctl->fr_edges[nxt];
-        cur = nxt;
+        slot = nxt;
+        queue ^= 1u;
         ++level;
     }
-    *cur_io = cur;
     return TC_OK;
 }
 
@@ -362,11 +496,10 @@ tc_status compute_levels(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t sl
     const unsigned cap = (unsigned)ctx->num_sms * 16u;
     if (n == 0) return TC_OK;
     k_init<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.rp, b.deg, b.L, ctx->d_ctl, ctx->opt.order);
-    int cur = 0;
-    k_seed<<<1, 1, 0, s>>>(b.deg, b.L, b.q0, ctx->d_ctl, cur);
+    k_seed<<<1, 1, 0, s>>>(b.deg, b.L, b.q0, ctx->d_ctl, 0);
     note_launch(ctx, 2);
     TC_CUDA(ctx, cudaGetLastError());
-    tc_status st = bfs_loop(ctx, b, n, slots, 0, &cur);
+    tc_status st = bfs_loop(ctx, b, n, slots, 0, 0, 0);
     if (st != TC_OK) return st;
     if (ctx->h_ctl->visited >= n) return TC_OK;
 
@@ -392,13 +525,12 @@ tc_status compute_levels(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t sl
         if (!ctx->h_ctl->changed) break;
         if (round > 64) return set_error(ctx, TC_ERR_TIMEOUT, "connected components did not converge");
     }
-    cur = 0;
-    k_reset_next<<<1, 1, 0, s>>>(ctx->d_ctl, cur);
-    k_cc_roots<<<grid_for(nr, 256, cap), 256, 0, s>>>(b.R, nr, b.parent, b.deg, b.L, b.q0, ctx->d_ctl, cur);
-    k_count_roots<<<1, 1, 0, s>>>(ctx->d_ctl, cur);
+    k_reset_next<<<1, 1, 0, s>>>(ctx->d_ctl, 0);
+    k_cc_roots<<<grid_for(nr, 256, cap), 256, 0, s>>>(b.R, nr, b.parent, b.deg, b.L, b.q0, ctx->d_ctl, 0);
+    k_count_roots<<<1, 1, 0, s>>>(ctx->d_ctl, 0);
     note_launch(ctx, 3);
     TC_CUDA(ctx, cudaGetLastError());
-    return bfs_loop(ctx, b, n, slots, 0, &cur);
+    return bfs_loop(ctx, b, n, slots, 0, 0, 0);
 }
 
 }  // namespace tc

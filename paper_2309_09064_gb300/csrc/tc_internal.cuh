@@ -47,9 +47,9 @@ struct Ctl {
     unsigned long long cls_probes[3];   // per intersection class (warp, block, hub)
     unsigned long long cls_build[3];    // hashed-row elements per class (each row once)
     unsigned long long cls_rows[3];     // rows (warp) / tasks (block, hub) per class
-    unsigned long long fr_edges[2];  // sum of degrees of the frontier being built
+    unsigned long long fr_edges[3];  // sum of degrees per frontier slot
     unsigned long long visited_edges;
-    unsigned int fr_count[2];        // frontier sizes
+    unsigned int fr_count[3];        // frontier sizes per slot (slots rotate in the persistent BFS)
     unsigned int visited;            // vertices with a level
     unsigned int max_level;
     unsigned int components;         // BFS roots
@@ -60,7 +60,9 @@ struct Ctl {
     unsigned long long n_tasks[3];   // tasks per class
     unsigned int error;              // nonzero: a device-side check failed
     unsigned int max_s2;             // largest hashed row among block-class rows / max degree
-    unsigned int pad[5];
+    unsigned int p_slot, p_queue, p_level;  // where the persistent BFS stopped
+    unsigned int bar_count, bar_gen;        // grid barrier of the persistent BFS
+    unsigned int pad[4];
 };
 
 // ----------------------------------------------------------------------------- arena
