@@ -237,6 +237,13 @@ tc_status tc_submit(tc_ctx *ctx, const tc_graph *g, uint64_t *ticket);
  */
 tc_status tc_poll(tc_ctx *ctx, uint64_t ticket, uint64_t *triangles);
 
+/*
+ * tc_poll that also returns the request's latency in nanoseconds, from its
+ * tc_submit to the moment the server published its result (the library's
+ * steady clock), so a client that polls late does not inflate it.
+ */
+tc_status tc_poll_ex(tc_ctx *ctx, uint64_t ticket, uint64_t *triangles, uint64_t *latency_ns);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,7 @@ __all__ = [
     "TC_ORDER_DEGREE", "TC_ORDER_ID", "tc_create", "tc_destroy", "tc_last_error", "tc_set_stream",
     "tc_arena_bytes", "tc_build_csr", "tc_graph_from_csr", "tc_graph_info", "tc_graph_copy_out",
     "tc_validate", "tc_graph_free", "tc_count", "tc_count_levels", "tc_count_batch", "tc_submit", "tc_poll",
-    "tc_get_tuning", "tc_set_tuning", "tc_count_noalloc", "library_path", "EXPORTED",
+    "tc_get_tuning", "tc_set_tuning", "tc_count_noalloc", "tc_poll_ex", "library_path", "EXPORTED",
 ]
 
 TC_OK, TC_ERR_INVALID, TC_ERR_OOM, TC_ERR_CUDA, TC_ERR_TIMEOUT, TC_ERR_BUSY, TC_NOT_READY = range(7)
@@ -35,7 +35,7 @@ _STATUS = {0: "TC_OK", 1: "TC_ERR_INVALID", 2: "TC_ERR_OOM", 3: "TC_ERR_CUDA", 4
 EXPORTED = ["tc_create", "tc_destroy", "tc_last_error", "tc_set_stream", "tc_get_tuning", "tc_set_tuning",
             "tc_arena_bytes", "tc_build_csr",
             "tc_graph_from_csr", "tc_graph_info", "tc_graph_copy_out", "tc_validate", "tc_graph_free",
-            "tc_count", "tc_count_levels", "tc_count_batch", "tc_submit", "tc_poll", "tc_count_noalloc"]
+            "tc_count", "tc_count_levels", "tc_count_batch", "tc_submit", "tc_poll", "tc_poll_ex", "tc_count_noalloc"]
 
 
 class TcError(RuntimeError):
@@ -103,6 +103,7 @@ def _load():
         "tc_count_batch": ([V, U32, P(V), P(U64)], I),
         "tc_submit": ([V, V, P(U64)], I),
         "tc_poll": ([V, U64, P(U64)], I),
+        "tc_poll_ex": ([V, U64, P(U64), P(U64)], I),
         "tc_count_noalloc": ([V, V, U32, U64, U32, V, V], I),
     }
     for name, (args, res) in sig.items():
@@ -277,6 +278,16 @@ def tc_count_batch(ctx, graphs):
     out = np.zeros(max(G, 1), dtype=np.uint64)
     _check(ctx, _lib.tc_count_batch(ctx, G, arr, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
     return out[:G]
+
+
+def tc_poll_ex(ctx, ticket: int):
+    """(T, latency_ns) when done, None while not ready; raises on failure."""
+    T, lat = ctypes.c_uint64(), ctypes.c_uint64()
+    st = _lib.tc_poll_ex(ctx, ticket, ctypes.byref(T), ctypes.byref(lat))
+    if st == TC_NOT_READY:
+        return None
+    _check(ctx, st)
+    return T.value, lat.value
 
 
 def tc_count_noalloc(row_ptr, col, n: int, slots: int, out, order: int = TC_ORDER_DEGREE, stream=None):

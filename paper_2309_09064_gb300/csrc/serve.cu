@@ -8,6 +8,8 @@
 // immediately admits whatever arrived meanwhile.  While one worker's round
 // runs on the device the other admits and launches the next, so rounds
 // overlap on the GPU and a request never waits for a full batch to form.
+#include <chrono>
+
 #include "pipeline.cuh"
 
 struct ServeRequest {
@@ -15,6 +17,7 @@ struct ServeRequest {
     uint64_t result = 0;
     tc_status st = TC_OK;
     int state = 0;  // 0 queued, 1 running, 2 done
+    std::chrono::steady_clock::time_point t_submit, t_done;
 };
 
 struct ServeState {
@@ -66,6 +69,7 @@ static void worker_loop(ServeState *S, tc_ctx *sub) {
         out.assign(tickets.size(), 0);
         tc_status st = tc_count_batch(sub, (uint32_t)graphs.size(), graphs.data(), out.data());
         {
+            const auto now = std::chrono::steady_clock::now();
             std::lock_guard<std::mutex> lk(S->mu);
             for (size_t i = 0; i < tickets.size(); ++i) {
                 auto it = S->reqs.find(tickets[i]);
@@ -73,6 +77,7 @@ static void worker_loop(ServeState *S, tc_ctx *sub) {
                 it->second.result = out[i];
                 it->second.st = st;
                 it->second.state = 2;
+                it->second.t_done = now;
             }
         }
     }
@@ -148,6 +153,7 @@ tc_status tc_submit(tc_ctx *ctx, const tc_graph *g, uint64_t *ticket) {
         const uint64_t t = S->next_ticket++;
         ServeRequest rq;
         rq.g = g;
+        rq.t_submit = std::chrono::steady_clock::now();
         S->reqs.emplace(t, rq);
         S->queue.push_back(t);
         *ticket = t;
@@ -156,7 +162,7 @@ tc_status tc_submit(tc_ctx *ctx, const tc_graph *g, uint64_t *ticket) {
     return TC_OK;
 }
 
-tc_status tc_poll(tc_ctx *ctx, uint64_t ticket, uint64_t *triangles) {
+tc_status tc_poll_ex(tc_ctx *ctx, uint64_t ticket, uint64_t *triangles, uint64_t *latency_ns) {
     if (!ctx || !triangles) return TC_ERR_INVALID;
     ServeState *S = ctx->serve;
     if (!S) return TC_ERR_INVALID;
@@ -166,8 +172,14 @@ tc_status tc_poll(tc_ctx *ctx, uint64_t ticket, uint64_t *triangles) {
     if (it->second.state != 2) return TC_NOT_READY;
     const tc_status st = it->second.st;
     *triangles = it->second.result;
+    if (latency_ns)
+        *latency_ns = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(it->second.t_done -
+                                                                                     it->second.t_submit)
+                          .count();
     S->reqs.erase(it);
     return st;
 }
+
+tc_status tc_poll(tc_ctx *ctx, uint64_t ticket, uint64_t *triangles) { return tc_poll_ex(ctx, ticket, triangles, nullptr); }
 
 }  // extern "C"

@@ -241,11 +241,13 @@ def test_served_results_alone_and_in_the_mix(tc):
                         got[i] = r
         assert len(got) == len(tickets)
         assert [got[i] for i in range(len(gs))] == alone
-        # one more request on its own after the mix
+        # one more request on its own after the mix, with its latency
         t = tc.tc_submit(c, gs[3])
-        while (r := tc.tc_poll(c, t)) is None:
+        while (r := tc.tc_poll_ex(c, t)) is None:
             pass
-        assert r == alone[3]
+        assert r[0] == alone[3] and r[1] > 0
+        with pytest.raises(tc.TcError):
+            tc.tc_poll(c, t)  # a ticket is released once its result has been read
         for g in gs:
             tc.tc_graph_free(g)
     finally:
