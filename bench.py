@@ -307,6 +307,7 @@ def main():
                     help="arrival rates as fractions of the measured batched throughput (requests/s)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="pick the intersection knobs by timing candidates first")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -334,6 +335,10 @@ def main():
     torch.cuda.synchronize()
     n_, slots, _, _ = tc.tc_graph_info(g)
     m = slots // 2
+    tuned = None
+    if args.autotune:
+        from paper_2309_09064_gb300 import autotune
+        tuned, _ = autotune.autotune(ctx, [g], reps=1)
 
     T0 = None
     for _ in range(max(args.warmup, 0)):
@@ -412,7 +417,8 @@ def main():
         "metric": "edges/sec counted (exact)", "value": value, "unit": "edges/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": config_of(args.workload, w, n_, m, {"parallelism": f"replicas x{world}"}),
+        "config": config_of(args.workload, w, n_, m, {"parallelism": f"replicas x{world}",
+                                                      "tuning": tuned or tc.tc_get_tuning(ctx)}),
         "triangles": T0, "t_same": last["t_same"], "t_cross": last["t_cross"],
         "horizontal_edges": last["horizontal_edges"], "levels": last["levels"],
         "stage_ms": {"levels": mean("ms_levels"), "rows": mean("ms_mark"), "intersect": mean("ms_isect"),

@@ -101,6 +101,7 @@ typedef struct tc_stats {
     uint64_t class_probes[3];   /* probed elements */
     uint64_t class_bytes[3];    /* algorithmic bytes: hashed rows once + probed rows */
     float ms_class[3];          /* device time of each class's kernel (0 if not launched) */
+    uint64_t class_inserts[3];  /* table / prefilter inserts done, rebuilds on other blocks included */
     uint32_t launches;          /* kernels this call launched */
     uint32_t reserved;
 } tc_stats;
@@ -110,13 +111,19 @@ typedef struct tc_stats {
  * rows are classed by the size s(u) of the hashed row of the first endpoint.
  */
 typedef struct tc_tuning {
-    uint32_t warp_cap;         /* s(u) <= warp_cap: one warp per row, per-warp shared table (1..4096) */
+    uint32_t warp_cap;         /* s(u) <= warp_cap: one warp per task, per-warp shared table (1..4096) */
     uint32_t block_cap;        /* s(u) <= block_cap: one block per task, shared table (warp_cap..16384);
-                                  larger rows use block-private tables in global memory */
+                                  larger rows are hub rows (L2 bitmaps + shared prefilter) */
     uint32_t task_work;        /* target probes per block task (large rows are split) */
     uint32_t warps_per_block;  /* warp-class kernel block size in warps (1..32) */
     uint32_t block_threads;    /* block-class kernel threads (64..1024, multiple of 32) */
-    uint32_t reserved[3];
+    uint32_t warp_task_work;   /* target probes per warp task */
+    uint32_t hub_task_work;    /* target probes per hub task */
+    uint32_t max_v;            /* out-neighbour rows per block / hub task (64..4096) */
+    uint32_t hub_group;        /* hub rows probed per launch, one n-bit bitmap each (1..64) */
+    uint32_t hub_filter_log2;  /* hub prefilter size: 2^k bits of shared memory (10..20) */
+    uint32_t hub_threads;      /* hub kernel threads (64..1024, multiple of 32) */
+    uint32_t reserved[5];
 } tc_tuning;
 
 /* ------------------------------------------------------------------ context */

@@ -50,9 +50,10 @@ class tc_options(ctypes.Structure):
 
 
 class tc_tuning(ctypes.Structure):
-    _fields_ = [("warp_cap", ctypes.c_uint32), ("block_cap", ctypes.c_uint32), ("task_work", ctypes.c_uint32),
-                ("warps_per_block", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 3)]
+    _fields_ = [(k, ctypes.c_uint32) for k in (
+        "warp_cap", "block_cap", "task_work", "warps_per_block", "block_threads", "warp_task_work",
+        "hub_task_work", "max_v", "hub_group", "hub_filter_log2", "hub_threads")] + [
+        ("reserved", ctypes.c_uint32 * 5)]
 
     def to_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -65,6 +66,7 @@ class tc_stats(ctypes.Structure):
             "ms_total", "ms_levels", "ms_mark", "ms_isect")] + [
         ("class_rows", ctypes.c_uint64 * 3), ("class_probes", ctypes.c_uint64 * 3),
         ("class_bytes", ctypes.c_uint64 * 3), ("ms_class", ctypes.c_float * 3),
+        ("class_inserts", ctypes.c_uint64 * 3),
         ("launches", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
     def to_dict(self):

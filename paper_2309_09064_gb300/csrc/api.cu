@@ -151,32 +151,45 @@ tc_status tc_set_stream(tc_ctx *ctx, void *stream) {
 tc_status tc_get_tuning(const tc_ctx *ctx, tc_tuning *out) {
     if (!ctx || !out) return TC_ERR_INVALID;
     std::memset(out, 0, sizeof(*out));
-    out->warp_cap = ctx->tune.warp_cap;
-    out->block_cap = ctx->tune.block_cap;
-    out->task_work = ctx->tune.task_work;
-    out->warps_per_block = ctx->tune.warps_per_block;
-    out->block_threads = ctx->tune.block_threads;
+    const Tuning &t = ctx->tune;
+    out->warp_cap = t.warp_cap;
+    out->block_cap = t.block_cap;
+    out->task_work = t.task_work;
+    out->warps_per_block = t.warps_per_block;
+    out->block_threads = t.block_threads;
+    out->warp_task_work = t.warp_task_work;
+    out->hub_task_work = t.hub_task_work;
+    out->max_v = t.max_v;
+    out->hub_group = t.hub_group;
+    out->hub_filter_log2 = t.hub_filter_log2;
+    out->hub_threads = t.hub_threads;
     return TC_OK;
 }
 
 tc_status tc_set_tuning(tc_ctx *ctx, const tc_tuning *t) {
     if (!ctx || !t) return TC_ERR_INVALID;
-    auto pow2 = [](uint64_t x) {
-        uint64_t p = 64;
-        while (p < x) p <<= 1;
-        return p;
-    };
-    const uint64_t smem_limit = 227 * 1024;
-    if (t->warp_cap < 1 || t->warp_cap > 4096 || t->block_cap < t->warp_cap || t->block_cap > 16384 ||
-        t->task_work < 1 || t->warps_per_block < 1 || t->warps_per_block > 32 || t->block_threads < 64 ||
-        t->block_threads > 1024 || t->block_threads % 32 ||
-        pow2(2ull * t->warp_cap) * 4 * t->warps_per_block > smem_limit || pow2(2ull * t->block_cap) * 4 > smem_limit)
+    Tuning nt;
+    nt.warp_cap = t->warp_cap;
+    nt.block_cap = t->block_cap;
+    nt.task_work = t->task_work;
+    nt.warps_per_block = t->warps_per_block;
+    nt.block_threads = t->block_threads;
+    nt.warp_task_work = t->warp_task_work;
+    nt.hub_task_work = t->hub_task_work;
+    nt.max_v = t->max_v;
+    nt.hub_group = t->hub_group;
+    nt.hub_filter_log2 = t->hub_filter_log2;
+    nt.hub_threads = t->hub_threads;
+    const size_t smem_limit = 227 * 1024;
+    auto threads_ok = [](uint32_t x) { return x >= 64 && x <= 1024 && x % 32 == 0; };
+    if (nt.warp_cap < 1 || nt.warp_cap > 4096 || nt.block_cap < nt.warp_cap || nt.block_cap > 16384 ||
+        nt.task_work < 1 || nt.warp_task_work < 1 || nt.hub_task_work < 1 || nt.warps_per_block < 1 ||
+        nt.warps_per_block > 32 || !threads_ok(nt.block_threads) || !threads_ok(nt.hub_threads) || nt.max_v < 64 ||
+        nt.max_v > 4096 || nt.hub_group < 1 || nt.hub_group > 64 || nt.hub_filter_log2 < 10 ||
+        nt.hub_filter_log2 > 20 || warp_kernel_smem(nt) > smem_limit || block_kernel_smem(nt) > smem_limit ||
+        hub_kernel_smem(nt) > smem_limit)
         return set_error(ctx, TC_ERR_INVALID, "tuning out of range");
-    ctx->tune.warp_cap = t->warp_cap;
-    ctx->tune.block_cap = t->block_cap;
-    ctx->tune.task_work = t->task_work;
-    ctx->tune.warps_per_block = t->warps_per_block;
-    ctx->tune.block_threads = t->block_threads;
+    ctx->tune = nt;
     return TC_OK;
 }
 

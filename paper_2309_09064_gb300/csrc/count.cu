@@ -148,6 +148,7 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
             stats->class_rows[c] = h.cls_rows[c];
             stats->class_probes[c] = h.cls_probes[c];
             stats->class_bytes[c] = 4ull * (h.cls_build[c] + h.cls_probes[c]);
+            stats->class_inserts[c] = h.cls_inserts[c];
             is += stats->class_bytes[c];
             stats->ms_class[c] = 0.f;
             if (ctx->isect_flags & (1u << c)) cudaEventElapsedTime(&stats->ms_class[c], ctx->ev[4 + c], ctx->ev[5 + c]);

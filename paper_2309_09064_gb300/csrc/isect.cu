@@ -28,9 +28,6 @@
 namespace tc {
 namespace {
 
-constexpr int kUnrollTable = 8;  // row elements in flight per lane, shared-table classes
-constexpr int kUnrollHub = 8;    // row elements in flight per lane, hub class
-constexpr uint32_t kFilterLog2 = 20;      // hub prefilter: 2^20 bits (128 KB)
 
 struct Acc {
     unsigned long long same = 0, cross = 0, probes = 0;
@@ -44,6 +41,7 @@ struct Acc {
 // whose last slot is empty ends every probe sequence that reaches it: a key
 // sits in the first bucket, from its home, that had room when it was inserted.
 struct BucketTable {
+    static constexpr int kUnroll = 8;  // row ids in flight per lane
     uint4 *bk;
     uint32_t shift, mask;  // home bucket = hash >> shift; mask = buckets - 1
 };
@@ -80,13 +78,15 @@ __device__ __forceinline__ void fill_table(const BucketTable &T, const uint32_t 
     }
 }
 
-// Hub rows: shared prefilter (one hash into 2^kFilterLog2 bits) in front of
-// the exact n-bit bitmap in global memory.
-__device__ __forceinline__ uint32_t filter_bit(uint32_t w) { return (w * 0x85EBCA6Bu) >> (32 - kFilterLog2); }
+// Hub rows: shared prefilter (one multiplicative hash into 2^k bits, k =
+// hub_filter_log2) in front of the exact n-bit bitmap in global memory.
+__device__ __forceinline__ uint32_t filter_bit(uint32_t w, uint32_t fshift) { return (w * 0x85EBCA6Bu) >> fshift; }
 
 struct HubSet {
+    static constexpr int kUnroll = 8;  // row ids in flight per lane
     const uint32_t *filter;  // shared
     const uint32_t *bits;    // global, read-only while probing
+    uint32_t fshift;         // 32 - hub_filter_log2
 };
 
 // ---------------------------------------------------------------------------- probing one row
@@ -94,7 +94,7 @@ struct HubSet {
 // Probe positions [j_lo, len) of row(v) = adj2[b .. b+len) with one warp;
 // position j < hv is the G0
 // part (a triangle inside G0), the rest the G1 part (a cross-level triangle).
-// Each lane first issues all its element loads (kUnrollTable or kUnrollHub), then all first lookups,
+// Each lane first issues all its element loads, then all first lookups,
 // then resolves them, so independent memory operations overlap.
 // Per-row-step hit counters stay 32-bit in registers; probe_row adds them to
 // the 64-bit accumulators once per call.
@@ -140,57 +140,50 @@ __device__ __forceinline__ void lookup_batch(const BucketTable &T, const uint32_
     }
 }
 
-__device__ __forceinline__ void probe_row(const BucketTable &T, const uint32_t *__restrict__ adj2,
-                                          unsigned long long b, uint32_t j_lo, uint32_t len, uint32_t hv, Acc &acc) {
-    const unsigned lane = lane_id();
-    const uint32_t *row = adj2 + b;
-    Hits hits;
-    for (uint32_t j0 = j_lo; j0 < len; j0 += 32u * kUnrollTable) {
-        uint32_t w[kUnrollTable];
+// Hub batch: shared prefilter for all N elements, then the exact bitmap word
+// for the prefilter-positive ones (predicated loads, all in flight together).
+template <int N>
+__device__ __forceinline__ void lookup_batch(const HubSet &H, const uint32_t (&w)[N], bool (&hit)[N]) {
+    bool pos[N];
 #pragma unroll
-        for (int i = 0; i < kUnrollTable; ++i) {
-            const uint32_t j = j0 + (uint32_t)i * 32u + lane;
-            w[i] = j < len ? row[j] : kEmpty;
-        }
-#pragma unroll
-        for (int half = 0; half < kUnrollTable; half += kUnrollTable / 2) {
-            uint32_t ww[kUnrollTable / 2];
-            bool hit[kUnrollTable / 2];
-#pragma unroll
-            for (int i = 0; i < kUnrollTable / 2; ++i) ww[i] = w[half + i];
-            lookup_batch(T, ww, hit);
-#pragma unroll
-            for (int i = 0; i < kUnrollTable / 2; ++i)
-                hits.add(hit[i], j0 + (uint32_t)(half + i) * 32u + lane, hv);
-        }
+    for (int i = 0; i < N; ++i) {
+        const uint32_t f = filter_bit(w[i], H.fshift);
+        pos[i] = w[i] != kEmpty && ((H.filter[f >> 5] >> (f & 31)) & 1u);
     }
-    hits.flush(acc);
+    uint32_t word[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) word[i] = pos[i] ? __ldg(H.bits + (w[i] >> 5)) : 0u;
+#pragma unroll
+    for (int i = 0; i < N; ++i) hit[i] = pos[i] && ((word[i] >> (w[i] & 31)) & 1u);
 }
 
-__device__ __forceinline__ void probe_row(const HubSet &H, const uint32_t *__restrict__ adj2, unsigned long long b,
-                                          uint32_t j_lo, uint32_t len, uint32_t hv, Acc &acc) {
+// Probe positions [j_lo, j_hi) of row(v) = adj2[b ..] with one warp, lanes
+// striding over the positions with U loads in flight each.  Position j < hv
+// is the G0 part (a triangle inside G0), the rest the G1 part (a cross-level
+// triangle).  Lookups are resolved in halves of U/2 to bound registers.
+template <int U, class Set>
+__device__ __forceinline__ void probe_row(const Set &set, const uint32_t *__restrict__ adj2, unsigned long long b,
+                                          uint32_t j_lo, uint32_t j_hi, uint32_t hv, Acc &acc) {
     const unsigned lane = lane_id();
     const uint32_t *row = adj2 + b;
     Hits hits;
-    for (uint32_t j0 = j_lo; j0 < len; j0 += 32u * kUnrollHub) {
-        uint32_t w[kUnrollHub];
+    for (uint32_t j0 = j_lo; j0 < j_hi; j0 += 32u * U) {
+        uint32_t w[U];
 #pragma unroll
-        for (int i = 0; i < kUnrollHub; ++i) {
+        for (int i = 0; i < U; ++i) {
             const uint32_t j = j0 + (uint32_t)i * 32u + lane;
-            w[i] = j < len ? row[j] : kEmpty;
+            w[i] = j < j_hi ? __ldg(row + j) : kEmpty;
         }
-        bool pos[kUnrollHub];
 #pragma unroll
-        for (int i = 0; i < kUnrollHub; ++i) {
-            const uint32_t f = filter_bit(w[i]);
-            pos[i] = w[i] != kEmpty && ((H.filter[f >> 5] >> (f & 31)) & 1u);
+        for (int half = 0; half < U; half += U / 2) {
+            uint32_t ww[U / 2];
+            bool hit[U / 2];
+#pragma unroll
+            for (int i = 0; i < U / 2; ++i) ww[i] = w[half + i];
+            lookup_batch(set, ww, hit);
+#pragma unroll
+            for (int i = 0; i < U / 2; ++i) hits.add(hit[i], j0 + (uint32_t)(half + i) * 32u + lane, hv);
         }
-        uint32_t word[kUnrollHub];
-#pragma unroll
-        for (int i = 0; i < kUnrollHub; ++i) word[i] = pos[i] ? __ldg(H.bits + (w[i] >> 5)) : 0u;
-#pragma unroll
-        for (int i = 0; i < kUnrollHub; ++i)
-            hits.add(pos[i] && ((word[i] >> (w[i] & 31)) & 1u), j0 + (uint32_t)i * 32u + lane, hv);
     }
     hits.flush(acc);
 }
@@ -233,7 +226,7 @@ __global__ void __launch_bounds__(1024) k_isect_warp(const uint2 *__restrict__ t
     uint4 *bk = reinterpret_cast<uint4 *>(smem_raw) + (size_t)warp * table_buckets;
     const unsigned long long ntasks = ctl->n_tasks[0];
     Acc acc;
-    unsigned long long build = 0, done = 0;
+    unsigned long long build = 0, done = 0, inserts = 0;
     uint32_t cur_row = 0xFFFFFFFFu;
     BucketTable T{bk, 0, 0};
     for (;;) {
@@ -254,6 +247,7 @@ __global__ void __launch_bounds__(1024) k_isect_warp(const uint2 *__restrict__ t
             fill_table(T, adj2 + ub, su, lane, 32);
             __syncwarp();
             cur_row = task.x;
+            inserts += su;
         }
         if (task.y == 0) build += su;
         ++done;
@@ -274,7 +268,7 @@ __global__ void __launch_bounds__(1024) k_isect_warp(const uint2 *__restrict__ t
                 const unsigned long long bt = __shfl_sync(0xFFFFFFFFu, b, t);
                 const uint32_t lt = __shfl_sync(0xFFFFFFFFu, len, t);
                 const uint32_t ht = __shfl_sync(0xFFFFFFFFu, hv, t);
-                probe_row(T, adj2, bt, 0, lt, ht, acc);
+                probe_row<BucketTable::kUnroll>(T, adj2, bt, 0, lt, ht, acc);
             }
         }
         if (groups.n_groups) {
@@ -283,6 +277,7 @@ __global__ void __launch_bounds__(1024) k_isect_warp(const uint2 *__restrict__ t
         }
     }
     flush(acc, ctl, 0, lane == 0 ? build : 0, lane == 0 ? done : 0);
+    if (lane == 0 && inserts) atomicAdd(&ctl->cls_inserts[0], inserts);
 }
 
 // ---------------------------------------------------------------------------- block and hub classes
@@ -381,7 +376,7 @@ __device__ __forceinline__ void probe_slice(const Set &set, const SliceSmem &S, 
         const uint32_t j_lo = (g - S.seg[a]) * kSeg;
         const uint32_t j_hi = min(len, j_lo + kSeg);
         if (lane == 0) acc.probes += j_hi - j_lo;
-        probe_row(set, adj2, S.b[a], j_lo, j_hi, S.h[a], acc);
+        probe_row<Set::kUnroll>(set, adj2, S.b[a], j_lo, j_hi, S.h[a], acc);
     }
 }
 
@@ -435,7 +430,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
     uint4 *bk = reinterpret_cast<uint4 *>(smem_raw + slice_smem_bytes(max_v));
     const unsigned long long ntasks = ctl->n_tasks[1];
     Acc acc;
-    unsigned long long build = 0, done = 0;
+    unsigned long long build = 0, done = 0, inserts = 0;
     uint32_t cur_row = 0xFFFFFFFFu;
     BucketTable T{bk, 0, 0};
     init_task_smem(&ts);
@@ -455,6 +450,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
             fill_table(T, adj2 + ub, su, threadIdx.x, blockDim.x);
             __syncthreads();
             cur_row = task.x;
+            if (threadIdx.x == 0) inserts += su;
         }
         if (threadIdx.x == 0) {
             if (task.y == 0) build += su;
@@ -470,6 +466,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
         }
     }
     flush(acc, ctl, 1, threadIdx.x == 0 ? build : 0, threadIdx.x == 0 ? done : 0);
+    if (threadIdx.x == 0 && inserts) atomicAdd(&ctl->cls_inserts[1], inserts);
 }
 
 // Set the bits of hub rows rows[i0 .. i0+g) into bitmaps bits + r * words.
@@ -496,15 +493,16 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
                                                     const uint64_t *__restrict__ off2, const uint32_t *__restrict__ adj2,
                                                     const uint32_t *__restrict__ hcnt, Ctl *ctl, const uint32_t *bits,
                                                     uint64_t words, uint32_t max_v, unsigned long long chunk,
-                                                    GroupSpec groups) {
+                                                    uint32_t filter_log2, GroupSpec groups) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TaskSmem ts;
     const unsigned lane = lane_id();
     const SliceSmem S = carve_slice(smem_raw, max_v);
     uint32_t *filter = reinterpret_cast<uint32_t *>(smem_raw + slice_smem_bytes(max_v));
-    constexpr uint32_t kFilterWords = 1u << (kFilterLog2 - 5);
+    const uint32_t kFilterWords = 1u << (filter_log2 - 5);
+    const uint32_t fshift = 32u - filter_log2;
     Acc acc;
-    unsigned long long build = 0, done = 0;
+    unsigned long long build = 0, done = 0, inserts = 0;
     uint32_t cur_row = 0xFFFFFFFFu;
     init_task_smem(&ts);
     while (next_task(ctl, 2, first, last, chunk, tasks, &ts)) {
@@ -522,17 +520,18 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
         scan_segments(S.len, S.seg, k_hi - k_lo);
         if (rebuild) {
             for (uint32_t j = threadIdx.x; j < su; j += blockDim.x) {
-                const uint32_t f = filter_bit(adj2[ub + j]);
+                const uint32_t f = filter_bit(adj2[ub + j], fshift);
                 atomicOr(filter + (f >> 5), 1u << (f & 31));
             }
             __syncthreads();
             cur_row = task.x;
+            if (threadIdx.x == 0) inserts += su;
         }
         if (threadIdx.x == 0) {
             if (task.y == 0) build += su;
             ++done;
         }
-        const HubSet H{filter, bits + (uint64_t)(task.x - i0) * words};
+        const HubSet H{filter, bits + (uint64_t)(task.x - i0) * words, fshift};
         const unsigned long long before = acc.same + acc.cross;
         probe_slice(H, S, k_hi - k_lo, adj2, &ts.next, acc);
         if (groups.n_groups) {
@@ -543,6 +542,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
         }
     }
     flush(acc, ctl, 2, threadIdx.x == 0 ? build : 0, threadIdx.x == 0 ? done : 0);
+    if (threadIdx.x == 0 && inserts) atomicAdd(&ctl->cls_inserts[2], inserts);
 }
 
 uint32_t pow2_at_least(uint64_t x, uint32_t lo) {
@@ -558,7 +558,7 @@ uint32_t warp_table_buckets(const Tuning &tu) { return pow2_at_least((tu.warp_ca
 uint32_t block_table_buckets(const Tuning &tu) { return pow2_at_least((tu.block_cap + 1) / 2, 16); }
 size_t warp_kernel_smem(const Tuning &tu) { return (size_t)tu.warps_per_block * 16ull * warp_table_buckets(tu); }
 size_t block_kernel_smem(const Tuning &tu) { return slice_smem_bytes(tu.max_v) + 16ull * block_table_buckets(tu); }
-size_t hub_kernel_smem(const Tuning &tu) { return slice_smem_bytes(tu.max_v) + (1ull << kFilterLog2) / 8; }
+size_t hub_kernel_smem(const Tuning &tu) { return slice_smem_bytes(tu.max_v) + (1ull << tu.hub_filter_log2) / 8; }
 
 tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
     (void)n;
@@ -619,7 +619,8 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
             const unsigned long long chunk = std::max<unsigned long long>(1, (last - first) / (grid * 4));
             k_isect_hub<<<(unsigned)grid, tu.hub_threads, smem, s>>>(b.tasks[2], first, last, b.rows[2], b.ntask[2], i0,
                                                                      b.off2, b.adj2, b.hcnt, ctx->d_ctl, b.hub_bits,
-                                                                     b.hub_words, tu.max_v, chunk, b.groups);
+                                                                     b.hub_words, tu.max_v, chunk, tu.hub_filter_log2,
+                                                                     b.groups);
             note_launch(ctx, 2);
         }
     }

@@ -26,14 +26,15 @@ constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 struct Tuning {
     uint32_t warp_cap = 1024;        // s(u) <= warp_cap: warp tasks, per-warp smem table
     uint32_t block_cap = 16384;      // s(u) <= block_cap: block tasks, smem table; larger: hub tasks
-    uint32_t task_work = 65536;      // target probes per block task (at least 2 s(u))
+    uint32_t task_work = 131072;     // target probes per block task (at least 2 s(u))
     uint32_t warps_per_block = 8;    // warp-class kernel: warps per block
     uint32_t block_threads = 1024;   // block-class kernel threads
     uint32_t warp_task_work = 16384; // target probes per warp task
-    uint32_t hub_task_work = 131072; // target probes per hub task
+    uint32_t hub_task_work = 262144; // target probes per hub task
     uint32_t max_v = 2048;           // out-neighbours per block / hub task (shared-memory metadata)
     uint32_t hub_group = 8;          // hub rows sharing one launch (one L2-resident bitmap each)
     uint32_t hub_threads = 1024;     // hub kernel threads
+    uint32_t hub_filter_log2 = 20;   // hub prefilter bits (log2)
 };
 
 // Control block in device memory: counters the kernels update and the host
@@ -47,6 +48,7 @@ struct Ctl {
     unsigned long long cls_probes[3];   // per intersection class (warp, block, hub)
     unsigned long long cls_build[3];    // hashed-row elements per class (each row once)
     unsigned long long cls_rows[3];     // rows (warp) / tasks (block, hub) per class
+    unsigned long long cls_inserts[3];  // table / prefilter inserts actually done (rebuilds included)
     unsigned long long fr_edges[3];  // sum of degrees per frontier slot
     unsigned long long visited_edges;
     unsigned int fr_count[3];        // frontier sizes per slot (slots rotate in the persistent BFS)
@@ -167,6 +169,11 @@ tc_status validate_csr_device(tc_ctx *ctx, uint32_t n, const uint64_t *rp, const
 tc_status max_degree_device(tc_ctx *ctx, uint32_t n, const uint64_t *rp, uint32_t *max_deg);
 // Batched counting of G graphs as one disjoint union (batch.cu).
 tc_status count_batch(tc_ctx *ctx, uint32_t G, const tc_graph *const *graphs, uint64_t *counts);
+
+// Shared-memory bytes of the intersection kernels under a tuning (isect.cu)
+size_t warp_kernel_smem(const Tuning &tu);
+size_t block_kernel_smem(const Tuning &tu);
+size_t hub_kernel_smem(const Tuning &tu);
 
 // Serving (serve.cu)
 void serve_shutdown(tc_ctx *ctx);

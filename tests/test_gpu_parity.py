@@ -298,3 +298,21 @@ def test_full_size_against_stored_oracle(tc, ctx, name):
     assert hashlib.sha256(Lh.astype("<u4").tobytes()).hexdigest() == ref["levels_sha256"]
     if "grid_diagonals" in ref:
         assert T == 2 * ref["grid_diagonals"]
+
+
+def test_autotuner_keeps_counts_and_sets_a_valid_tuning(tc, tmp_path):
+    from paper_2309_09064_gb300 import autotune
+    c = tc.tc_create(0)
+    try:
+        graphs = [tc.tc_build_csr(c, *gg.rmat(13, 16, seed=3)), tc.tc_build_csr(c, *SMALL["union"])]
+        want = [tc.tc_count(c, g)[0] for g in graphs]
+        cache = str(tmp_path / "tune.json")
+        best, table = autotune.autotune(c, graphs, reps=1, cache_path=cache)
+        assert table and tc.tc_get_tuning(c) == best
+        assert list(tc.tc_count_batch(c, graphs)) == want
+        again, table2 = autotune.autotune(c, graphs, cache_path=cache)  # served from the cache
+        assert again == best and table2 == []
+        for g in graphs:
+            tc.tc_graph_free(g)
+    finally:
+        tc.tc_destroy(c)
