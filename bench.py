@@ -308,6 +308,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true", help="pick the intersection knobs by timing candidates first")
+    ap.add_argument("--shard", action="store_true",
+                    help="with N > 1: split one count across the ranks (strong scaling) instead of N replicas")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -340,9 +342,19 @@ def main():
         from paper_2309_09064_gb300 import autotune
         tuned, _ = autotune.autotune(ctx, [g], reps=1)
 
+    sharded = args.shard and world > 1
+    if sharded:
+        from paper_2309_09064_gb300 import shard as shard_mod
+
+    def one_count():
+        if sharded:
+            part, st = tc.tc_count_shard(ctx, g, rank, world)
+            return shard_mod.sum_partials(part), st
+        return tc.tc_count(ctx, g)
+
     T0 = None
     for _ in range(max(args.warmup, 0)):
-        T0, _ = tc.tc_count(ctx, g)
+        T0, _ = one_count()
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -353,7 +365,7 @@ def main():
     stats = []
     e0.record(stream)
     for _ in range(args.steps):
-        T, st = tc.tc_count(ctx, g)
+        T, st = one_count()
         stats.append(st)
         assert T0 is None or T == T0, "count changed between steps"
     e1.record(stream)
@@ -366,7 +378,7 @@ def main():
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = world * m / (ms / 1e3)
+    value = (1 if sharded else world) * m / (ms / 1e3)
 
     # dominant kernel of the count by device time, from the library's own events
     def mean(key, i=None):
@@ -416,8 +428,9 @@ def main():
     line = {
         "metric": "edges/sec counted (exact)", "value": value, "unit": "edges/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": config_of(args.workload, w, n_, m, {"parallelism": f"replicas x{world}",
+        "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": config_of(args.workload, w, n_, m, {"parallelism": (f"intersection tasks sharded x{world}"
+                                                                      if sharded else f"replicas x{world}"),
                                                       "tuning": tuned or tc.tc_get_tuning(ctx)}),
         "triangles": T0, "t_same": last["t_same"], "t_cross": last["t_cross"],
         "horizontal_edges": last["horizontal_edges"], "levels": last["levels"],

@@ -142,6 +142,17 @@ tc_status tc_set_tuning(tc_ctx *ctx, const tc_tuning *t);
 /* Bytes of device memory currently held by the context's arena. */
 tc_status tc_arena_bytes(const tc_ctx *ctx, uint64_t *bytes);
 
+/*
+ * Self-test of the bounded device-wide wait used by the persistent BFS: one
+ * launch waits at a grid barrier that can never complete (one arrival is
+ * missing), gives up after timeout_ms (1..10000) and reports it.  Returns
+ * TC_ERR_TIMEOUT when the wait ended as designed; the context stays usable.
+ * Fault injection: if the environment variable TC_FAIL_ALLOC_AT=k is set when
+ * a context is created, the context's k-th device allocation fails (once)
+ * and the call that made it returns TC_ERR_OOM with nothing leaked.
+ */
+tc_status tc_selftest_barrier(tc_ctx *ctx, uint32_t timeout_ms);
+
 /* ------------------------------------------------------------------- graphs */
 
 /*
@@ -196,6 +207,17 @@ tc_status tc_count(tc_ctx *ctx, const tc_graph *g, uint64_t *triangles, tc_stats
  */
 tc_status tc_count_levels(tc_ctx *ctx, const tc_graph *g, uint32_t *d_levels, uint64_t *triangles,
                           tc_stats *stats);
+
+/*
+ * One shard of a count split across nshards processes or devices (the
+ * multi-GPU form of the method: BFS levels and rows are computed in full on
+ * every shard, the intersection tasks -- contiguous slices of the oriented
+ * horizontal edges, of about equal probe work -- are divided, and the exact
+ * total is the sum of the nshards partial counts, one 8-byte exchange).
+ * *partial gets this shard's share; shard < nshards.
+ */
+tc_status tc_count_shard(tc_ctx *ctx, const tc_graph *g, uint32_t shard, uint32_t nshards, uint64_t *partial,
+                         tc_stats *stats);
 
 /*
  * Count G independent graphs in one batched launch sequence; counts is a host

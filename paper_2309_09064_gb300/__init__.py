@@ -21,7 +21,9 @@ __all__ = [
     "TC_ORDER_DEGREE", "TC_ORDER_ID", "tc_create", "tc_destroy", "tc_last_error", "tc_set_stream",
     "tc_arena_bytes", "tc_build_csr", "tc_graph_from_csr", "tc_graph_info", "tc_graph_copy_out",
     "tc_validate", "tc_graph_free", "tc_count", "tc_count_levels", "tc_count_batch", "tc_submit", "tc_poll",
-    "tc_get_tuning", "tc_set_tuning", "tc_count_noalloc", "tc_poll_ex", "library_path", "EXPORTED",
+    "tc_get_tuning", "tc_set_tuning", "tc_count_noalloc", "tc_poll_ex", "tc_count_shard", "tc_selftest_barrier",
+    "library_path",
+    "EXPORTED",
 ]
 
 TC_OK, TC_ERR_INVALID, TC_ERR_OOM, TC_ERR_CUDA, TC_ERR_TIMEOUT, TC_ERR_BUSY, TC_NOT_READY = range(7)
@@ -33,9 +35,11 @@ _STATUS = {0: "TC_OK", 1: "TC_ERR_INVALID", 2: "TC_ERR_OOM", 3: "TC_ERR_CUDA", 4
 
 # every entry point tc.h declares
 EXPORTED = ["tc_create", "tc_destroy", "tc_last_error", "tc_set_stream", "tc_get_tuning", "tc_set_tuning",
+            "tc_selftest_barrier",
             "tc_arena_bytes", "tc_build_csr",
             "tc_graph_from_csr", "tc_graph_info", "tc_graph_copy_out", "tc_validate", "tc_graph_free",
-            "tc_count", "tc_count_levels", "tc_count_batch", "tc_submit", "tc_poll", "tc_poll_ex", "tc_count_noalloc"]
+            "tc_count", "tc_count_levels", "tc_count_shard", "tc_count_batch", "tc_submit", "tc_poll", "tc_poll_ex",
+            "tc_count_noalloc"]
 
 
 class TcError(RuntimeError):
@@ -94,6 +98,7 @@ def _load():
         "tc_get_tuning": ([V, P(tc_tuning)], I),
         "tc_set_tuning": ([V, P(tc_tuning)], I),
         "tc_arena_bytes": ([V, P(U64)], I),
+        "tc_selftest_barrier": ([V, U32], I),
         "tc_build_csr": ([V, U32, U64, V, V, I, P(V)], I),
         "tc_graph_from_csr": ([V, U32, V, V, I, I, P(V)], I),
         "tc_graph_info": ([V, P(U32), P(U64), P(V), P(V)], I),
@@ -102,6 +107,7 @@ def _load():
         "tc_graph_free": ([V], I),
         "tc_count": ([V, V, P(U64), P(tc_stats)], I),
         "tc_count_levels": ([V, V, V, P(U64), P(tc_stats)], I),
+        "tc_count_shard": ([V, V, U32, U32, P(U64), P(tc_stats)], I),
         "tc_count_batch": ([V, U32, P(V), P(U64)], I),
         "tc_submit": ([V, V, P(U64)], I),
         "tc_poll": ([V, U64, P(U64)], I),
@@ -190,6 +196,11 @@ def tc_set_tuning(ctx, **kw):
     _check(ctx, _lib.tc_set_tuning(ctx, ctypes.byref(t)))
 
 
+def tc_selftest_barrier(ctx, timeout_ms: int = 200) -> int:
+    """Run the bounded-wait self-test; returns its status (TC_ERR_TIMEOUT when the wait ended as designed)."""
+    return _lib.tc_selftest_barrier(ctx, timeout_ms)
+
+
 def tc_arena_bytes(ctx) -> int:
     b = ctypes.c_uint64()
     _check(ctx, _lib.tc_arena_bytes(ctx, ctypes.byref(b)))
@@ -271,6 +282,14 @@ def tc_count_levels(ctx, g, levels):
     T = ctypes.c_uint64()
     st = tc_stats()
     _check(ctx, _lib.tc_count_levels(ctx, g, p, ctypes.byref(T), ctypes.byref(st)))
+    return T.value, st.to_dict()
+
+
+def tc_count_shard(ctx, g, shard: int, nshards: int):
+    """(partial T of shard `shard` of `nshards`, stats); the partials of all shards sum to T."""
+    T = ctypes.c_uint64()
+    st = tc_stats()
+    _check(ctx, _lib.tc_count_shard(ctx, g, shard, nshards, ctypes.byref(T), ctypes.byref(st)))
     return T.value, st.to_dict()
 
 

@@ -1,5 +1,6 @@
 // api.cu -- the C ABI: contexts, graphs, counting entry points.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "pipeline.cuh"
@@ -17,6 +18,15 @@ tc_status cuda_error(tc_ctx *ctx, cudaError_t e, const char *what) {
     return set_error(ctx, st, m);
 }
 
+cudaError_t device_alloc(tc_ctx *ctx, void **p, size_t bytes) {
+    ++ctx->alloc_calls;
+    if (ctx->fail_alloc_at && ctx->alloc_calls == ctx->fail_alloc_at) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;  // injected: nothing was allocated
+    }
+    return cudaMalloc(p, bytes);
+}
+
 // Grow-only device arena owned by the context.  Growing waits for the stream
 // (earlier work may still read the old buffer), then replaces the buffer.
 static tc_status reserve_in(tc_ctx *ctx, Arena &a, size_t bytes) {
@@ -28,9 +38,9 @@ static tc_status reserve_in(tc_ctx *ctx, Arena &a, size_t bytes) {
         a.cap = 0;
     }
     size_t want = bytes + bytes / 8;
-    if (cudaMalloc(&a.base, want) != cudaSuccess) {
+    if (device_alloc(ctx, (void **)&a.base, want) != cudaSuccess) {
         cudaGetLastError();
-        if (cudaMalloc(&a.base, bytes) != cudaSuccess) {
+        if (device_alloc(ctx, (void **)&a.base, bytes) != cudaSuccess) {
             cudaGetLastError();
             a.base = nullptr;
             return set_error(ctx, TC_ERR_OOM, "device arena allocation of " + std::to_string(bytes) + " bytes failed");
@@ -98,6 +108,7 @@ tc_status tc_create(tc_ctx **out, int device, const tc_options *opt) {
         return TC_ERR_INVALID;
     }
     if (!ctx->opt.max_queue) ctx->opt.max_queue = 65536;
+    if (const char *f = std::getenv("TC_FAIL_ALLOC_AT")) ctx->fail_alloc_at = std::strtoull(f, nullptr, 10);
     bool ok = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess;
     if (ok && ctx->opt.stream) {
         ctx->stream = (cudaStream_t)ctx->opt.stream;
@@ -224,8 +235,8 @@ tc_status tc_graph_from_csr(tc_ctx *ctx, uint32_t n, const uint64_t *row_ptr, co
         g->owned = false;
     } else {
         g->owned = true;
-        if (cudaMalloc(&g->rp, sizeof(uint64_t) * ((size_t)n + 1)) != cudaSuccess ||
-            cudaMalloc(&g->col, sizeof(uint32_t) * (size_t)(slots + 1)) != cudaSuccess) {
+        if (device_alloc(ctx, (void **)&g->rp, sizeof(uint64_t) * ((size_t)n + 1)) != cudaSuccess ||
+            device_alloc(ctx, (void **)&g->col, sizeof(uint32_t) * (size_t)(slots + 1)) != cudaSuccess) {
             cudaGetLastError();
             tc_graph_free(g);
             return set_error(ctx, TC_ERR_OOM, "graph allocation failed");
@@ -252,7 +263,7 @@ tc_status tc_build_csr(tc_ctx *ctx, uint32_t n, uint64_t n_tuples, const uint32_
     const uint32_t *ds = src, *dd = dst;
     uint32_t *tmp = nullptr;
     if (where == TC_HOST && n_tuples) {
-        if (cudaMalloc(&tmp, sizeof(uint32_t) * 2 * (size_t)n_tuples) != cudaSuccess) {
+        if (device_alloc(ctx, (void **)&tmp, sizeof(uint32_t) * 2 * (size_t)n_tuples) != cudaSuccess) {
             cudaGetLastError();
             return set_error(ctx, TC_ERR_OOM, "tuple upload allocation failed");
         }
@@ -337,6 +348,23 @@ tc_status tc_count_levels(tc_ctx *ctx, const tc_graph *g, uint32_t *d_levels, ui
 
 tc_status tc_count(tc_ctx *ctx, const tc_graph *g, uint64_t *triangles, tc_stats *stats) {
     return tc_count_levels(ctx, g, nullptr, triangles, stats);
+}
+
+tc_status tc_selftest_barrier(tc_ctx *ctx, uint32_t timeout_ms) {
+    if (!ctx || timeout_ms == 0 || timeout_ms > 10000) return set_error(ctx, TC_ERR_INVALID, "bad timeout");
+    DeviceGuard guard(ctx->device);
+    return selftest_barrier(ctx, timeout_ms);
+}
+
+tc_status tc_count_shard(tc_ctx *ctx, const tc_graph *g, uint32_t shard, uint32_t nshards, uint64_t *partial,
+                         tc_stats *stats) {
+    if (!ctx || nshards == 0 || shard >= nshards) return set_error(ctx, TC_ERR_INVALID, "bad shard");
+    ctx->shard = shard;
+    ctx->nshards = nshards;
+    const tc_status st = tc_count_levels(ctx, g, nullptr, partial, stats);
+    ctx->shard = 0;
+    ctx->nshards = 1;
+    return st;
 }
 
 tc_status tc_count_batch(tc_ctx *ctx, uint32_t G, const tc_graph *const *graphs, uint64_t *counts) {

@@ -279,9 +279,12 @@ tc_status build_csr_device(tc_ctx *ctx, uint32_t n, uint64_t t, const uint32_t *
         TC_CUDA(ctx, cudaMemcpyAsync(&U, pos + nk, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
         TC_CUDA(ctx, cudaStreamSynchronize(s));
     }
-    if (cudaMalloc(&rp, sizeof(uint64_t) * ((size_t)n + 1)) != cudaSuccess)
+    if (device_alloc(ctx, (void **)&rp, sizeof(uint64_t) * ((size_t)n + 1)) != cudaSuccess) {
+        cudaGetLastError();
         return set_error(ctx, TC_ERR_OOM, "tc_build_csr: row_ptr allocation failed");
-    if (cudaMalloc(&col, sizeof(uint32_t) * (size_t)(U + 1)) != cudaSuccess) {
+    }
+    if (device_alloc(ctx, (void **)&col, sizeof(uint32_t) * (size_t)(U + 1)) != cudaSuccess) {
+        cudaGetLastError();
         cudaFree(rp);
         return set_error(ctx, TC_ERR_OOM, "tc_build_csr: col allocation failed");
     }

@@ -220,20 +220,20 @@ __global__ void __launch_bounds__(1024) k_isect_warp(const uint2 *__restrict__ t
                                                      const uint64_t *__restrict__ off2,
                                                      const uint32_t *__restrict__ adj2,
                                                      const uint32_t *__restrict__ hcnt, Ctl *ctl, uint32_t table_buckets,
+                                                     unsigned long long first, unsigned long long last,
                                                      GroupSpec groups) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     uint4 *bk = reinterpret_cast<uint4 *>(smem_raw) + (size_t)warp * table_buckets;
-    const unsigned long long ntasks = ctl->n_tasks[0];
     Acc acc;
     unsigned long long build = 0, done = 0, inserts = 0;
     uint32_t cur_row = 0xFFFFFFFFu;
     BucketTable T{bk, 0, 0};
     for (;;) {
         unsigned long long k = 0;
-        if (lane == 0) k = atomicAdd(&ctl->task_next[0], 1u);
+        if (lane == 0) k = first + atomicAdd(&ctl->task_next[0], 1u);
         k = __shfl_sync(0xFFFFFFFFu, k, 0);
-        if (k >= ntasks) break;
+        if (k >= last) break;
         const uint2 task = tasks[k];
         const uint32_t u = rows[task.x], nt = ntask[task.x];
         const uint64_t ub = off2[u];
@@ -422,19 +422,19 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
                                                       const uint32_t *__restrict__ adj2,
                                                       const uint32_t *__restrict__ hcnt, Ctl *ctl, uint32_t max_v,
                                                       uint32_t table_buckets, unsigned long long chunk,
+                                                      unsigned long long first, unsigned long long last,
                                                       GroupSpec groups) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TaskSmem ts;
     const unsigned lane = lane_id();
     const SliceSmem S = carve_slice(smem_raw, max_v);
     uint4 *bk = reinterpret_cast<uint4 *>(smem_raw + slice_smem_bytes(max_v));
-    const unsigned long long ntasks = ctl->n_tasks[1];
     Acc acc;
     unsigned long long build = 0, done = 0, inserts = 0;
     uint32_t cur_row = 0xFFFFFFFFu;
     BucketTable T{bk, 0, 0};
     init_task_smem(&ts);
-    while (next_task(ctl, 1, 0, ntasks, chunk, tasks, &ts)) {
+    while (next_task(ctl, 1, first, last, chunk, tasks, &ts)) {
         const uint2 task = ts.task;
         const uint32_t u = rows[task.x], nt = ntask[task.x];
         const uint64_t ub = off2[u];
@@ -566,37 +566,48 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
     const Tuning &tu = ctx->tune;
     const Ctl &h = *ctx->h_ctl;  // pulled after planning
     // ev[4..7] bracket the warp, block and hub kernels
+    // this count's share of every class's task list (all of it unless sharded)
+    auto share = [&](unsigned long long total, unsigned long long *lo, unsigned long long *hi) {
+        *lo = total * ctx->shard / ctx->nshards;
+        *hi = total * (ctx->shard + 1) / ctx->nshards;
+    };
+    unsigned long long lo0, hi0, lo1, hi1, lo2, hi2;
+    share(h.n_tasks[0], &lo0, &hi0);
+    share(h.n_tasks[1], &lo1, &hi1);
+    share(h.n_tasks[2], &lo2, &hi2);
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[4], s));
-    if (h.n_tasks[0]) {
+    if (hi0 > lo0) {
         const size_t smem = warp_kernel_smem(tu);
         TC_CUDA(ctx, cudaFuncSetAttribute(k_isect_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
         TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect_warp, 32 * tu.warps_per_block, smem));
         if (per_sm < 1) per_sm = 1;
         uint64_t grid = (uint64_t)ctx->num_sms * per_sm;
-        const uint64_t need = (h.n_tasks[0] + tu.warps_per_block - 1) / tu.warps_per_block;
+        const uint64_t need = (hi0 - lo0 + tu.warps_per_block - 1) / tu.warps_per_block;
         if (grid > need) grid = need;
-        k_isect_warp<<<(unsigned)grid, 32 * tu.warps_per_block, smem, s>>>(
-            b.tasks[0], b.rows[0], b.ntask[0], b.off2, b.adj2, b.hcnt, ctx->d_ctl, warp_table_buckets(tu), b.groups);
+        k_isect_warp<<<(unsigned)grid, 32 * tu.warps_per_block, smem, s>>>(b.tasks[0], b.rows[0], b.ntask[0], b.off2,
+                                                                            b.adj2, b.hcnt, ctx->d_ctl,
+                                                                            warp_table_buckets(tu), lo0, hi0, b.groups);
         note_launch(ctx);
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[5], s));
-    if (h.n_tasks[1]) {
+    if (hi1 > lo1) {
         const size_t smem = block_kernel_smem(tu);
         TC_CUDA(ctx, cudaFuncSetAttribute(k_isect_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
         TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect_block, tu.block_threads, smem));
         if (per_sm < 1) per_sm = 1;
         uint64_t grid = (uint64_t)ctx->num_sms * per_sm;
-        if (grid > h.n_tasks[1]) grid = h.n_tasks[1];
-        const unsigned long long chunk = std::max<unsigned long long>(1, h.n_tasks[1] / (grid * 8));
+        if (grid > hi1 - lo1) grid = hi1 - lo1;
+        const unsigned long long chunk = std::max<unsigned long long>(1, (hi1 - lo1) / (grid * 8));
         k_isect_block<<<(unsigned)grid, tu.block_threads, smem, s>>>(b.tasks[1], b.rows[1], b.ntask[1], b.off2, b.adj2,
                                                                      b.hcnt, ctx->d_ctl, tu.max_v,
-                                                                     block_table_buckets(tu), chunk, b.groups);
+                                                                     block_table_buckets(tu), chunk, lo1, hi1,
+                                                                     b.groups);
         note_launch(ctx);
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[6], s));
-    const uint32_t nh = h.n_rows[2];
+    const uint32_t nh = hi2 > lo2 ? h.n_rows[2] : 0;
     if (nh) {
         // task ranges of the hub rows: the host walks the groups
         std::vector<unsigned long long> pref(nh + 1);
@@ -609,11 +620,13 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         if (per_sm < 1) per_sm = 1;
         for (uint32_t i0 = 0; i0 < nh; i0 += tu.hub_group) {
             const uint32_t g = std::min<uint32_t>(tu.hub_group, nh - i0);
+            const unsigned long long first = std::max<unsigned long long>(pref[i0], lo2);
+            const unsigned long long last = std::min<unsigned long long>(pref[i0 + g], hi2);
+            if (first >= last) continue;  // none of this group's tasks is in this shard
             TC_CUDA(ctx, cudaMemsetAsync(b.hub_bits, 0, 4ull * b.hub_words * g, s));
             TC_CUDA(ctx, cudaMemsetAsync(&ctx->d_ctl->task_next[2], 0, sizeof(unsigned), s));
             k_hub_set<<<(unsigned)ctx->num_sms * 4u, 256, 0, s>>>(b.rows[2], i0, g, b.off2, b.adj2, b.hub_bits,
                                                                  b.hub_words);
-            const unsigned long long first = pref[i0], last = pref[i0 + g];
             uint64_t grid = (uint64_t)ctx->num_sms * per_sm;
             if (grid > last - first) grid = last - first;
             const unsigned long long chunk = std::max<unsigned long long>(1, (last - first) / (grid * 4));
@@ -625,7 +638,7 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         }
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[7], s));
-    ctx->isect_flags = (h.n_tasks[0] ? 1u : 0u) | (h.n_tasks[1] ? 2u : 0u) | (nh ? 4u : 0u);
+    ctx->isect_flags = (hi0 > lo0 ? 1u : 0u) | (hi1 > lo1 ? 2u : 0u) | (nh ? 4u : 0u);
     TC_CUDA(ctx, cudaGetLastError());
     return TC_OK;
 }

@@ -296,9 +296,10 @@ __global__ void k_after_level(Ctl *ctl, int nxt, uint32_t level) {
 }
 
 // Grid-wide barrier for the persistent BFS (all blocks are co-resident: the
-// kernel is launched cooperatively).  Sense by generation counter; the wait
-// gives up after ~2 s of clock time, raises the error flag and returns false.
-__device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned nblocks) {
+// kernel is launched cooperatively).  Sense by generation counter; a wait
+// gives up after `timeout_cycles` of clock time, raises the error flag and
+// returns false, so the kernel ends and the host reads TC_ERR_TIMEOUT.
+__device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned nblocks, long long timeout_cycles) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -313,7 +314,7 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned nblocks) {
         } else {
             const long long t0 = clock64();
             while (*gen == g) {
-                if (clock64() - t0 > 4000000000ll) {  // ~2 s at 2 GHz
+                if (clock64() - t0 > timeout_cycles) {
                     ctl->error = 4;
                     ok = 0;
                     break;
@@ -376,7 +377,7 @@ __global__ void __launch_bounds__(512) k_bfs_persist(uint32_t *__restrict__ q0, 
         }
         edges = warp_sum(edges);
         if (lane == 0 && edges) atomicAdd(&ctl->fr_edges[s1], edges);
-        if (!grid_barrier(ctl, gridDim.x)) return;
+        if (!grid_barrier(ctl, gridDim.x, 4000000000ll)) return;  // ~2 s at 2 GHz
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             const uint32_t c = vcount[s1];
             ctl->visited += c;
@@ -392,6 +393,12 @@ __global__ void __launch_bounds__(512) k_bfs_persist(uint32_t *__restrict__ q0, 
         ctl->p_queue = queue;
         ctl->p_level = level;
     }
+}
+
+// Self-test of the bounded wait: the barrier expects one more block than the
+// grid has, so no generation change ever comes and every block times out.
+__global__ void k_barrier_selftest(Ctl *ctl, long long timeout_cycles) {
+    grid_barrier(ctl, gridDim.x + 1, timeout_cycles);
 }
 
 unsigned grid_for(uint64_t work, unsigned threads, unsigned cap) {
@@ -489,6 +496,19 @@ static tc_status bfs_loop(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t s
         ++level;
     }
     return TC_OK;
+}
+
+tc_status selftest_barrier(tc_ctx *ctx, uint32_t timeout_ms) {
+    cudaStream_t s = ctx->stream;
+    TC_CUDA(ctx, cudaMemsetAsync(ctx->d_ctl, 0, sizeof(Ctl), s));
+    Ctl *ctl = ctx->d_ctl;
+    long long cycles = (long long)timeout_ms * 2000000ll;  // clock64 ticks at about 2 GHz
+    void *args[] = {&ctl, &cycles};
+    TC_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_barrier_selftest, dim3(ctx->num_sms), dim3(64), args, 0, s));
+    tc_status st = pull_ctl(ctx);
+    if (st != TC_OK) return st;
+    if (ctx->h_ctl->error == 4) return set_error(ctx, TC_ERR_TIMEOUT, "device wait timed out (self-test)");
+    return set_error(ctx, TC_ERR_CUDA, "self-test barrier did not time out");
 }
 
 tc_status compute_levels(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t slots) {

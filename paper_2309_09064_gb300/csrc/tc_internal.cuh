@@ -111,6 +111,9 @@ struct tc_ctx {
     cudaEvent_t ev[8] = {};
     uint32_t launches = 0;    // kernels launched by the current call
     uint32_t isect_flags = 0; // which intersection kernels the last count launched (1 warp, 2 block, 4 hub)
+    uint32_t shard = 0, nshards = 1;  // intersection tasks of this count: share `shard` of `nshards`
+    uint64_t alloc_calls = 0;         // device allocations made by this context
+    uint64_t fail_alloc_at = 0;       // fault injection: fail this allocation (1-based; 0 = never)
     std::string err;
     ServeState *serve = nullptr;
 };
@@ -121,6 +124,8 @@ namespace tc {
 tc_status set_error(tc_ctx *ctx, tc_status st, const std::string &msg);
 tc_status cuda_error(tc_ctx *ctx, cudaError_t e, const char *what);
 tc_status arena_reserve(tc_ctx *ctx, size_t bytes);
+// cudaMalloc through the context (counts calls; honours the injected failure).
+cudaError_t device_alloc(tc_ctx *ctx, void **p, size_t bytes);
 
 // Launch bookkeeping: every kernel launch site calls this once per launch.
 inline void note_launch(tc_ctx *ctx, uint32_t k = 1) { ctx->launches += k; }

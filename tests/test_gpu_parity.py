@@ -316,3 +316,65 @@ def test_autotuner_keeps_counts_and_sets_a_valid_tuning(tc, tmp_path):
             tc.tc_graph_free(g)
     finally:
         tc.tc_destroy(c)
+
+
+@pytest.mark.parametrize("nshards", [1, 2, 3, 8])
+def test_shards_sum_to_the_count(tc, ctx, nshards):
+    for graph in (gg.rmat(14, 16, seed=2), two_hub_graph(), SMALL["union"]):
+        g = tc.tc_build_csr(ctx, *graph[:3])
+        T, _ = tc.tc_count(ctx, g)
+        parts = [tc.tc_count_shard(ctx, g, k, nshards)[0] for k in range(nshards)]
+        tc.tc_graph_free(g)
+        assert sum(parts) == T
+
+
+def test_bounded_device_wait_times_out_and_context_survives(tc):
+    c = tc.tc_create(0)
+    try:
+        assert tc.tc_selftest_barrier(c, 200) == tc.TC_ERR_TIMEOUT
+        g = tc.tc_build_csr(c, *SMALL["rmat10"])
+        T, _ = tc.tc_count(c, g)  # the context still works
+        rp, col = oracle.build_csr(*SMALL["rmat10"])
+        assert T == oracle.count_definition(rp, col)
+        tc.tc_graph_free(g)
+    finally:
+        tc.tc_destroy(c)
+
+
+def test_injected_allocation_failure_is_reported_and_recovered(tc, monkeypatch):
+    monkeypatch.setenv("TC_FAIL_ALLOC_AT", "1")
+    c = tc.tc_create(0)  # the variable is read here
+    monkeypatch.delenv("TC_FAIL_ALLOC_AT")
+    try:
+        n, s, d = SMALL["rmat10"]
+        rp, col = oracle.build_csr(n, s, d)
+        with pytest.raises(tc.TcError) as e:
+            tc.tc_graph_from_csr(c, rp, col)  # its first allocation fails
+        assert e.value.status == tc.TC_ERR_OOM
+        g = tc.tc_graph_from_csr(c, rp, col)  # the next one succeeds
+        assert tc.tc_count(c, g)[0] == oracle.count_definition(rp, col)
+        tc.tc_graph_free(g)
+    finally:
+        tc.tc_destroy(c)
+
+
+def test_queue_full_reports_busy(tc):
+    c = tc.tc_create(0, max_queue=4)
+    try:
+        g = tc.tc_build_csr(c, *gg.rmat(12, 16, seed=9))
+        want = tc.tc_count(c, g)[0]
+        tickets, busy = [], 0
+        for _ in range(2000):
+            try:
+                tickets.append(tc.tc_submit(c, g))
+            except tc.TcError as e:
+                assert e.status == tc.TC_ERR_BUSY
+                busy += 1
+        assert busy > 0
+        for t in tickets:
+            while (r := tc.tc_poll(c, t)) is None:
+                pass
+            assert r == want
+        tc.tc_graph_free(g)
+    finally:
+        tc.tc_destroy(c)
