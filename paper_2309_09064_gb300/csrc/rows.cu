@@ -145,25 +145,20 @@ __global__ void k_row_fill(uint32_t n, const uint64_t *__restrict__ rp, const ui
 // Rows with at least one oriented horizontal edge are the hashed side of the
 // intersections; split them by the size s(u) of their compacted row:
 // class 0 (warp) s <= warp_cap, class 1 (block) s <= block_cap, class 2 (hub).
-__global__ void k_classify(uint32_t n, const uint32_t *__restrict__ hcnt, const uint32_t *__restrict__ scnt,
-                           uint32_t *__restrict__ r0, uint32_t *__restrict__ r1, uint32_t *__restrict__ r2, Ctl *ctl,
-                           uint32_t warp_cap, uint32_t block_cap) {
+// The lists are built by a stable scan, so they (and the task lists made from
+// them) are in vertex order on every run: shards of a count agree on them.
+__global__ void k_class_flags(uint32_t n, const uint32_t *__restrict__ hcnt, const uint32_t *__restrict__ scnt,
+                              uint32_t *__restrict__ cls, Ctl *ctl, uint32_t warp_cap, uint32_t block_cap) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t n_round = ((uint64_t)n + 31) & ~uint64_t(31);
     unsigned my_max = 0;
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_round; x += stride) {
-        const bool active = x < n && hcnt[x] > 0;
-        const uint32_t s = active ? scnt[x] : 0;
-        const bool c0 = active && s <= warp_cap;
-        const bool c1 = active && s > warp_cap && s <= block_cap;
-        const bool c2 = active && s > block_cap;
-        const uint32_t p0 = warp_append(c0, &ctl->n_rows[0]);
-        const uint32_t p1 = warp_append(c1, &ctl->n_rows[1]);
-        const uint32_t p2 = warp_append(c2, &ctl->n_rows[2]);
-        if (c0) r0[p0] = (uint32_t)x;
-        if (c1) r1[p1] = (uint32_t)x;
-        if (c2) r2[p2] = (uint32_t)x;
-        if (c1 || c2) my_max = s > my_max ? s : my_max;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
+        uint32_t c = 3;  // no oriented horizontal edge: not a hashed row
+        if (hcnt[x] > 0) {
+            const uint32_t s = scnt[x];
+            c = s <= warp_cap ? 0u : (s <= block_cap ? 1u : 2u);
+            if (c) my_max = s > my_max ? s : my_max;
+        }
+        cls[x] = c;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -171,6 +166,20 @@ __global__ void k_classify(uint32_t n, const uint32_t *__restrict__ hcnt, const 
         my_max = y > my_max ? y : my_max;
     }
     if (lane_id() == 0 && my_max) atomicMax(&ctl->max_s2, my_max);
+}
+
+__global__ void k_class_indicator(uint32_t n, const uint32_t *__restrict__ cls, uint32_t c, uint32_t *__restrict__ ind) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) ind[x] = cls[x] == c;
+}
+
+__global__ void k_class_scatter(uint32_t n, const uint32_t *__restrict__ cls, uint32_t c,
+                                const unsigned long long *__restrict__ pos, uint32_t *__restrict__ rows,
+                                unsigned int *__restrict__ n_rows) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride)
+        if (cls[x] == c) rows[pos[x]] = (uint32_t)x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *n_rows = (unsigned int)pos[n];
 }
 
 // Split every hashed row u of class c into tasks (contiguous slices of H(u))
@@ -240,9 +249,16 @@ tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n) {
     k_row_count<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.rp, b.col, b.deg, b.L, b.hcnt, b.scnt, ctx->d_ctl, order);
     uint32_t launches = 1 + scan_u32_to_u64(b.scnt, b.off2, n, b.scan_tmp, s);
     k_row_fill<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.rp, b.col, b.deg, b.L, b.hcnt, b.off2, b.adj2, order);
-    k_classify<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.hcnt, b.scnt, b.rows[0], b.rows[1], b.rows[2], ctx->d_ctl,
-                                                     tu.warp_cap, tu.block_cap);
+    // fdeg and R are free after the levels: class of every vertex, 0/1 indicator
+    k_class_flags<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.hcnt, b.scnt, b.fdeg, ctx->d_ctl, tu.warp_cap,
+                                                        tu.block_cap);
     launches += 2;
+    for (uint32_t c = 0; c < 3; ++c) {
+        k_class_indicator<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.fdeg, c, b.R);
+        launches += 2 + scan_u32_to_u64(b.R, b.fpref, n, b.scan_tmp, s);
+        k_class_scatter<<<grid_for(n, 256, cap), 256, 0, s>>>(
+            n, b.fdeg, c, reinterpret_cast<const unsigned long long *>(b.fpref), b.rows[c], &ctx->d_ctl->n_rows[c]);
+    }
     const uint32_t work[3] = {tu.warp_task_work, tu.task_work, tu.hub_task_work};
     const uint32_t mult[3] = {1, 2, 2};
     const uint32_t maxv[3] = {0xFFFFFFFFu, tu.max_v, tu.max_v};
