@@ -93,7 +93,7 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     st = compute_levels(ctx, b, n, g.slots);
     if (st != TC_OK) return st;
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[1], s));
-    st = build_rows(ctx, b, n);
+    st = build_rows(ctx, b, n, g.max_deg);
     if (st != TC_OK) return st;
     st = pull(ctx);  // row counts per class
     if (st != TC_OK) return st;

@@ -42,6 +42,7 @@ struct Acc {
 // sits in the first bucket, from its home, that had room when it was inserted.
 struct BucketTable {
     static constexpr int kUnroll = 8;  // row ids in flight per lane
+    static constexpr int kBatch = 4;   // lookups resolved together
     uint4 *bk;
     uint32_t shift, mask;  // home bucket = hash >> shift; mask = buckets - 1
 };
@@ -84,6 +85,7 @@ __device__ __forceinline__ uint32_t filter_bit(uint32_t w, uint32_t fshift) { re
 
 struct HubSet {
     static constexpr int kUnroll = 8;  // row ids in flight per lane
+    static constexpr int kBatch = 8;   // prefilter tests, then all bitmap loads together
     const uint32_t *filter;  // shared
     const uint32_t *bits;    // global, read-only while probing
     uint32_t fshift;         // 32 - hub_filter_log2
@@ -160,7 +162,7 @@ __device__ __forceinline__ void lookup_batch(const HubSet &H, const uint32_t (&w
 // Probe positions [j_lo, j_hi) of row(v) = adj2[b ..] with one warp, lanes
 // striding over the positions with U loads in flight each.  Position j < hv
 // is the G0 part (a triangle inside G0), the rest the G1 part (a cross-level
-// triangle).  Lookups are resolved in halves of U/2 to bound registers.
+// triangle).  Lookups are resolved Set::kBatch at a time (registers).
 template <int U, class Set>
 __device__ __forceinline__ void probe_row(const Set &set, const uint32_t *__restrict__ adj2, unsigned long long b,
                                           uint32_t j_lo, uint32_t j_hi, uint32_t hv, Acc &acc) {
@@ -174,15 +176,16 @@ __device__ __forceinline__ void probe_row(const Set &set, const uint32_t *__rest
             const uint32_t j = j0 + (uint32_t)i * 32u + lane;
             w[i] = j < j_hi ? __ldg(row + j) : kEmpty;
         }
+        constexpr int B = Set::kBatch;
 #pragma unroll
-        for (int half = 0; half < U; half += U / 2) {
-            uint32_t ww[U / 2];
-            bool hit[U / 2];
+        for (int half = 0; half < U; half += B) {
+            uint32_t ww[B];
+            bool hit[B];
 #pragma unroll
-            for (int i = 0; i < U / 2; ++i) ww[i] = w[half + i];
+            for (int i = 0; i < B; ++i) ww[i] = w[half + i];
             lookup_batch(set, ww, hit);
 #pragma unroll
-            for (int i = 0; i < U / 2; ++i) hits.add(hit[i], j0 + (uint32_t)(half + i) * 32u + lane, hv);
+            for (int i = 0; i < B; ++i) hits.add(hit[i], j0 + (uint32_t)(half + i) * 32u + lane, hv);
         }
     }
     hits.flush(acc);

@@ -42,7 +42,7 @@ struct PipeBufs {
 tc_status compute_levels(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t slots);
 tc_status selftest_barrier(tc_ctx *ctx, uint32_t timeout_ms);
 // partition, orientation, compaction, classification and per-class task counts
-tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n);
+tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_deg);
 // scans of the per-class task counts (after the host has read the row counts)
 tc_status plan_scans(tc_ctx *ctx, const PipeBufs &b);
 // task emission (after the host knows the task totals)

@@ -21,19 +21,45 @@ namespace {
 // at a time (lanes stride over the row, ballots keep the order).
 constexpr uint32_t kSmallRow = 32;
 
-__device__ __forceinline__ bool is_h(uint32_t x, uint32_t dx, uint32_t lx, uint32_t y, const uint32_t *__restrict__ L,
-                                     const uint32_t *__restrict__ deg, uint32_t order, bool *is_g) {
-    const uint32_t ly = L[y];
+// Level and degree of a neighbour, either from the two arrays or from one
+// packed word (level << 24 | degree) when every level is < 255 and every
+// degree < 2^24: one random 4-byte read instead of two.
+struct LevelDeg {
+    const uint32_t *L, *deg, *packed;
+    __device__ __forceinline__ void get(uint32_t y, uint32_t &ly, uint32_t &dy) const {
+        if (packed) {
+            const uint32_t p = packed[y];
+            ly = p >> 24;
+            dy = p & 0xFFFFFFu;
+        } else {
+            ly = L[y];
+            dy = 0xFFFFFFFFu;  // loaded on demand
+        }
+    }
+    __device__ __forceinline__ uint32_t degree(uint32_t y, uint32_t dy) const { return packed ? dy : deg[y]; }
+};
+
+__device__ __forceinline__ bool is_h(uint32_t x, uint32_t dx, uint32_t lx, uint32_t y, const LevelDeg &ld,
+                                     uint32_t order, bool *is_g) {
+    uint32_t ly, dy;
+    ld.get(y, ly, dy);
     if (ly != lx) {
         *is_g = true;
         return false;
     }
     *is_g = false;
-    return precedes(x, dx, y, deg[y], order);
+    return precedes(x, dx, y, ld.degree(y, dy), order);
+}
+
+__global__ void k_pack_level_deg(uint32_t n, const uint32_t *__restrict__ L, const uint32_t *__restrict__ deg,
+                                 uint32_t *__restrict__ packed) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        packed[v] = (L[v] << 24) | deg[v];
 }
 
 __global__ void k_row_count(uint32_t n, const uint64_t *__restrict__ rp, const uint32_t *__restrict__ col,
-                            const uint32_t *__restrict__ deg, const uint32_t *__restrict__ L,
+                            const uint32_t *__restrict__ deg, const uint32_t *__restrict__ L, LevelDeg ld,
                             uint32_t *__restrict__ hcnt, uint32_t *__restrict__ scnt, Ctl *ctl, uint32_t order) {
     __shared__ unsigned long long s_e0;
     if (threadIdx.x == 0) s_e0 = 0;
@@ -51,7 +77,7 @@ __global__ void k_row_count(uint32_t n, const uint64_t *__restrict__ rp, const u
         if (dx <= kSmallRow) {
             for (uint32_t j = 0; j < dx; ++j) {
                 bool isg;
-                if (is_h((uint32_t)x, dx, lx, col[b + j], L, deg, order, &isg)) ++h;
+                if (is_h((uint32_t)x, dx, lx, col[b + j], ld, order, &isg)) ++h;
                 g += isg;
             }
         }
@@ -66,7 +92,7 @@ __global__ void k_row_count(uint32_t n, const uint64_t *__restrict__ rp, const u
             uint32_t hh = 0, gg = 0;
             for (uint32_t j = lane; j < bd; j += 32) {
                 bool isg;
-                if (is_h(bx, bd, bl, col[bb + j], L, deg, order, &isg)) ++hh;
+                if (is_h(bx, bd, bl, col[bb + j], ld, order, &isg)) ++hh;
                 gg += isg;
             }
             hh = warp_sum(hh);
@@ -89,7 +115,7 @@ __global__ void k_row_count(uint32_t n, const uint64_t *__restrict__ rp, const u
 }
 
 __global__ void k_row_fill(uint32_t n, const uint64_t *__restrict__ rp, const uint32_t *__restrict__ col,
-                           const uint32_t *__restrict__ deg, const uint32_t *__restrict__ L,
+                           const uint32_t *__restrict__ deg, const uint32_t *__restrict__ L, LevelDeg ld,
                            const uint32_t *__restrict__ hcnt, const uint64_t *__restrict__ off2,
                            uint32_t *__restrict__ adj2, uint32_t order) {
     const unsigned lane = lane_id();
@@ -108,7 +134,7 @@ __global__ void k_row_fill(uint32_t n, const uint64_t *__restrict__ rp, const ui
             for (uint32_t j = 0; j < dx; ++j) {
                 const uint32_t y = col[b + j];
                 bool isg;
-                if (is_h((uint32_t)x, dx, lx, y, L, deg, order, &isg)) adj2[base + hp++] = y;
+                if (is_h((uint32_t)x, dx, lx, y, ld, order, &isg)) adj2[base + hp++] = y;
                 else if (isg) adj2[base + hx + gp++] = y;
             }
         }
@@ -129,7 +155,7 @@ __global__ void k_row_fill(uint32_t n, const uint64_t *__restrict__ rp, const ui
                 uint32_t y = 0;
                 if (j < bd) {
                     y = col[bb + j];
-                    isH = is_h(bx, bd, bl, y, L, deg, order, &isG);
+                    isH = is_h(bx, bd, bl, y, ld, order, &isG);
                 }
                 const unsigned mh = __ballot_sync(0xFFFFFFFFu, isH);
                 const unsigned mg = __ballot_sync(0xFFFFFFFFu, isG);
@@ -240,15 +266,24 @@ unsigned grid_for(uint64_t work, unsigned threads, unsigned cap) {
 
 }  // namespace
 
-tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n) {
+tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_deg) {
     cudaStream_t s = ctx->stream;
     const unsigned cap = (unsigned)ctx->num_sms * 16u;
     const uint32_t order = ctx->opt.order;
     const Tuning &tu = ctx->tune;
     if (n == 0) return TC_OK;
-    k_row_count<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.rp, b.col, b.deg, b.L, b.hcnt, b.scnt, ctx->d_ctl, order);
-    uint32_t launches = 1 + scan_u32_to_u64(b.scnt, b.off2, n, b.scan_tmp, s);
-    k_row_fill<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.rp, b.col, b.deg, b.L, b.hcnt, b.off2, b.adj2, order);
+    // pack (level, degree) into one word when both fit (q0 is free after the levels)
+    LevelDeg ld{b.L, b.deg, nullptr};
+    uint32_t launches = 0;
+    if (ctx->h_ctl->max_level < 255 && max_deg < (1u << 24)) {
+        k_pack_level_deg<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.L, b.deg, b.q0);
+        ld.packed = b.q0;
+        ++launches;
+    }
+    k_row_count<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.rp, b.col, b.deg, b.L, ld, b.hcnt, b.scnt, ctx->d_ctl,
+                                                      order);
+    launches += 1 + scan_u32_to_u64(b.scnt, b.off2, n, b.scan_tmp, s);
+    k_row_fill<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.rp, b.col, b.deg, b.L, ld, b.hcnt, b.off2, b.adj2, order);
     // fdeg and R are free after the levels: class of every vertex, 0/1 indicator
     k_class_flags<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.hcnt, b.scnt, b.fdeg, ctx->d_ctl, tu.warp_cap,
                                                         tu.block_cap);
