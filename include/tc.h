@@ -96,12 +96,13 @@ typedef struct tc_stats {
     float ms_levels;            /* degrees + BFS levels */
     float ms_mark;              /* partition, orientation, compaction, planning */
     float ms_isect;             /* intersections + reduction */
-    /* intersection classes: [0] warp, [1] block (shared table), [2] hub (global table) */
-    uint64_t class_rows[3];     /* hashed rows u (warp) or tasks (block, hub) */
-    uint64_t class_probes[3];   /* probed elements */
-    uint64_t class_bytes[3];    /* algorithmic bytes: hashed rows once + probed rows */
-    float ms_class[3];          /* device time of each class's kernel (0 if not launched) */
-    uint64_t class_inserts[3];  /* table / prefilter inserts done, rebuilds on other blocks included */
+    /* intersection classes: [0] warp (shared table per warp), [1] block (shared table), [2] hub (L2
+       bitmaps + shared prefilter), [3] tiny (thread-per-row sorted merges) */
+    uint64_t class_rows[4];     /* tasks (warp, block, hub) or rows (tiny) */
+    uint64_t class_probes[4];   /* probed elements */
+    uint64_t class_bytes[4];    /* algorithmic bytes: hashed rows once + probed rows */
+    float ms_class[4];          /* device time of each class's kernel (0 if not launched) */
+    uint64_t class_inserts[4];  /* table / prefilter inserts done, rebuilds on other blocks included */
     uint32_t launches;          /* kernels this call launched */
     uint32_t reserved;
 } tc_stats;
@@ -123,7 +124,10 @@ typedef struct tc_tuning {
     uint32_t hub_group;        /* hub rows probed per launch, one n-bit bitmap each (1..64) */
     uint32_t hub_filter_log2;  /* hub prefilter size: 2^k bits of shared memory (10..20) */
     uint32_t hub_threads;      /* hub kernel threads (64..1024, multiple of 32) */
-    uint32_t reserved[5];
+    uint32_t tiny_cap;         /* s(u) <= tiny_cap (and degree <= 4 tiny_cap): one thread per row, sorted
+                                  merges instead of a table; takes precedence over the classes above
+                                  (0..64; 0 turns it off) */
+    uint32_t reserved[4];
 } tc_tuning;
 
 /* ------------------------------------------------------------------ context */

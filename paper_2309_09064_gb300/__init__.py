@@ -56,8 +56,8 @@ class tc_options(ctypes.Structure):
 class tc_tuning(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint32) for k in (
         "warp_cap", "block_cap", "task_work", "warps_per_block", "block_threads", "warp_task_work",
-        "hub_task_work", "max_v", "hub_group", "hub_filter_log2", "hub_threads")] + [
-        ("reserved", ctypes.c_uint32 * 5)]
+        "hub_task_work", "max_v", "hub_group", "hub_filter_log2", "hub_threads", "tiny_cap")] + [
+        ("reserved", ctypes.c_uint32 * 4)]
 
     def to_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -68,9 +68,9 @@ class tc_stats(ctypes.Structure):
         "n", "m", "triangles", "t_same", "t_cross", "horizontal_edges", "levels", "components", "probes",
         "row2_slots", "alg_bytes", "isect_bytes")] + [(k, ctypes.c_float) for k in (
             "ms_total", "ms_levels", "ms_mark", "ms_isect")] + [
-        ("class_rows", ctypes.c_uint64 * 3), ("class_probes", ctypes.c_uint64 * 3),
-        ("class_bytes", ctypes.c_uint64 * 3), ("ms_class", ctypes.c_float * 3),
-        ("class_inserts", ctypes.c_uint64 * 3),
+        ("class_rows", ctypes.c_uint64 * 4), ("class_probes", ctypes.c_uint64 * 4),
+        ("class_bytes", ctypes.c_uint64 * 4), ("ms_class", ctypes.c_float * 4),
+        ("class_inserts", ctypes.c_uint64 * 4),
         ("launches", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
     def to_dict(self):

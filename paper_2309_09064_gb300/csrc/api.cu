@@ -118,7 +118,7 @@ tc_status tc_create(tc_ctx **out, int device, const tc_options *opt) {
     }
     ok = ok && cudaMalloc(&ctx->d_ctl, sizeof(Ctl)) == cudaSuccess;
     ok = ok && cudaMallocHost(&ctx->h_ctl, sizeof(Ctl)) == cudaSuccess;
-    for (int i = 0; ok && i < 8; ++i) ok = cudaEventCreate(&ctx->ev[i]) == cudaSuccess;
+    for (int i = 0; ok && i < 10; ++i) ok = cudaEventCreate(&ctx->ev[i]) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         tc_destroy(ctx);
@@ -137,7 +137,7 @@ tc_status tc_destroy(tc_ctx *ctx) {
     if (ctx->batch_arena.base) cudaFree(ctx->batch_arena.base);
     if (ctx->d_ctl) cudaFree(ctx->d_ctl);
     if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 10; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
@@ -174,6 +174,7 @@ tc_status tc_get_tuning(const tc_ctx *ctx, tc_tuning *out) {
     out->hub_group = t.hub_group;
     out->hub_filter_log2 = t.hub_filter_log2;
     out->hub_threads = t.hub_threads;
+    out->tiny_cap = t.tiny_cap;
     return TC_OK;
 }
 
@@ -191,13 +192,14 @@ tc_status tc_set_tuning(tc_ctx *ctx, const tc_tuning *t) {
     nt.hub_group = t->hub_group;
     nt.hub_filter_log2 = t->hub_filter_log2;
     nt.hub_threads = t->hub_threads;
+    nt.tiny_cap = t->tiny_cap;
     const size_t smem_limit = 227 * 1024;
     auto threads_ok = [](uint32_t x) { return x >= 64 && x <= 1024 && x % 32 == 0; };
     if (nt.warp_cap < 1 || nt.warp_cap > 4096 || nt.block_cap < nt.warp_cap || nt.block_cap > 16384 ||
         nt.task_work < 1 || nt.warp_task_work < 1 || nt.hub_task_work < 1 || nt.warps_per_block < 1 ||
         nt.warps_per_block > 32 || !threads_ok(nt.block_threads) || !threads_ok(nt.hub_threads) || nt.max_v < 64 ||
         nt.max_v > 4096 || nt.hub_group < 1 || nt.hub_group > 64 || nt.hub_filter_log2 < 10 ||
-        nt.hub_filter_log2 > 20 || warp_kernel_smem(nt) > smem_limit || block_kernel_smem(nt) > smem_limit ||
+        nt.hub_filter_log2 > 20 || nt.tiny_cap > 64 || warp_kernel_smem(nt) > smem_limit || block_kernel_smem(nt) > smem_limit ||
         hub_kernel_smem(nt) > smem_limit)
         return set_error(ctx, TC_ERR_INVALID, "tuning out of range");
     ctx->tune = nt;

@@ -28,7 +28,7 @@ size_t pipeline_bytes(const tc_ctx *ctx, uint32_t n, uint64_t slots, uint32_t ma
     auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t n1 = (size_t)n + 1;
     size_t bytes = 0;
-    bytes += 14 * r(4 * n1);                       // deg q0 q1 fdeg R parent hcnt scnt rows[3] ntask[3]
+    bytes += 15 * r(4 * n1);                       // deg q0 q1 fdeg R parent hcnt scnt rows[4] ntask[3]
     if (own_levels) bytes += r(4 * n1);            // L
     bytes += 5 * r(8 * n1);                        // fpref off2 tpref[3]
     bytes += r(4 * (slots + 1));                   // adj2
@@ -69,6 +69,8 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     b.hcnt = a.take<uint32_t>(n1);
     b.scnt = a.take<uint32_t>(n1);
     bool ok = b.deg && b.L && b.q0 && b.q1 && b.fdeg && b.R && b.parent && b.hcnt && b.scnt;
+    b.rows[3] = a.take<uint32_t>(n1);
+    ok = ok && b.rows[3];
     for (int c = 0; c < 3; ++c) {
         b.rows[c] = a.take<uint32_t>(n1);
         b.ntask[c] = a.take<uint32_t>(n1);
@@ -144,14 +146,18 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
         const uint64_t lv = 8 * N1 + 4 * S + 4 * S + 4ull * n;
         const uint64_t rw = 8 * N1 + 4 * S + 8 * S + 4 * row2 + 16 * N1;
         uint64_t is = 0;
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < 4; ++c) {
             stats->class_rows[c] = h.cls_rows[c];
             stats->class_probes[c] = h.cls_probes[c];
             stats->class_bytes[c] = 4ull * (h.cls_build[c] + h.cls_probes[c]);
             stats->class_inserts[c] = h.cls_inserts[c];
             is += stats->class_bytes[c];
             stats->ms_class[c] = 0.f;
-            if (ctx->isect_flags & (1u << c)) cudaEventElapsedTime(&stats->ms_class[c], ctx->ev[4 + c], ctx->ev[5 + c]);
+            // events: ev[4..7] bracket the warp, block and hub kernels, ev[8..9] the tiny one
+            if (ctx->isect_flags & (1u << c)) {
+                if (c < 3) cudaEventElapsedTime(&stats->ms_class[c], ctx->ev[4 + c], ctx->ev[5 + c]);
+                else cudaEventElapsedTime(&stats->ms_class[3], ctx->ev[8], ctx->ev[9]);
+            }
         }
         stats->launches = ctx->launches;
         stats->reserved = 0;

@@ -200,7 +200,7 @@ __device__ __forceinline__ uint32_t group_of(const GroupSpec &g, uint32_t u) {
     return a;
 }
 
-// Reduce a warp's counters into the control block (class c: 0 warp, 1 block, 2 hub).
+// Reduce a warp's counters into the control block (class c: 0 warp, 1 block, 2 hub, 3 tiny).
 __device__ __forceinline__ void flush(const Acc &acc, Ctl *ctl, int c, unsigned long long build_elems,
                                       unsigned long long tasks) {
     const unsigned long long s = warp_sum(acc.same), x = warp_sum(acc.cross), p = warp_sum(acc.probes);
@@ -281,6 +281,63 @@ __global__ void __launch_bounds__(1024) k_isect_warp(const uint2 *__restrict__ t
     }
     flush(acc, ctl, 0, lane == 0 ? build : 0, lane == 0 ? done : 0);
     if (lane == 0 && inserts) atomicAdd(&ctl->cls_inserts[0], inserts);
+}
+
+// ---------------------------------------------------------------------------- tiny class
+
+// Sorted intersection size of a[0..na) (shared, column `stride` apart) and
+// b[0..nb) (global), both ascending: two-pointer merge.
+__device__ __forceinline__ uint32_t merge_count(const uint32_t *a, uint32_t stride, uint32_t na,
+                                                const uint32_t *__restrict__ b, uint32_t nb) {
+    uint32_t i = 0, j = 0, c = 0;
+    while (i < na && j < nb) {
+        const uint32_t x = a[i * stride], y = __ldg(b + j);
+        c += x == y;
+        i += x <= y;
+        j += y <= x;
+    }
+    return c;
+}
+
+// Tiny class: one thread per row u (s(u) <= tiny_cap).  u's row is copied to
+// a shared column; for every v in H(u) the G0 parts H(u), H(v) and the G1
+// parts of the two rows are intersected by sorted merges -- the rows keep the
+// CSR order, so each part is ascending.
+__global__ void __launch_bounds__(256) k_isect_tiny(const uint32_t *__restrict__ rows, uint32_t lo, uint32_t hi,
+                                                    const uint64_t *__restrict__ off2,
+                                                    const uint32_t *__restrict__ adj2,
+                                                    const uint32_t *__restrict__ hcnt, Ctl *ctl, uint32_t tiny_cap,
+                                                    GroupSpec groups) {
+    extern __shared__ uint32_t srow[];  // tiny_cap x blockDim, column per thread
+    uint32_t *mine = srow + threadIdx.x;
+    const uint32_t stride = blockDim.x;
+    Acc acc;
+    unsigned long long build = 0, done = 0;
+    const uint32_t total = (uint32_t)((uint64_t)gridDim.x * blockDim.x);
+    for (uint32_t i = lo + blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += total) {
+        const uint32_t u = rows[i];
+        const uint64_t ub = off2[u];
+        const uint32_t su = (uint32_t)(off2[u + 1] - ub), hu = hcnt[u];
+        for (uint32_t k = 0; k < su; ++k) mine[k * stride] = __ldg(adj2 + ub + k);
+        uint32_t same = 0, cross = 0;
+        unsigned long long probes = 0;
+        for (uint32_t k = 0; k < hu; ++k) {
+            const uint32_t v = mine[k * stride];
+            const uint64_t vb = off2[v];
+            const uint32_t vs = (uint32_t)(off2[v + 1] - vb), hv = hcnt[v];
+            same += merge_count(mine, stride, hu, adj2 + vb, hv);
+            cross += merge_count(mine + hu * stride, stride, su - hu, adj2 + vb + hv, vs - hv);
+            probes += vs;
+        }
+        acc.same += same;
+        acc.cross += cross;
+        acc.probes += probes;
+        build += su;
+        ++done;
+        if (groups.n_groups && same + cross) atomicAdd(&groups.counts[group_of(groups, u)], (unsigned long long)(same + cross));
+    }
+    const unsigned long long b = warp_sum(build), d = warp_sum(done);
+    flush(acc, ctl, 3, lane_id() == 0 ? b : 0, lane_id() == 0 ? d : 0);
 }
 
 // ---------------------------------------------------------------------------- block and hub classes
@@ -569,6 +626,20 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
     const Tuning &tu = ctx->tune;
     const Ctl &h = *ctx->h_ctl;  // pulled after planning
     // ev[4..7] bracket the warp, block and hub kernels
+    // tiny rows: one thread each (this count's share of them)
+    TC_CUDA(ctx, cudaEventRecord(ctx->ev[8], s));
+    const uint32_t nt3 = h.n_rows[3];
+    const uint32_t lo3 = (uint32_t)((uint64_t)nt3 * ctx->shard / ctx->nshards);
+    const uint32_t hi3 = (uint32_t)((uint64_t)nt3 * (ctx->shard + 1) / ctx->nshards);
+    if (hi3 > lo3) {
+        const size_t smem = 4ull * tu.tiny_cap * 256;
+        TC_CUDA(ctx, cudaFuncSetAttribute(k_isect_tiny, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const uint32_t grid = std::min<uint32_t>((hi3 - lo3 + 255) / 256, (uint32_t)ctx->num_sms * 8u);
+        k_isect_tiny<<<grid, 256, smem, s>>>(b.rows[3], lo3, hi3, b.off2, b.adj2, b.hcnt, ctx->d_ctl, tu.tiny_cap,
+                                             b.groups);
+        note_launch(ctx);
+    }
+    TC_CUDA(ctx, cudaEventRecord(ctx->ev[9], s));
     // this count's share of every class's task list (all of it unless sharded)
     auto share = [&](unsigned long long total, unsigned long long *lo, unsigned long long *hi) {
         *lo = total * ctx->shard / ctx->nshards;
@@ -641,7 +712,7 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         }
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[7], s));
-    ctx->isect_flags = (hi0 > lo0 ? 1u : 0u) | (hi1 > lo1 ? 2u : 0u) | (nh ? 4u : 0u);
+    ctx->isect_flags = (hi0 > lo0 ? 1u : 0u) | (hi1 > lo1 ? 2u : 0u) | (nh ? 4u : 0u) | (hi3 > lo3 ? 8u : 0u);
     TC_CUDA(ctx, cudaGetLastError());
     return TC_OK;
 }

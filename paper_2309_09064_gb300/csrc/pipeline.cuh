@@ -26,7 +26,7 @@ struct PipeBufs {
     uint64_t *off2 = nullptr;       // [n+1] offsets of the compacted rows
     uint32_t *adj2 = nullptr;       // [S]   rows [G0 out-list | G1 list], each part ascending
     // intersection planning, per class c (0 warp, 1 block, 2 hub)
-    uint32_t *rows[3] = {};         // [n]   hashed rows u of class c
+    uint32_t *rows[4] = {};         // [n]   rows u of class c (0 warp, 1 block, 2 hub, 3 tiny)
     uint32_t *ntask[3] = {};        // [n]   tasks per row
     uint64_t *tpref[3] = {};        // [n+1] exclusive prefix of ntask
     uint2 *tasks[3] = {};           // {row index i, slice t} per task (carved after planning)

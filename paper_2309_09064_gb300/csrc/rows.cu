@@ -170,19 +170,22 @@ __global__ void k_row_fill(uint32_t n, const uint64_t *__restrict__ rp, const ui
 
 // Rows with at least one oriented horizontal edge are the hashed side of the
 // intersections; split them by the size s(u) of their compacted row:
-// class 0 (warp) s <= warp_cap, class 1 (block) s <= block_cap, class 2 (hub).
+// class 3 (tiny) s <= tiny_cap and degree <= 4 tiny_cap, class 0 (warp)
+// s <= warp_cap, class 1 (block) s <= block_cap, class 2 (hub).
 // The lists are built by a stable scan, so they (and the task lists made from
 // them) are in vertex order on every run: shards of a count agree on them.
 __global__ void k_class_flags(uint32_t n, const uint32_t *__restrict__ hcnt, const uint32_t *__restrict__ scnt,
-                              uint32_t *__restrict__ cls, Ctl *ctl, uint32_t warp_cap, uint32_t block_cap) {
+                              const uint32_t *__restrict__ deg, uint32_t *__restrict__ cls, Ctl *ctl,
+                              uint32_t warp_cap, uint32_t block_cap, uint32_t tiny_cap) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     unsigned my_max = 0;
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
-        uint32_t c = 3;  // no oriented horizontal edge: not a hashed row
+        uint32_t c = 4;  // no oriented horizontal edge: nothing to intersect
         if (hcnt[x] > 0) {
             const uint32_t s = scnt[x];
             c = s <= warp_cap ? 0u : (s <= block_cap ? 1u : 2u);
-            if (c) my_max = s > my_max ? s : my_max;
+            if (s <= tiny_cap && deg[x] <= 4 * tiny_cap) c = 3;
+            if (c == 1 || c == 2) my_max = s > my_max ? s : my_max;
         }
         cls[x] = c;
     }
@@ -285,10 +288,10 @@ tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_de
     launches += 1 + scan_u32_to_u64(b.scnt, b.off2, n, b.scan_tmp, s);
     k_row_fill<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.rp, b.col, b.deg, b.L, ld, b.hcnt, b.off2, b.adj2, order);
     // fdeg and R are free after the levels: class of every vertex, 0/1 indicator
-    k_class_flags<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.hcnt, b.scnt, b.fdeg, ctx->d_ctl, tu.warp_cap,
-                                                        tu.block_cap);
+    k_class_flags<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.hcnt, b.scnt, b.deg, b.fdeg, ctx->d_ctl, tu.warp_cap,
+                                                        tu.block_cap, tu.tiny_cap);
     launches += 2;
-    for (uint32_t c = 0; c < 3; ++c) {
+    for (uint32_t c = 0; c < 4; ++c) {
         k_class_indicator<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.fdeg, c, b.R);
         launches += 2 + scan_u32_to_u64(b.R, b.fpref, n, b.scan_tmp, s);
         k_class_scatter<<<grid_for(n, 256, cap), 256, 0, s>>>(

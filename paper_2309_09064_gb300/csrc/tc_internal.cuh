@@ -35,6 +35,7 @@ struct Tuning {
     uint32_t hub_group = 8;          // hub rows sharing one launch (one L2-resident bitmap each)
     uint32_t hub_threads = 1024;     // hub kernel threads
     uint32_t hub_filter_log2 = 20;   // hub prefilter bits (log2)
+    uint32_t tiny_cap = 16;          // s(u) <= tiny_cap and deg(u) <= 4 tiny_cap: thread-per-row merges (0: off)
 };
 
 // Control block in device memory: counters the kernels update and the host
@@ -45,10 +46,10 @@ struct Ctl {
     unsigned long long t_cross;      // triangles with one horizontal edge
     unsigned long long e0;           // |E0|
     unsigned long long probes;       // probed elements
-    unsigned long long cls_probes[3];   // per intersection class (warp, block, hub)
-    unsigned long long cls_build[3];    // hashed-row elements per class (each row once)
-    unsigned long long cls_rows[3];     // rows (warp) / tasks (block, hub) per class
-    unsigned long long cls_inserts[3];  // table / prefilter inserts actually done (rebuilds included)
+    unsigned long long cls_probes[4];   // per intersection class (warp, block, hub, tiny)
+    unsigned long long cls_build[4];    // hashed-row elements per class (each row once)
+    unsigned long long cls_rows[4];     // tasks (warp, block, hub) / rows (tiny) per class
+    unsigned long long cls_inserts[4];  // table / prefilter inserts actually done (rebuilds included)
     unsigned long long fr_edges[3];  // sum of degrees per frontier slot
     unsigned long long visited_edges;
     unsigned int fr_count[3];        // frontier sizes per slot (slots rotate in the persistent BFS)
@@ -57,7 +58,7 @@ struct Ctl {
     unsigned int components;         // BFS roots
     unsigned int changed;            // CC hooking made progress
     unsigned int n_residual;
-    unsigned int n_rows[3];          // hashed rows per intersection class (warp, block, hub)
+    unsigned int n_rows[4];          // rows per intersection class (warp, block, hub, tiny)
     unsigned int task_next[3];       // dynamic scheduling counters per class
     unsigned long long n_tasks[3];   // tasks per class
     unsigned int error;              // nonzero: a device-side check failed
@@ -108,7 +109,7 @@ struct tc_ctx {
     tc::Arena batch_arena;   // union CSR of tc_count_batch
     tc::Ctl *d_ctl = nullptr;
     tc::Ctl *h_ctl = nullptr;   // pinned
-    cudaEvent_t ev[8] = {};
+    cudaEvent_t ev[10] = {};
     uint32_t launches = 0;    // kernels launched by the current call
     uint32_t isect_flags = 0; // which intersection kernels the last count launched (1 warp, 2 block, 4 hub)
     uint32_t shard = 0, nshards = 1;  // intersection tasks of this count: share `shard` of `nshards`

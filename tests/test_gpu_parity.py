@@ -107,7 +107,20 @@ def test_every_intersection_class(tc, name, caps):
     global-table (hub) kernels, with maximal task splitting."""
     c = tc.tc_create(0)
     try:
-        tc.tc_set_tuning(c, warp_cap=caps[0], block_cap=caps[1], task_work=caps[2])
+        tc.tc_set_tuning(c, warp_cap=caps[0], block_cap=caps[1], task_work=caps[2], tiny_cap=0)
+        g = SMALL[name]
+        assert_parity(*gpu_count(tc, c, g), g)
+    finally:
+        tc.tc_destroy(c)
+
+
+@pytest.mark.parametrize("tiny", [1, 8, 64])
+@pytest.mark.parametrize("name", ["rmat10", "grid33x47", "union", "wheel101", "er4096"])
+def test_tiny_merge_class(tc, name, tiny):
+    """Rows up to `tiny` go to the thread-per-row merge kernel, the rest to the tables."""
+    c = tc.tc_create(0)
+    try:
+        tc.tc_set_tuning(c, tiny_cap=tiny)
         g = SMALL[name]
         assert_parity(*gpu_count(tc, c, g), g)
     finally:
