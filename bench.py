@@ -387,8 +387,9 @@ def main():
 
     kernels = {
         "k_isect_warp": (mean("ms_class", 0), mean("class_bytes", 0)),
-        "k_isect_block<shared>": (mean("ms_class", 1), mean("class_bytes", 1)),
-        "k_isect_block<global>": (mean("ms_class", 2), mean("class_bytes", 2)),
+        "k_isect_block": (mean("ms_class", 1), mean("class_bytes", 1)),
+        "k_isect_hub": (mean("ms_class", 2), mean("class_bytes", 2)),
+        "k_isect_tiny": (mean("ms_class", 3), mean("class_bytes", 3)),
     }
     dom = max(kernels, key=lambda k: kernels[k][0])
     dom_ms, dom_bytes = kernels[dom]
@@ -436,7 +437,7 @@ def main():
         "horizontal_edges": last["horizontal_edges"], "levels": last["levels"],
         "stage_ms": {"levels": mean("ms_levels"), "rows": mean("ms_mark"), "intersect": mean("ms_isect"),
                      "isect_warp": mean("ms_class", 0), "isect_block": mean("ms_class", 1),
-                     "isect_hub": mean("ms_class", 2)},
+                     "isect_hub": mean("ms_class", 2), "isect_tiny": mean("ms_class", 3)},
         "roofline": roofline, "gpu_launches": int(sum(st["launches"] for st in stats)),
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clock_info,
     }

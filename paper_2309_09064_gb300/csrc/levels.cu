@@ -319,7 +319,7 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned nblocks, long lo
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
         __threadfence();
@@ -330,25 +330,30 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned nblocks, long lo
 }
 
 // Persistent top-down BFS for small frontiers (high-diameter graphs): one
-// launch runs level after level, warp per frontier vertex, one grid barrier
-// per level, until the frontier is empty or exceeds (max_f, max_e); then the
-// host takes over again.  Counter slots rotate mod 3 (level L reads slot s,
+// launch runs level after level, one grid barrier per level, until the
+// frontier is empty or leaves [min_f, max_f] x [0, max_e]; then the host
+// takes over again.  A thread expands a frontier vertex of degree <= 32 on its
+// own; larger rows are expanded by the whole warp, one at a time.  Counter slots rotate mod 3 (level L reads slot s,
 // writes s+1, and s+2 is cleared for level L+1); queues alternate.
 __global__ void __launch_bounds__(512) k_bfs_persist(uint32_t *__restrict__ q0, uint32_t *__restrict__ q1,
                                                      const uint64_t *__restrict__ rp,
                                                      const uint32_t *__restrict__ col,
                                                      const uint32_t *__restrict__ deg, uint32_t *L, Ctl *ctl,
                                                      uint32_t slot, uint32_t queue, uint32_t level, uint32_t max_f,
-                                                     unsigned long long max_e) {
+                                                     unsigned long long max_e, uint32_t min_f) {
     const unsigned lane = lane_id();
     const unsigned gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
     volatile unsigned *vcount = ctl->fr_count;
     volatile unsigned long long *vedges = ctl->fr_edges;
+    // levels this launch adds (written once at the end by block 0, thread 0)
+    unsigned int add_visited = 0;
+    unsigned long long add_edges = 0;
+    uint32_t start_level = level;
     for (;;) {
         const uint32_t fcount = vcount[slot];
         const unsigned long long fedges = vedges[slot];
-        if (fcount == 0 || fcount > max_f || fedges > max_e) break;
+        if (fcount == 0 || fcount > max_f || fedges > max_e || fcount < min_f) break;
         const uint32_t s1 = slot == 2 ? 0 : slot + 1, s2 = s1 == 2 ? 0 : s1 + 1;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             ctl->fr_count[s2] = 0;
@@ -357,21 +362,40 @@ __global__ void __launch_bounds__(512) k_bfs_persist(uint32_t *__restrict__ q0, 
         const uint32_t *q = queue ? q1 : q0;
         uint32_t *qn = queue ? q0 : q1;
         unsigned long long edges = 0;
-        for (uint32_t i = gwarp; i < fcount; i += nwarps) {
-            const uint32_t v = q[i];
-            const uint64_t b = rp[v], e = rp[v + 1];
-            for (uint64_t j0 = b; j0 < e; j0 += 32) {
-                const uint64_t j = j0 + lane;
-                bool claim = false;
-                uint32_t w = 0;
-                if (j < e) {
-                    w = col[j];
-                    claim = L[w] == kUnvisited && atomicCAS(&L[w], kUnvisited, level + 1) == kUnvisited;
+        const uint32_t nthreads = nwarps * 32u, gtid = gwarp * 32u + lane;
+        const uint32_t f_round = (fcount + 31u) & ~31u;
+        for (uint32_t i = gtid; i < f_round; i += nthreads) {
+            const bool valid = i < fcount;
+            const uint32_t v = valid ? q[i] : 0u;
+            const uint64_t b = valid ? rp[v] : 0, e = valid ? rp[v + 1] : 0;
+            const bool small = e - b <= 32;
+            if (small) {
+                for (uint64_t j = b; j < e; ++j) {
+                    const uint32_t w = col[j];
+                    if (L[w] == kUnvisited && atomicCAS(&L[w], kUnvisited, level + 1) == kUnvisited) {
+                        qn[atomicAdd(&ctl->fr_count[s1], 1u)] = w;
+                        edges += deg[w];
+                    }
                 }
-                const uint32_t pos = warp_append(claim, &ctl->fr_count[s1]);
-                if (claim) {
-                    qn[pos] = w;
-                    edges += deg[w];
+            }
+            unsigned big = __ballot_sync(0xFFFFFFFFu, !small);
+            while (big) {
+                const int src = __ffs(big) - 1;
+                big &= big - 1;
+                const uint64_t bb = __shfl_sync(0xFFFFFFFFu, b, src), be = __shfl_sync(0xFFFFFFFFu, e, src);
+                for (uint64_t j0 = bb; j0 < be; j0 += 32) {
+                    const uint64_t j = j0 + lane;
+                    bool claim = false;
+                    uint32_t w = 0;
+                    if (j < be) {
+                        w = col[j];
+                        claim = L[w] == kUnvisited && atomicCAS(&L[w], kUnvisited, level + 1) == kUnvisited;
+                    }
+                    const uint32_t pos = warp_append(claim, &ctl->fr_count[s1]);
+                    if (claim) {
+                        qn[pos] = w;
+                        edges += deg[w];
+                    }
                 }
             }
         }
@@ -379,10 +403,8 @@ __global__ void __launch_bounds__(512) k_bfs_persist(uint32_t *__restrict__ q0, 
         if (lane == 0 && edges) atomicAdd(&ctl->fr_edges[s1], edges);
         if (!grid_barrier(ctl, gridDim.x, 4000000000ll)) return;  // ~2 s at 2 GHz
         if (blockIdx.x == 0 && threadIdx.x == 0) {
-            const uint32_t c = vcount[s1];
-            ctl->visited += c;
-            ctl->visited_edges += vedges[s1];
-            if (c) ctl->max_level = level + 1 > ctl->max_level ? level + 1 : ctl->max_level;
+            add_visited += vcount[s1];
+            add_edges += vedges[s1];
         }
         slot = s1;
         queue ^= 1u;
@@ -392,6 +414,12 @@ __global__ void __launch_bounds__(512) k_bfs_persist(uint32_t *__restrict__ q0, 
         ctl->p_slot = slot;
         ctl->p_queue = queue;
         ctl->p_level = level;
+        ctl->visited += add_visited;
+        ctl->visited_edges += add_edges;
+        // the last level that received vertices: the final frontier's level if it is
+        // non-empty, else the one before
+        const uint32_t last = vcount[slot] ? level : level - 1;
+        if (level > start_level && last > ctl->max_level) ctl->max_level = last;
     }
 }
 
@@ -408,7 +436,7 @@ unsigned grid_for(uint64_t work, unsigned threads, unsigned cap) {
     return (unsigned)b;
 }
 
-constexpr uint32_t kPersistMaxF = 32768;          // frontier vertices
+constexpr uint32_t kPersistMaxF = 32768;          // frontier vertices (whole-grid mode)
 constexpr unsigned long long kPersistMaxE = 65536;  // frontier edges
 
 }  // namespace
@@ -445,7 +473,7 @@ static tc_status bfs_loop(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t s
             if (persist_blocks < 0) {
                 int per_sm = 0;
                 TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs_persist, 512, 0));
-                persist_blocks = std::max(1, std::min(per_sm, 2)) * ctx->num_sms;
+                persist_blocks = std::max(1, std::min(per_sm, 1)) * ctx->num_sms;
             }
             k_reset_next<<<1, 1, 0, s>>>(ctx->d_ctl, (int)nxt);
             uint32_t *q0 = b.q0, *q1 = b.q1;
@@ -453,11 +481,13 @@ static tc_status bfs_loop(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t s
             const uint32_t *col = b.col, *deg = b.deg;
             uint32_t *L = b.L;
             Ctl *ctl = ctx->d_ctl;
-            uint32_t a_slot = slot, a_queue = queue, a_level = level, a_max_f = kPersistMaxF;
+            uint32_t a_slot = slot, a_queue = queue, a_level = level;
+            uint32_t a_max_f = kPersistMaxF, a_min_f = 0;
             unsigned long long a_max_e = kPersistMaxE;
-            void *args[] = {&q0, &q1, &rp, &col, &deg, &L, &ctl, &a_slot, &a_queue, &a_level, &a_max_f, &a_max_e};
-            TC_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_bfs_persist, dim3(persist_blocks), dim3(512), args,
-                                                     0, s));
+            void *args[] = {&q0, &q1, &rp, &col, &deg, &L, &ctl, &a_slot, &a_queue, &a_level, &a_max_f, &a_max_e,
+                            &a_min_f};
+            TC_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_bfs_persist, dim3(persist_blocks), dim3(512),
+                                                     args, 0, s));
             note_launch(ctx, 2);
             st = pull_ctl(ctx);
             if (st != TC_OK) return st;
