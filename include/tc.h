@@ -116,7 +116,7 @@ typedef struct tc_tuning {
     uint32_t block_cap;        /* s(u) <= block_cap: one block per task, shared table (warp_cap..16384);
                                   larger rows are hub rows (L2 bitmaps + shared prefilter) */
     uint32_t task_work;        /* target probes per block task (large rows are split) */
-    uint32_t warps_per_block;  /* warp-class kernel block size in warps (1..32) */
+    uint32_t warps_per_block;  /* warp-class kernel block size in warps (1..8) */
     uint32_t block_threads;    /* block-class kernel threads (64..1024, multiple of 32) */
     uint32_t warp_task_work;   /* target probes per warp task */
     uint32_t hub_task_work;    /* target probes per hub task */
@@ -127,7 +127,11 @@ typedef struct tc_tuning {
     uint32_t tiny_cap;         /* s(u) <= tiny_cap (and degree <= 4 tiny_cap): one thread per row, sorted
                                   merges instead of a table; takes precedence over the classes above
                                   (0..64; 0 turns it off) */
-    uint32_t reserved[4];
+    uint32_t block_filter_log2; /* block-class filter in front of the table: 2^k bits of shared memory
+                                   (10..19; 0: no filter) */
+    uint32_t flat_cap;          /* warp class: probe ranges shorter than this are concatenated so that every
+                                   lane of a warp has work; longer ones are walked range by range (0..4096) */
+    uint32_t reserved[2];
 } tc_tuning;
 
 /* ------------------------------------------------------------------ context */

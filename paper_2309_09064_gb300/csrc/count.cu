@@ -1,4 +1,7 @@
 // count.cu -- one exact count: arena layout, stage sequence, readback, stats.
+#include <algorithm>
+#include <cstdio>
+
 #include "pipeline.cuh"
 
 namespace tc {
@@ -27,12 +30,17 @@ size_t pipeline_bytes(const tc_ctx *ctx, uint32_t n, uint64_t slots, uint32_t ma
                       uint64_t *hub_words, uint32_t *hub_maps) {
     auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t n1 = (size_t)n + 1;
+    const uint64_t rtiles = radix_tiles(n1);
     size_t bytes = 0;
-    bytes += 15 * r(4 * n1);                       // deg q0 q1 fdeg R parent hcnt scnt rows[4] ntask[3]
+    bytes += 18 * r(4 * n1);                       // deg q0 q1 fdeg R parent fcnt gcnt rank big lvp rows[4] ntask[3]
+    bytes += r(16 * n1);                           // vmeta
+    bytes += r(4 * (slots / 2 / 256 + 2));         // chunk_row
     if (own_levels) bytes += r(4 * n1);            // L
-    bytes += 5 * r(8 * n1);                        // fpref off2 tpref[3]
+    bytes += 8 * r(8 * n1);                        // fpref eoff tpref[3] lv rkeys0 rkeys1
     bytes += r(4 * (slots + 1));                   // adj2
-    bytes += r(8 * scan_tmp_elems(n1 + 1));        // scan tiles
+    bytes += r(16 * (slots / 2 + 1));              // probe records: one per oriented G0 edge
+    bytes += r(4 * (256 * rtiles + 1)) + r(8 * (256 * rtiles + 2));  // radix digit counts and offsets
+    bytes += r(8 * scan_tmp_elems(std::max<uint64_t>(n1 + 1, 256 * rtiles + 2)));  // scan tiles
     bytes += r(8 * (slots / 2 + 1));               // task pool: at most one task per oriented G0 edge
     *hub_words = 0;
     *hub_maps = 0;
@@ -66,9 +74,15 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     b.fdeg = a.take<uint32_t>(n1);
     b.R = a.take<uint32_t>(n1);
     b.parent = a.take<uint32_t>(n1);
-    b.hcnt = a.take<uint32_t>(n1);
-    b.scnt = a.take<uint32_t>(n1);
-    bool ok = b.deg && b.L && b.q0 && b.q1 && b.fdeg && b.R && b.parent && b.hcnt && b.scnt;
+    b.fcnt = a.take<uint32_t>(n1);
+    b.gcnt = a.take<uint32_t>(n1);
+    b.rank = a.take<uint32_t>(n1);
+    b.big = a.take<uint32_t>(n1);
+    uint32_t *lvp = a.take<uint32_t>(n1);
+    b.vmeta = a.take<uint4>(n1);
+    b.chunk_row = a.take<uint32_t>(g.slots / 2 / 256 + 2);
+    bool ok = b.deg && b.L && b.q0 && b.q1 && b.fdeg && b.R && b.parent && b.fcnt && b.gcnt && b.rank && b.big &&
+              lvp && b.vmeta && b.chunk_row;
     b.rows[3] = a.take<uint32_t>(n1);
     ok = ok && b.rows[3];
     for (int c = 0; c < 3; ++c) {
@@ -78,15 +92,24 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
         ok = ok && b.rows[c] && b.ntask[c] && b.tpref[c];
     }
     b.fpref = a.take<uint64_t>(n1);
-    b.off2 = a.take<uint64_t>(n1);
+    b.eoff = a.take<uint64_t>(n1);
+    b.lv = a.take<uint2>(n1);
+    b.rkeys0 = a.take<unsigned long long>(n1);
+    b.rkeys1 = a.take<unsigned long long>(n1);
+    const uint64_t rtiles = radix_tiles(n1);
+    b.rcounts = a.take<uint32_t>(256 * rtiles + 1);
+    b.roffs = a.take<uint64_t>(256 * rtiles + 2);
     b.adj2 = a.take<uint32_t>(g.slots + 1);
-    b.scan_tmp = a.take<uint64_t>(scan_tmp_elems(n1 + 1));
+    b.erec_cap = g.slots / 2 + 1;
+    b.erec = a.take<uint4>(b.erec_cap);
+    b.scan_tmp = a.take<uint64_t>(scan_tmp_elems(std::max<uint64_t>(n1 + 1, 256 * rtiles + 2)));
     b.task_cap = g.slots / 2 + 1;
     b.task_pool = a.take<uint2>(b.task_cap);
     b.hub_words = hub_words;
     if (hub_maps) b.hub_bits = a.take<uint32_t>(hub_words * hub_maps);
     b.groups = groups;
-    ok = ok && b.fpref && b.off2 && b.adj2 && b.scan_tmp && b.task_pool && (!hub_maps || b.hub_bits);
+    ok = ok && b.fpref && b.eoff && b.lv && b.rkeys0 && b.rkeys1 && b.rcounts && b.roffs && b.adj2 && b.erec &&
+         b.scan_tmp && b.task_pool && (!hub_maps || b.hub_bits);
     if (!ok) return set_error(ctx, TC_ERR_OOM, "arena carve failed");
 
     k_ctl_reset<<<1, 128, 0, s>>>(ctx->d_ctl);
@@ -95,6 +118,10 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     st = compute_levels(ctx, b, n, g.slots);
     if (st != TC_OK) return st;
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[1], s));
+    // the packed 4-byte {rank, level} word needs ranks below 2^24 and levels below 255
+    b.lvp = (n <= (1u << 24) && ctx->h_ctl->max_level < 255) ? lvp : nullptr;
+    st = compute_ranks(ctx, b, n, g.max_deg);
+    if (st != TC_OK) return st;
     st = build_rows(ctx, b, n, g.max_deg);
     if (st != TC_OK) return st;
     st = pull(ctx);  // row counts per class
@@ -112,7 +139,11 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     st = pull(ctx);
     if (st != TC_OK) return st;
     const Ctl &h = *ctx->h_ctl;
-    if (h.error) return set_error(ctx, TC_ERR_INVALID, "device-side check failed during the count");
+    if (h.error) {
+        char msg[96];
+        std::snprintf(msg, sizeof msg, "device-side check failed during the count (code 0x%x)", h.error);
+        return set_error(ctx, TC_ERR_INVALID, msg);
+    }
     const uint64_t T = h.t_same + h.t_cross;
     if (triangles) *triangles = T;
     if (stats) {
@@ -129,22 +160,19 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
         stats->levels = n ? (uint64_t)h.max_level + 1 : 0;
         stats->components = h.components;
         stats->probes = h.probes;
-        stats->row2_slots = 0;
-        uint64_t row2 = 0;
-        if (n) {
-            TC_CUDA(ctx, cudaMemcpyAsync(&row2, b.off2 + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
-            TC_CUDA(ctx, cudaStreamSynchronize(s));
-        }
+        // slots of the hashed and probed parts A and G1: every slot but F's
+        const uint64_t row2 = g.slots - h.e0;
         stats->row2_slots = row2;
         // Algorithmic bytes (4-byte ids, 8-byte offsets):
         //   levels: row_ptr 8(n+1) + col 4S + neighbour levels 4S + level writes 4n
-        //   rows:   row_ptr 8(n+1) + col 4S + neighbour level and degree 8S
-        //           + compacted rows 4*row2 + offsets/counts writes 16(n+1)
-        //   intersections: hashed rows read once per u + probed rows per edge
+        //   rows:   row_ptr 8(n+1) + col 4S + neighbour rank and level 8S
+        //           + rewritten rows 4S + |F|, |G1| writes 8n
+        //   intersections: per hashed row its set and out-list 4(s(u) + |F(u)|),
+        //           per oriented edge the probed range 4(|G1(v)| + p)
         //   output: 8
         const uint64_t S = g.slots, N1 = (uint64_t)n + 1;
         const uint64_t lv = 8 * N1 + 4 * S + 4 * S + 4ull * n;
-        const uint64_t rw = 8 * N1 + 4 * S + 8 * S + 4 * row2 + 16 * N1;
+        const uint64_t rw = 8 * N1 + 4 * S + 8 * S + 4 * S + 8ull * n;
         uint64_t is = 0;
         for (int c = 0; c < 4; ++c) {
             stats->class_rows[c] = h.cls_rows[c];

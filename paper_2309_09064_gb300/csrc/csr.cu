@@ -220,6 +220,23 @@ tc_status pull(tc_ctx *ctx) {
 
 }  // namespace
 
+uint64_t radix_tiles(uint64_t count) { return (count + kRsTile - 1) / kRsTile; }
+
+uint32_t radix_sort_u64(unsigned long long **cur, unsigned long long **alt, uint64_t count, const int *shifts,
+                        int nshifts, uint32_t *counts, uint64_t *coffs, uint64_t *tmp, cudaStream_t s) {
+    if (count < 2) return 0;
+    const uint32_t nblk = (uint32_t)radix_tiles(count);
+    uint32_t launches = 0;
+    for (int i = 0; i < nshifts; ++i) {
+        k_rs_hist<<<nblk, kRsThreads, 0, s>>>(*cur, count, shifts[i], counts, nblk);
+        launches += 2 + scan_u32_to_u64(counts, coffs, 256ull * nblk, tmp, s);
+        k_rs_scatter<<<nblk, kRsThreads, 0, s>>>(*cur, *alt, count, shifts[i],
+                                                 reinterpret_cast<const unsigned long long *>(coffs), nblk);
+        std::swap(*cur, *alt);
+    }
+    return launches;
+}
+
 tc_status build_csr_device(tc_ctx *ctx, uint32_t n, uint64_t t, const uint32_t *d_src, const uint32_t *d_dst,
                            uint64_t **rp_out, uint32_t **col_out, uint64_t *slots_out) {
     cudaStream_t s = ctx->stream;
@@ -260,16 +277,7 @@ tc_status build_csr_device(tc_ctx *ctx, uint32_t n, uint64_t t, const uint32_t *
     for (int sh = 0; sh < B; sh += 8) shifts.push_back(sh);
     for (int sh = 0; sh < B; sh += 8) shifts.push_back(32 + sh);
     unsigned long long *cur = k0, *alt = k1;
-    const uint32_t nblk = (uint32_t)((nk + kRsTile - 1) / kRsTile);
-    if (nk > 1) {
-        for (int sh : shifts) {
-            k_rs_hist<<<nblk, kRsThreads, 0, s>>>(cur, nk, sh, counts, nblk);
-            scan_u32_to_u64(counts, coffs, 256ull * nblk, tmp, s);
-            k_rs_scatter<<<nblk, kRsThreads, 0, s>>>(cur, alt, nk, sh,
-                                                     reinterpret_cast<const unsigned long long *>(coffs), nblk);
-            std::swap(cur, alt);
-        }
-    }
+    radix_sort_u64(&cur, &alt, nk, shifts.data(), (int)shifts.size(), counts, coffs, tmp, s);
     uint64_t *rp = nullptr;
     uint32_t *col = nullptr;
     uint64_t U = 0;

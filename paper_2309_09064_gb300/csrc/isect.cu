@@ -1,24 +1,34 @@
-// isect.cu -- hashed intersections of the compacted rows over every oriented
-// horizontal edge u -> v (Algorithm 4 with Algorithm 2 on G0), and the
-// reduction of the counts into 64-bit totals.
+// isect.cu -- hashed intersections over every oriented horizontal edge
+// u -> v (Algorithm 4 with Algorithm 2 on G0), and the reduction of the
+// counts into 64-bit totals.
 //
-// As in the paper's hashed loop, the row of u (the endpoint that comes first
-// in the working order, the higher-degree one under the degree order) is put
-// in a set once, and the rows of its horizontal out-neighbours v are probed
-// against it; the cost per edge is |row(v)| <= min(d(u), d(v)).  Rows are
-// split by the size s(u) of the hashed row, and every row's out-edges are cut
-// into tasks (contiguous slices of H(u)) of bounded probe work:
+// As in the paper's hashed loops, u (the endpoint that comes first in the
+// working order, the higher-degree one under the degree order) is put in a
+// set once -- its A(u) and G1(u), as ranks -- and for every v in F(u) the
+// range of v's slots that k_plan recorded is probed against it: the elements
+// of A(v) ranked below u (Algorithm 2's intersection A(u) & A(v) at edge
+// (u, v): a triangle inside G0, found once, at the edge between its two later
+// vertices) and all of G1(v) (Algorithm 4's hashed loop: a triangle with
+// exactly one horizontal edge, found once, at that edge).  A common element
+// of G1(u) and A(v) or of A(u) and G1(v) is impossible (different levels), so
+// one set and one probe range serve both counts; the position of a hit in the
+// range (below or above the record's split) says which kind it is.
+//
+// Rows are split by the size s(u) = |A(u)| + |G1(u)| of the set, and every
+// row's out-edges are cut into tasks (contiguous slices of F(u)) of bounded
+// probe work:
 //   warp class  s(u) <= warp_cap : one warp per task, bucketed hash table in
 //                                  the warp's slice of shared memory;
 //   block class s(u) <= block_cap: one block per task, bucketed hash table in
 //                                  shared memory;
 //   hub class   larger           : hub rows are taken `hub_group` at a time,
-//                                  each gets an n-bit bitmap in global memory
-//                                  (L2-resident while its group runs); a block
-//                                  keeps a shared-memory prefilter of its row
-//                                  so that only prefilter-positive probes read
-//                                  the bitmap.
-// Within a task, warps take out-neighbour rows dynamically and walk each row
+//                                  each gets an n-bit bitmap (by rank) in
+//                                  global memory (L2-resident while its group
+//                                  runs); a block keeps a shared-memory
+//                                  prefilter of its set so that only
+//                                  prefilter-positive probes read the bitmap;
+//   tiny class  s(u) <= tiny_cap : one thread per row, sorted merges / scans.
+// Within a task, warps take probe ranges dynamically and walk each range
 // with every lane holding several independent loads.  A block keeps its table
 // (or prefilter) when its next task belongs to the same row.
 #include <algorithm>
@@ -41,11 +51,21 @@ struct Acc {
 // whose last slot is empty ends every probe sequence that reaches it: a key
 // sits in the first bucket, from its home, that had room when it was inserted.
 struct BucketTable {
-    static constexpr int kUnroll = 8;  // row ids in flight per lane
+    static constexpr int kUnroll = 8;  // ids in flight per lane
     static constexpr int kBatch = 4;   // lookups resolved together
     uint4 *bk;
     uint32_t shift, mask;  // home bucket = hash >> shift; mask = buckets - 1
+    unsigned int *err;     // device error word: a walk longer than the table sets kGuardTable
 };
+
+// Guard codes OR-ed into the control block's error word when a loop whose
+// length depends on the data runs past its bound (the loop then stops and
+// the count reports an error instead of spinning).
+constexpr unsigned kGuardInsert = 0x10u;    // table insert found no free slot
+constexpr unsigned kGuardTable = 0x20u;     // table probe walked the whole table
+constexpr unsigned kGuardWalk = 0x40u;      // concatenated ranges walked past the last range
+constexpr unsigned kGuardWatchdog = 0x80u;  // a kernel ran past its time limit
+constexpr long long kWatchdogCycles = 20000000000ll;  // about 10 s of SM clock
 
 // Buckets for len keys: at most `cap` buckets, at least len / 2 (load factor
 // <= 1/2), preferably len (load factor <= 1/4); a power of two >= 16.
@@ -56,64 +76,75 @@ __device__ __forceinline__ uint32_t buckets_for(uint32_t len, uint32_t cap) {
 }
 
 __device__ __forceinline__ BucketTable clear_table(uint4 *bk, uint32_t len, uint32_t cap, uint32_t t,
-                                                   uint32_t nthreads) {
+                                                   uint32_t nthreads, unsigned int *err) {
     const uint32_t nb = buckets_for(len, cap);
-    BucketTable T{bk, (uint32_t)__clz(nb) + 1u, nb - 1u};
+    BucketTable T{bk, (uint32_t)__clz(nb) + 1u, nb - 1u, err};
     const uint4 e = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
     for (uint32_t j = t; j < nb; j += nthreads) bk[j] = e;
     return T;
 }
 
-__device__ __forceinline__ void fill_table(const BucketTable &T, const uint32_t *__restrict__ row, uint32_t len,
-                                           uint32_t t, uint32_t nthreads) {
-    for (uint32_t j = t; j < len; j += nthreads) {
-        const uint32_t w = row[j];
-        uint32_t b = hash_slot(w, T.shift);
-        for (;;) {
-            uint32_t *s = reinterpret_cast<uint32_t *>(T.bk + b);
-            if (atomicCAS(s + 0, kEmpty, w) == kEmpty || atomicCAS(s + 1, kEmpty, w) == kEmpty ||
-                atomicCAS(s + 2, kEmpty, w) == kEmpty || atomicCAS(s + 3, kEmpty, w) == kEmpty)
-                break;
-            b = (b + 1) & T.mask;
-        }
+__device__ __forceinline__ void table_insert(const BucketTable &T, uint32_t w) {
+    uint32_t b = hash_slot(w, T.shift);
+    for (uint32_t step = 0; step <= T.mask; ++step) {
+        uint32_t *s = reinterpret_cast<uint32_t *>(T.bk + b);
+        if (atomicCAS(s + 0, kEmpty, w) == kEmpty || atomicCAS(s + 1, kEmpty, w) == kEmpty ||
+            atomicCAS(s + 2, kEmpty, w) == kEmpty || atomicCAS(s + 3, kEmpty, w) == kEmpty)
+            return;
+        b = (b + 1) & T.mask;
     }
+    atomicOr(T.err, kGuardInsert);
 }
 
-// Hub rows: shared prefilter (one multiplicative hash into 2^k bits, k =
-// hub_filter_log2) in front of the exact n-bit bitmap in global memory.
+__device__ __forceinline__ void fill_table(const BucketTable &T, const uint32_t *__restrict__ row, uint32_t len,
+                                           uint32_t t, uint32_t nthreads) {
+    for (uint32_t j = t; j < len; j += nthreads) table_insert(T, row[j]);
+}
+
+// Continue the probe sequence of w past its full home bucket (rare).
+__device__ __forceinline__ bool table_find_rest(const BucketTable &T, uint32_t home, uint32_t w) {
+    uint32_t bb = home;
+    for (uint32_t step = 0; step < T.mask; ++step) {
+        bb = (bb + 1) & T.mask;
+        const uint4 r = T.bk[bb];
+        if (r.x == w || r.y == w || r.z == w || r.w == w) return true;
+        if (r.w == kEmpty) return false;
+    }
+    atomicOr(T.err, kGuardTable);
+    return false;
+}
+
+// One multiplicative hash into 2^k bits (fshift = 32 - k): the shared filters
+// of the block and hub classes.
 __device__ __forceinline__ uint32_t filter_bit(uint32_t w, uint32_t fshift) { return (w * 0x85EBCA6Bu) >> fshift; }
 
+__device__ __forceinline__ bool filter_test(const uint32_t *filter, uint32_t w, uint32_t fshift) {
+    const uint32_t f = filter_bit(w, fshift);
+    return (filter[f >> 5] >> (f & 31)) & 1u;
+}
+
+// Block rows: shared filter (2^block_filter_log2 bits) in front of the bucket
+// table; most probes miss and end at the filter with one 32-bit shared load.
+struct FilteredTable {
+    static constexpr int kUnroll = 8;
+    static constexpr int kBatch = 8;
+    BucketTable T;
+    const uint32_t *filter;
+    uint32_t fshift;
+};
+
+// Hub rows: shared prefilter (2^hub_filter_log2 bits) in front of the exact
+// n-bit bitmap (by rank) in global memory.
 struct HubSet {
-    static constexpr int kUnroll = 8;  // row ids in flight per lane
+    static constexpr int kUnroll = 8;  // ids in flight per lane
     static constexpr int kBatch = 8;   // prefilter tests, then all bitmap loads together
     const uint32_t *filter;  // shared
     const uint32_t *bits;    // global, read-only while probing
-    uint32_t fshift;         // 32 - hub_filter_log2
+    uint32_t fshift;
 };
 
-// ---------------------------------------------------------------------------- probing one row
-
-// Probe positions [j_lo, len) of row(v) = adj2[b .. b+len) with one warp;
-// position j < hv is the G0
-// part (a triangle inside G0), the rest the G1 part (a cross-level triangle).
-// Each lane first issues all its element loads, then all first lookups,
-// then resolves them, so independent memory operations overlap.
-// Per-row-step hit counters stay 32-bit in registers; probe_row adds them to
-// the 64-bit accumulators once per call.
-struct Hits {
-    uint32_t all = 0, same = 0;
-    __device__ __forceinline__ void add(bool hit, uint32_t j, uint32_t hv) {
-        all += hit;
-        same += hit && j < hv;
-    }
-    __device__ __forceinline__ void flush(Acc &acc) const {
-        acc.same += same;
-        acc.cross += all - same;
-    }
-};
-
-// Probe one element batch against the bucket table: first buckets for all,
-// then the rare continuation for lanes whose home bucket was full.
+// Probe one batch of N elements against the bucket table: first buckets for
+// all, then the rare continuation for those whose home bucket was full.
 template <int N>
 __device__ __forceinline__ void lookup_batch(const BucketTable &T, const uint32_t (&w)[N], bool (&hit)[N]) {
     uint4 q[N];
@@ -126,32 +157,36 @@ __device__ __forceinline__ void lookup_batch(const BucketTable &T, const uint32_
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         hit[i] = q[i].x == w[i] || q[i].y == w[i] || q[i].z == w[i] || q[i].w == w[i];
-        if (!hit[i] && q[i].w != kEmpty && w[i] != kEmpty) {  // bucket full: continue the probe sequence
-            uint32_t bb = home[i];
-            for (;;) {
-                bb = (bb + 1) & T.mask;
-                const uint4 r = T.bk[bb];
-                if (r.x == w[i] || r.y == w[i] || r.z == w[i] || r.w == w[i]) {
-                    hit[i] = true;
-                    break;
-                }
-                if (r.w == kEmpty) break;
-            }
-        }
+        if (!hit[i] && q[i].w != kEmpty && w[i] != kEmpty) hit[i] = table_find_rest(T, home[i], w[i]);
         hit[i] = hit[i] && w[i] != kEmpty;
     }
 }
 
-// Hub batch: shared prefilter for all N elements, then the exact bitmap word
-// for the prefilter-positive ones (predicated loads, all in flight together).
+// Filter tests for all N elements, then the table for the positive ones.
+template <int N>
+__device__ __forceinline__ void lookup_batch(const FilteredTable &F, const uint32_t (&w)[N], bool (&hit)[N]) {
+    bool pos[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) pos[i] = w[i] != kEmpty && filter_test(F.filter, w[i], F.fshift);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        hit[i] = false;
+        if (pos[i]) {
+            const uint32_t home = hash_slot(w[i], F.T.shift);
+            const uint4 q = F.T.bk[home];
+            hit[i] = q.x == w[i] || q.y == w[i] || q.z == w[i] || q.w == w[i];
+            if (!hit[i] && q.w != kEmpty) hit[i] = table_find_rest(F.T, home, w[i]);
+        }
+    }
+}
+
+// Prefilter for all N elements, then the exact bitmap word for the positive
+// ones (predicated loads, all in flight together).
 template <int N>
 __device__ __forceinline__ void lookup_batch(const HubSet &H, const uint32_t (&w)[N], bool (&hit)[N]) {
     bool pos[N];
 #pragma unroll
-    for (int i = 0; i < N; ++i) {
-        const uint32_t f = filter_bit(w[i], H.fshift);
-        pos[i] = w[i] != kEmpty && ((H.filter[f >> 5] >> (f & 31)) & 1u);
-    }
+    for (int i = 0; i < N; ++i) pos[i] = w[i] != kEmpty && filter_test(H.filter, w[i], H.fshift);
     uint32_t word[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) word[i] = pos[i] ? __ldg(H.bits + (w[i] >> 5)) : 0u;
@@ -159,13 +194,44 @@ __device__ __forceinline__ void lookup_batch(const HubSet &H, const uint32_t (&w
     for (int i = 0; i < N; ++i) hit[i] = pos[i] && ((word[i] >> (w[i] & 31)) & 1u);
 }
 
-// Probe positions [j_lo, j_hi) of row(v) = adj2[b ..] with one warp, lanes
-// striding over the positions with U loads in flight each.  Position j < hv
-// is the G0 part (a triangle inside G0), the rest the G1 part (a cross-level
-// triangle).  Lookups are resolved Set::kBatch at a time (registers).
+// ---------------------------------------------------------------------------- probing
+
+// Hit counters of one probing call, 32-bit in registers, added to the 64-bit
+// accumulators once per call.  A hit in the A part of a probe range is a
+// triangle inside G0, a hit in the G1 part a cross-level triangle.
+struct Hits {
+    uint32_t all = 0, same = 0;
+    __device__ __forceinline__ void add(bool hit, bool in_a) {
+        all += hit;
+        same += hit && in_a;
+    }
+    __device__ __forceinline__ void flush(Acc &acc) const {
+        acc.same += same;
+        acc.cross += all - same;
+    }
+};
+
+template <class Set, int U>
+__device__ __forceinline__ void lookup_all(const Set &set, const uint32_t (&w)[U], const bool (&in_a)[U], Hits &hits) {
+    constexpr int B = Set::kBatch;
+#pragma unroll
+    for (int half = 0; half < U; half += B) {
+        uint32_t ww[B];
+        bool hit[B];
+#pragma unroll
+        for (int i = 0; i < B; ++i) ww[i] = w[half + i];
+        lookup_batch(set, ww, hit);
+#pragma unroll
+        for (int i = 0; i < B; ++i) hits.add(hit[i], in_a[half + i]);
+    }
+}
+
+// Positions [j_lo, j_hi) of one probe range adj2[b ..] with one warp, lanes
+// striding over the positions with U loads in flight each; positions below
+// `split` are the A part.
 template <int U, class Set>
 __device__ __forceinline__ void probe_row(const Set &set, const uint32_t *__restrict__ adj2, unsigned long long b,
-                                          uint32_t j_lo, uint32_t j_hi, uint32_t hv, Acc &acc) {
+                                          uint32_t j_lo, uint32_t j_hi, uint32_t split, Acc &acc) {
     const unsigned lane = lane_id();
     const uint32_t *row = adj2 + b;
     Hits hits;
@@ -185,8 +251,59 @@ __device__ __forceinline__ void probe_row(const Set &set, const uint32_t *__rest
             for (int i = 0; i < B; ++i) ww[i] = w[half + i];
             lookup_batch(set, ww, hit);
 #pragma unroll
-            for (int i = 0; i < B; ++i) hits.add(hit[i], j0 + (uint32_t)(half + i) * 32u + lane, hv);
+            for (int i = 0; i < B; ++i) hits.add(hit[i], j0 + (uint32_t)(half + i) * 32u + lane < split);
         }
+    }
+    hits.flush(acc);
+}
+
+// Short probe ranges, concatenated: range r covers positions
+// [pre[r], pre[r+1]) of one flat sequence (ranges of length 0 allowed,
+// pre[nv] = total), starts at adj2[b[r]] and has its A part below split[r].
+// One warp probes positions [q_lo, q_hi) (q_hi <= total) with every lane busy
+// however short the ranges are: each lane finds the range of its first
+// position by binary search and then walks forward.
+template <int U, class Set>
+__device__ __forceinline__ void probe_flat(const Set &set, const uint32_t *__restrict__ adj2,
+                                           const unsigned long long *sb, const uint32_t *spre,
+                                           const uint32_t *ssplit, uint32_t nv, uint32_t q_lo, uint32_t q_hi,
+                                           Acc &acc, unsigned int *err) {
+    const unsigned lane = lane_id();
+    const uint32_t q0 = min(q_lo + lane, q_hi - 1);
+    uint32_t r = 0, e = nv;  // largest r < nv with pre[r] <= q0
+    while (e - r > 1) {
+        const uint32_t m = (r + e) >> 1;
+        if (spre[m] <= q0) r = m; else e = m;
+    }
+    uint32_t lo = spre[r], hi = spre[r + 1];
+    unsigned long long base = sb[r] - lo;
+    uint32_t split = lo + ssplit[r];
+    Hits hits;
+    for (uint32_t j0 = q_lo; j0 < q_hi; j0 += 32u * U) {
+        uint32_t w[U];
+        bool in_a[U];
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            const uint32_t q = j0 + (uint32_t)i * 32u + lane;
+            bool valid = q < q_hi;
+            if (valid) {
+                while (q >= hi) {
+                    if (r + 1 >= nv) {  // past the last range: inconsistent prefix
+                        atomicOr(err, kGuardWalk);
+                        valid = false;
+                        break;
+                    }
+                    ++r;
+                    lo = hi;
+                    hi = spre[r + 1];
+                    base = sb[r] - lo;
+                    split = lo + ssplit[r];
+                }
+            }
+            w[i] = valid ? __ldg(adj2 + base + q) : kEmpty;
+            in_a[i] = q < split;
+        }
+        lookup_all(set, w, in_a, hits);
     }
     hits.flush(acc);
 }
@@ -216,62 +333,109 @@ __device__ __forceinline__ void flush(const Acc &acc, Ctl *ctl, int c, unsigned 
     }
 }
 
+__device__ __forceinline__ unsigned long long rec_start(const uint4 &r) {
+    return ((unsigned long long)r.y << 32) | r.x;
+}
+
+// Long probe ranges are walked in kSeg pieces, one warp each.  In the warp
+// class, ranges shorter than flat_cap (a tuning knob) are concatenated
+// (probe_flat) so that every lane has work.
+constexpr uint32_t kSeg = 512;
+
 // ---------------------------------------------------------------------------- warp class
 
-__global__ void __launch_bounds__(1024) k_isect_warp(const uint2 *__restrict__ tasks, const uint32_t *__restrict__ rows,
+// Per-warp shared metadata of the 32 probe records a warp holds at a time.
+struct WarpMeta {
+    unsigned long long b[32];
+    uint32_t pre[33];
+    uint32_t split[32];
+};
+constexpr size_t kWarpMetaBytes = (sizeof(WarpMeta) + 15) & ~size_t(15);
+
+__global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__ tasks, const uint32_t *__restrict__ rows,
                                                      const uint32_t *__restrict__ ntask,
-                                                     const uint64_t *__restrict__ off2,
+                                                     const uint64_t *__restrict__ rp,
                                                      const uint32_t *__restrict__ adj2,
-                                                     const uint32_t *__restrict__ hcnt, Ctl *ctl, uint32_t table_buckets,
-                                                     unsigned long long first, unsigned long long last,
-                                                     GroupSpec groups) {
+                                                     const uint32_t *__restrict__ fcnt,
+                                                     const uint64_t *__restrict__ eoff,
+                                                     const uint4 *__restrict__ erec, Ctl *ctl, uint32_t table_buckets,
+                                                     uint32_t flat_cap, unsigned long long first,
+                                                     unsigned long long last, GroupSpec groups) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
-    uint4 *bk = reinterpret_cast<uint4 *>(smem_raw) + (size_t)warp * table_buckets;
+    unsigned char *mine = smem_raw + (size_t)warp * (16ull * table_buckets + kWarpMetaBytes);
+    uint4 *bk = reinterpret_cast<uint4 *>(mine);
+    WarpMeta *meta = reinterpret_cast<WarpMeta *>(mine + 16ull * table_buckets);
     Acc acc;
     unsigned long long build = 0, done = 0, inserts = 0;
     uint32_t cur_row = 0xFFFFFFFFu;
-    BucketTable T{bk, 0, 0};
+    BucketTable T{bk, 0, 0, &ctl->error};
+    const long long t_start = clock64();
     for (;;) {
         unsigned long long k = 0;
-        if (lane == 0) k = first + atomicAdd(&ctl->task_next[0], 1u);
+        if (lane == 0) {
+            k = first + atomicAdd(&ctl->task_next[0], 1u);
+            if (clock64() - t_start > kWatchdogCycles) {
+                atomicOr(&ctl->error, kGuardWatchdog);
+                k = last;
+            }
+        }
         k = __shfl_sync(0xFFFFFFFFu, k, 0);
         if (k >= last) break;
         const uint2 task = tasks[k];
         const uint32_t u = rows[task.x], nt = ntask[task.x];
-        const uint64_t ub = off2[u];
-        const uint32_t su = (uint32_t)(off2[u + 1] - ub);
-        const uint32_t hu = hcnt[u];
-        const uint32_t k_lo = (uint32_t)((uint64_t)task.y * hu / nt), k_hi = (uint32_t)((uint64_t)(task.y + 1) * hu / nt);
+        const uint32_t fu = fcnt[u];
+        const uint64_t hb = rp[u] + fu;
+        const uint32_t su = (uint32_t)(rp[u + 1] - hb);
+        const uint4 *rec = erec + eoff[u];
+        const uint32_t k_lo = (uint32_t)((uint64_t)task.y * fu / nt), k_hi = (uint32_t)((uint64_t)(task.y + 1) * fu / nt);
         if (task.x != cur_row) {  // tasks of one row reuse its table
             __syncwarp();
-            T = clear_table(bk, su, table_buckets, lane, 32);
+            T = clear_table(bk, su, table_buckets, lane, 32, &ctl->error);
             __syncwarp();
-            fill_table(T, adj2 + ub, su, lane, 32);
+            fill_table(T, adj2 + hb, su, lane, 32);
             __syncwarp();
             cur_row = task.x;
             inserts += su;
         }
-        if (task.y == 0) build += su;
+        if (task.y == 0) build += su + fu;
         ++done;
         const unsigned long long before = acc.same + acc.cross;
         for (uint32_t k0 = k_lo; k0 < k_hi; k0 += 32) {
             const uint32_t kk = k0 + lane;
-            uint32_t len = 0, hv = 0;
-            unsigned long long b = 0;
-            if (kk < k_hi) {
-                const uint32_t v = adj2[ub + kk];
-                b = off2[v];
-                len = (uint32_t)(off2[v + 1] - b);
-                hv = hcnt[v];
-            }
-            acc.probes += len;
-            const uint32_t cnt = min(32u, k_hi - k0);
-            for (uint32_t t = 0; t < cnt; ++t) {
+            uint4 r = make_uint4(0, 0, 0, 0);
+            if (kk < k_hi) r = rec[kk];
+            acc.probes += r.z;
+            const unsigned long long b = rec_start(r);
+            // long ranges: the whole warp on each in turn
+            const bool longr = r.z >= flat_cap;
+            unsigned lm = __ballot_sync(0xFFFFFFFFu, longr);
+            while (lm) {
+                const int t = __ffs(lm) - 1;
+                lm &= lm - 1;
                 const unsigned long long bt = __shfl_sync(0xFFFFFFFFu, b, t);
-                const uint32_t lt = __shfl_sync(0xFFFFFFFFu, len, t);
-                const uint32_t ht = __shfl_sync(0xFFFFFFFFu, hv, t);
+                const uint32_t lt = __shfl_sync(0xFFFFFFFFu, r.z, t);
+                const uint32_t ht = __shfl_sync(0xFFFFFFFFu, r.w, t);
                 probe_row<BucketTable::kUnroll>(T, adj2, bt, 0, lt, ht, acc);
+            }
+            // short ranges: concatenated
+            const uint32_t sl = longr ? 0u : r.z;
+            uint32_t incl = sl;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= (unsigned)o) incl += y;
+            }
+            const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            if (total) {
+                meta->b[lane] = b;
+                meta->pre[lane] = incl - sl;
+                meta->split[lane] = r.w;
+                if (lane == 31) meta->pre[32] = total;
+                __syncwarp();
+                probe_flat<BucketTable::kUnroll>(T, adj2, meta->b, meta->pre, meta->split, 32, 0, total, acc,
+                                                 &ctl->error);
+                __syncwarp();
             }
         }
         if (groups.n_groups) {
@@ -285,28 +449,43 @@ __global__ void __launch_bounds__(1024) k_isect_warp(const uint2 *__restrict__ t
 
 // ---------------------------------------------------------------------------- tiny class
 
-// Sorted intersection size of a[0..na) (shared, column `stride` apart) and
-// b[0..nb) (global), both ascending: two-pointer merge.
-__device__ __forceinline__ uint32_t merge_count(const uint32_t *a, uint32_t stride, uint32_t na,
-                                                const uint32_t *__restrict__ b, uint32_t nb) {
+// Size of the intersection of a[0..na) (shared, column `stride` apart) and
+// b[0..nb) (global), both descending: two-pointer merge.
+__device__ __forceinline__ uint32_t merge_count_desc(const uint32_t *a, uint32_t stride, uint32_t na,
+                                                     const uint32_t *__restrict__ b, uint32_t nb) {
     uint32_t i = 0, j = 0, c = 0;
     while (i < na && j < nb) {
         const uint32_t x = a[i * stride], y = __ldg(b + j);
         c += x == y;
-        i += x <= y;
-        j += y <= x;
+        i += x >= y;
+        j += y >= x;
     }
     return c;
 }
 
-// Tiny class: one thread per row u (s(u) <= tiny_cap).  u's row is copied to
-// a shared column; for every v in H(u) the G0 parts H(u), H(v) and the G1
-// parts of the two rows are intersected by sorted merges -- the rows keep the
-// CSR order, so each part is ascending.
+// Size of the intersection of a[0..na) (shared, column `stride` apart) and
+// b[0..nb) (global), in any order: every pair compared (na <= tiny_cap).
+__device__ __forceinline__ uint32_t scan_count(const uint32_t *a, uint32_t stride, uint32_t na,
+                                               const uint32_t *__restrict__ b, uint32_t nb) {
+    uint32_t c = 0;
+    for (uint32_t j = 0; j < nb; ++j) {
+        const uint32_t y = __ldg(b + j);
+        for (uint32_t i = 0; i < na; ++i) c += a[i * stride] == y;
+    }
+    return c;
+}
+
+// Tiny class: one thread per row u (s(u) <= tiny_cap, deg(u) <= 4 tiny_cap,
+// so every v in F(u), which comes later in the working order, has at most
+// 4 tiny_cap neighbours too).  A(u) and G1(u) are copied to a shared column;
+// for every v in F(u) the A parts (both descending) are merged -- only
+// elements ranked below u can match, since A(u) holds no other -- and the G1
+// parts compared pairwise.
 __global__ void __launch_bounds__(256) k_isect_tiny(const uint32_t *__restrict__ rows, uint32_t lo, uint32_t hi,
-                                                    const uint64_t *__restrict__ off2,
+                                                    const uint64_t *__restrict__ rp,
                                                     const uint32_t *__restrict__ adj2,
-                                                    const uint32_t *__restrict__ hcnt, Ctl *ctl, uint32_t tiny_cap,
+                                                    const uint32_t *__restrict__ fcnt,
+                                                    const uint32_t *__restrict__ gcnt, Ctl *ctl, uint32_t tiny_cap,
                                                     GroupSpec groups) {
     extern __shared__ uint32_t srow[];  // tiny_cap x blockDim, column per thread
     uint32_t *mine = srow + threadIdx.x;
@@ -316,23 +495,25 @@ __global__ void __launch_bounds__(256) k_isect_tiny(const uint32_t *__restrict__
     const uint32_t total = (uint32_t)((uint64_t)gridDim.x * blockDim.x);
     for (uint32_t i = lo + blockIdx.x * blockDim.x + threadIdx.x; i < hi; i += total) {
         const uint32_t u = rows[i];
-        const uint64_t ub = off2[u];
-        const uint32_t su = (uint32_t)(off2[u + 1] - ub), hu = hcnt[u];
-        for (uint32_t k = 0; k < su; ++k) mine[k * stride] = __ldg(adj2 + ub + k);
+        const uint64_t ub = rp[u];
+        const uint32_t fu = fcnt[u], gu = gcnt[u];
+        const uint32_t su = (uint32_t)(rp[u + 1] - ub) - fu, au = su - gu;
+        for (uint32_t k = 0; k < su; ++k) mine[k * stride] = __ldg(adj2 + ub + fu + k);  // A(u) then G1(u)
         uint32_t same = 0, cross = 0;
         unsigned long long probes = 0;
-        for (uint32_t k = 0; k < hu; ++k) {
-            const uint32_t v = mine[k * stride];
-            const uint64_t vb = off2[v];
-            const uint32_t vs = (uint32_t)(off2[v + 1] - vb), hv = hcnt[v];
-            same += merge_count(mine, stride, hu, adj2 + vb, hv);
-            cross += merge_count(mine + hu * stride, stride, su - hu, adj2 + vb + hv, vs - hv);
-            probes += vs;
+        for (uint32_t k = 0; k < fu; ++k) {
+            const uint32_t v = __ldg(adj2 + ub + k);
+            const uint64_t vb = rp[v], ve = rp[v + 1];
+            const uint32_t fv = fcnt[v], gv = gcnt[v];
+            const uint32_t av = (uint32_t)(ve - vb) - fv - gv;
+            same += merge_count_desc(mine, stride, au, adj2 + vb + fv, av);
+            cross += scan_count(mine + au * stride, stride, gu, adj2 + (ve - gv), gv);
+            probes += av + gv;
         }
         acc.same += same;
         acc.cross += cross;
         acc.probes += probes;
-        build += su;
+        build += su + fu;
         ++done;
         if (groups.n_groups && same + cross) atomicAdd(&groups.counts[group_of(groups, u)], (unsigned long long)(same + cross));
     }
@@ -342,12 +523,9 @@ __global__ void __launch_bounds__(256) k_isect_tiny(const uint32_t *__restrict__
 
 // ---------------------------------------------------------------------------- block and hub classes
 
-// Per-task shared metadata of up to max_v out-neighbour rows.  Rows are cut
-// into segments of kSeg positions; seg[i] is the exclusive prefix of segment
-// counts, so warps can take segments one at a time and no long row holds up
-// the block.
-constexpr uint32_t kSeg = 512;
-
+// Per-task shared metadata of up to max_v probe records: start, length and
+// split of each range, and seg = exclusive prefix of their kSeg-piece counts.
+// Warps take pieces one at a time, so no long range holds up the block.
 struct SliceSmem {
     unsigned long long *b;
     uint32_t *len, *h, *seg;
@@ -364,12 +542,12 @@ __device__ __forceinline__ SliceSmem carve_slice(unsigned char *p, uint32_t max_
 
 __host__ __device__ constexpr size_t slice_smem_bytes(uint32_t max_v) { return (20ull * max_v + 4 + 15) & ~15ull; }
 
-// Block-wide exclusive scan of the segment counts of rows 0..nv-1 into
+// Block-wide exclusive scan of the piece counts of ranges 0..nv-1 into
 // seg[0..nv]; all threads of the block call it; ends with a barrier.
 __device__ __forceinline__ void scan_segments(const uint32_t *len, uint32_t *seg, uint32_t nv) {
     __shared__ uint32_t warp_tot[32];
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const uint32_t per = (nv + blockDim.x - 1) / blockDim.x;  // rows per thread (contiguous)
+    const uint32_t per = (nv + blockDim.x - 1) / blockDim.x;  // ranges per thread (contiguous)
     const uint32_t beg = threadIdx.x * per;
     uint32_t sum = 0;
     for (uint32_t i = 0; i < per; ++i)
@@ -403,20 +581,18 @@ __device__ __forceinline__ void scan_segments(const uint32_t *len, uint32_t *seg
     __syncthreads();
 }
 
-// Load the metadata of v = hrow[k], k in [k_lo, k_hi) (no barrier).
-__device__ __forceinline__ void load_slice(const SliceSmem &S, const uint32_t *__restrict__ hrow, uint32_t k_lo,
-                                           uint32_t k_hi, const uint64_t *__restrict__ off2,
-                                           const uint32_t *__restrict__ hcnt) {
+// Load the probe records of edges k in [k_lo, k_hi) of one row (no barrier).
+__device__ __forceinline__ void load_slice(const SliceSmem &S, const uint4 *__restrict__ rec, uint32_t k_lo,
+                                           uint32_t k_hi) {
     for (uint32_t i = threadIdx.x; i < k_hi - k_lo; i += blockDim.x) {
-        const uint32_t v = hrow[k_lo + i];
-        const unsigned long long b = off2[v];
-        S.b[i] = b;
-        S.len[i] = (uint32_t)(off2[v + 1] - b);
-        S.h[i] = hcnt[v];
+        const uint4 r = rec[k_lo + i];
+        S.b[i] = rec_start(r);
+        S.len[i] = r.z;
+        S.h[i] = r.w;
     }
 }
 
-// Warps take row segments of the slice one at a time (shared counter).
+// Warps take the slice's pieces one at a time (shared counter).
 template <class Set>
 __device__ __forceinline__ void probe_slice(const Set &set, const SliceSmem &S, uint32_t nv,
                                             const uint32_t *__restrict__ adj2, unsigned int *next, Acc &acc) {
@@ -427,7 +603,7 @@ __device__ __forceinline__ void probe_slice(const Set &set, const SliceSmem &S, 
         if (lane == 0) g = atomicAdd(next, 1u);
         g = __shfl_sync(0xFFFFFFFFu, g, 0);
         if (g >= total) break;
-        uint32_t a = 0, e = nv;  // row of segment g: largest t with seg[t] <= g
+        uint32_t a = 0, e = nv;  // range of piece g: largest t with seg[t] <= g
         while (e - a > 1) {
             const uint32_t m = (a + e) >> 1;
             if (S.seg[m] <= g) a = m; else e = m;
@@ -452,16 +628,22 @@ struct TaskSmem {
 // of `chunk` consecutive tasks, so the tasks of one row mostly stay on one
 // block and its table is built once.  All threads see the task.
 __device__ __forceinline__ bool next_task(Ctl *ctl, int c, unsigned long long first, unsigned long long last,
-                                          unsigned long long chunk, const uint2 *tasks, TaskSmem *ts) {
+                                          unsigned long long chunk, const uint2 *tasks, TaskSmem *ts,
+                                          long long t_start) {
     __syncthreads();  // everyone is done with the previous task
     if (threadIdx.x == 0) {
-        if (ts->chunk_pos >= ts->chunk_end) {
-            const unsigned long long k = first + (unsigned long long)atomicAdd(&ctl->task_next[c], 1u) * chunk;
-            ts->chunk_pos = k;
-            ts->chunk_end = k + chunk < last ? k + chunk : last;
+        if (clock64() - t_start > kWatchdogCycles) {
+            atomicOr(&ctl->error, kGuardWatchdog);
+            ts->task = make_uint2(0xFFFFFFFFu, 0u);
+        } else {
+            if (ts->chunk_pos >= ts->chunk_end) {
+                const unsigned long long k = first + (unsigned long long)atomicAdd(&ctl->task_next[c], 1u) * chunk;
+                ts->chunk_pos = k;
+                ts->chunk_end = k + chunk < last ? k + chunk : last;
+            }
+            const unsigned long long k = ts->chunk_pos++;
+            ts->task = k < ts->chunk_end ? tasks[k] : make_uint2(0xFFFFFFFFu, 0u);
         }
-        const unsigned long long k = ts->chunk_pos++;
-        ts->task = k < ts->chunk_end ? tasks[k] : make_uint2(0xFFFFFFFFu, 0u);
         ts->next = 0;
         ts->found = 0;
     }
@@ -476,48 +658,83 @@ __device__ __forceinline__ void init_task_smem(TaskSmem *ts) {
     }
 }
 
+// Block rows: shared bucket table, optionally behind a shared filter
+// (block_filter_log2 > 0).
+template <class Set>
+__device__ __forceinline__ Set make_block_set(uint4 *bk, uint32_t *filter, uint32_t filter_log2, unsigned int *err);
+template <>
+__device__ __forceinline__ BucketTable make_block_set<BucketTable>(uint4 *bk, uint32_t *, uint32_t, unsigned int *err) {
+    return BucketTable{bk, 0, 0, err};
+}
+template <>
+__device__ __forceinline__ FilteredTable make_block_set<FilteredTable>(uint4 *bk, uint32_t *filter, uint32_t filter_log2,
+                                                                       unsigned int *err) {
+    return FilteredTable{BucketTable{bk, 0, 0, err}, filter, 32u - filter_log2};
+}
+__device__ __forceinline__ BucketTable &table_of(BucketTable &s) { return s; }
+__device__ __forceinline__ BucketTable &table_of(FilteredTable &s) { return s.T; }
+
+template <class Set>
 __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict__ tasks, const uint32_t *__restrict__ rows,
                                                       const uint32_t *__restrict__ ntask,
-                                                      const uint64_t *__restrict__ off2,
+                                                      const uint64_t *__restrict__ rp,
                                                       const uint32_t *__restrict__ adj2,
-                                                      const uint32_t *__restrict__ hcnt, Ctl *ctl, uint32_t max_v,
-                                                      uint32_t table_buckets, unsigned long long chunk,
-                                                      unsigned long long first, unsigned long long last,
-                                                      GroupSpec groups) {
+                                                      const uint32_t *__restrict__ fcnt,
+                                                      const uint64_t *__restrict__ eoff,
+                                                      const uint4 *__restrict__ erec, Ctl *ctl, uint32_t max_v,
+                                                      uint32_t table_buckets, uint32_t filter_log2,
+                                                      unsigned long long chunk, unsigned long long first,
+                                                      unsigned long long last, GroupSpec groups) {
+    constexpr bool kFiltered = sizeof(Set) != sizeof(BucketTable);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TaskSmem ts;
     const unsigned lane = lane_id();
     const SliceSmem S = carve_slice(smem_raw, max_v);
     uint4 *bk = reinterpret_cast<uint4 *>(smem_raw + slice_smem_bytes(max_v));
+    uint32_t *filter = reinterpret_cast<uint32_t *>(bk + table_buckets);
+    const uint32_t filter_words = kFiltered ? 1u << (filter_log2 - 5) : 0u;
+    const uint32_t fshift = 32u - filter_log2;
     Acc acc;
     unsigned long long build = 0, done = 0, inserts = 0;
     uint32_t cur_row = 0xFFFFFFFFu;
-    BucketTable T{bk, 0, 0};
+    Set set = make_block_set<Set>(bk, filter, filter_log2, &ctl->error);
     init_task_smem(&ts);
-    while (next_task(ctl, 1, first, last, chunk, tasks, &ts)) {
+    const long long t_start = clock64();
+    while (next_task(ctl, 1, first, last, chunk, tasks, &ts, t_start)) {
         const uint2 task = ts.task;
         const uint32_t u = rows[task.x], nt = ntask[task.x];
-        const uint64_t ub = off2[u];
-        const uint32_t su = (uint32_t)(off2[u + 1] - ub);
-        const uint32_t hu = hcnt[u];
-        const uint32_t k_lo = (uint32_t)((uint64_t)task.y * hu / nt), k_hi = (uint32_t)((uint64_t)(task.y + 1) * hu / nt);
+        const uint32_t fu = fcnt[u];
+        const uint64_t hb = rp[u] + fu;
+        const uint32_t su = (uint32_t)(rp[u + 1] - hb);
+        const uint32_t k_lo = (uint32_t)((uint64_t)task.y * fu / nt), k_hi = (uint32_t)((uint64_t)(task.y + 1) * fu / nt);
         const bool rebuild = task.x != cur_row;
-        if (rebuild) T = clear_table(bk, su, table_buckets, threadIdx.x, blockDim.x);
-        load_slice(S, adj2 + ub, k_lo, k_hi, off2, hcnt);
+        if (rebuild) {
+            table_of(set) = clear_table(bk, su, table_buckets, threadIdx.x, blockDim.x, &ctl->error);
+            if constexpr (kFiltered)
+                for (uint32_t j = threadIdx.x; j < filter_words; j += blockDim.x) filter[j] = 0u;
+        }
+        load_slice(S, erec + eoff[u], k_lo, k_hi);
         __syncthreads();
         scan_segments(S.len, S.seg, k_hi - k_lo);
         if (rebuild) {
-            fill_table(T, adj2 + ub, su, threadIdx.x, blockDim.x);
+            for (uint32_t j = threadIdx.x; j < su; j += blockDim.x) {
+                const uint32_t w = adj2[hb + j];
+                table_insert(table_of(set), w);
+                if constexpr (kFiltered) {
+                    const uint32_t f = filter_bit(w, fshift);
+                    atomicOr(filter + (f >> 5), 1u << (f & 31));
+                }
+            }
             __syncthreads();
             cur_row = task.x;
             if (threadIdx.x == 0) inserts += su;
         }
         if (threadIdx.x == 0) {
-            if (task.y == 0) build += su;
+            if (task.y == 0) build += su + fu;
             ++done;
         }
         const unsigned long long before = acc.same + acc.cross;
-        probe_slice(T, S, k_hi - k_lo, adj2, &ts.next, acc);
+        probe_slice(set, S, k_hi - k_lo, adj2, &ts.next, acc);
         if (groups.n_groups) {
             const unsigned long long found = warp_sum(acc.same + acc.cross - before);
             if (lane == 0 && found) atomicAdd(&ts.found, found);
@@ -529,14 +746,15 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
     if (threadIdx.x == 0 && inserts) atomicAdd(&ctl->cls_inserts[1], inserts);
 }
 
-// Set the bits of hub rows rows[i0 .. i0+g) into bitmaps bits + r * words.
+// Set the bits of the hashed sets of hub rows rows[i0 .. i0+g) into bitmaps
+// bits + r * words (bit index = rank).
 __global__ void k_hub_set(const uint32_t *__restrict__ rows, uint32_t i0, uint32_t g,
-                          const uint64_t *__restrict__ off2, const uint32_t *__restrict__ adj2, uint32_t *bits,
-                          uint64_t words) {
+                          const uint64_t *__restrict__ rp, const uint32_t *__restrict__ fcnt,
+                          const uint32_t *__restrict__ adj2, uint32_t *bits, uint64_t words) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint32_t r = 0; r < g; ++r) {
         const uint32_t u = rows[i0 + r];
-        const uint64_t b = off2[u], e = off2[u + 1];
+        const uint64_t b = rp[u] + fcnt[u], e = rp[u + 1];
         uint32_t *bm = bits + (uint64_t)r * words;
         for (uint64_t j = b + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < e; j += stride) {
             const uint32_t w = adj2[j];
@@ -550,37 +768,39 @@ __global__ void k_hub_set(const uint32_t *__restrict__ rows, uint32_t i0, uint32
 __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__ tasks, unsigned long long first,
                                                     unsigned long long last, const uint32_t *__restrict__ rows,
                                                     const uint32_t *__restrict__ ntask, uint32_t i0,
-                                                    const uint64_t *__restrict__ off2, const uint32_t *__restrict__ adj2,
-                                                    const uint32_t *__restrict__ hcnt, Ctl *ctl, const uint32_t *bits,
-                                                    uint64_t words, uint32_t max_v, unsigned long long chunk,
-                                                    uint32_t filter_log2, GroupSpec groups) {
+                                                    const uint64_t *__restrict__ rp, const uint32_t *__restrict__ adj2,
+                                                    const uint32_t *__restrict__ fcnt,
+                                                    const uint64_t *__restrict__ eoff, const uint4 *__restrict__ erec,
+                                                    Ctl *ctl, const uint32_t *bits, uint64_t words, uint32_t max_v,
+                                                    unsigned long long chunk, uint32_t filter_log2, GroupSpec groups) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TaskSmem ts;
     const unsigned lane = lane_id();
     const SliceSmem S = carve_slice(smem_raw, max_v);
     uint32_t *filter = reinterpret_cast<uint32_t *>(smem_raw + slice_smem_bytes(max_v));
-    const uint32_t kFilterWords = 1u << (filter_log2 - 5);
+    const uint32_t filter_words = 1u << (filter_log2 - 5);
     const uint32_t fshift = 32u - filter_log2;
     Acc acc;
     unsigned long long build = 0, done = 0, inserts = 0;
     uint32_t cur_row = 0xFFFFFFFFu;
     init_task_smem(&ts);
-    while (next_task(ctl, 2, first, last, chunk, tasks, &ts)) {
+    const long long t_start = clock64();
+    while (next_task(ctl, 2, first, last, chunk, tasks, &ts, t_start)) {
         const uint2 task = ts.task;
         const uint32_t u = rows[task.x], nt = ntask[task.x];
-        const uint64_t ub = off2[u];
-        const uint32_t su = (uint32_t)(off2[u + 1] - ub);
-        const uint32_t hu = hcnt[u];
-        const uint32_t k_lo = (uint32_t)((uint64_t)task.y * hu / nt), k_hi = (uint32_t)((uint64_t)(task.y + 1) * hu / nt);
+        const uint32_t fu = fcnt[u];
+        const uint64_t hb = rp[u] + fu;
+        const uint32_t su = (uint32_t)(rp[u + 1] - hb);
+        const uint32_t k_lo = (uint32_t)((uint64_t)task.y * fu / nt), k_hi = (uint32_t)((uint64_t)(task.y + 1) * fu / nt);
         const bool rebuild = task.x != cur_row;
         if (rebuild)
-            for (uint32_t j = threadIdx.x; j < kFilterWords; j += blockDim.x) filter[j] = 0u;
-        load_slice(S, adj2 + ub, k_lo, k_hi, off2, hcnt);
+            for (uint32_t j = threadIdx.x; j < filter_words; j += blockDim.x) filter[j] = 0u;
+        load_slice(S, erec + eoff[u], k_lo, k_hi);
         __syncthreads();
         scan_segments(S.len, S.seg, k_hi - k_lo);
         if (rebuild) {
             for (uint32_t j = threadIdx.x; j < su; j += blockDim.x) {
-                const uint32_t f = filter_bit(adj2[ub + j], fshift);
+                const uint32_t f = filter_bit(adj2[hb + j], fshift);
                 atomicOr(filter + (f >> 5), 1u << (f & 31));
             }
             __syncthreads();
@@ -588,7 +808,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
             if (threadIdx.x == 0) inserts += su;
         }
         if (threadIdx.x == 0) {
-            if (task.y == 0) build += su;
+            if (task.y == 0) build += su + fu;
             ++done;
         }
         const HubSet H{filter, bits + (uint64_t)(task.x - i0) * words, fshift};
@@ -616,8 +836,13 @@ uint32_t pow2_at_least(uint64_t x, uint32_t lo) {
 // Buckets per table: enough for load factor 1/2 at the class cap.
 uint32_t warp_table_buckets(const Tuning &tu) { return pow2_at_least((tu.warp_cap + 1) / 2, 16); }
 uint32_t block_table_buckets(const Tuning &tu) { return pow2_at_least((tu.block_cap + 1) / 2, 16); }
-size_t warp_kernel_smem(const Tuning &tu) { return (size_t)tu.warps_per_block * 16ull * warp_table_buckets(tu); }
-size_t block_kernel_smem(const Tuning &tu) { return slice_smem_bytes(tu.max_v) + 16ull * block_table_buckets(tu); }
+size_t warp_kernel_smem(const Tuning &tu) {
+    return (size_t)tu.warps_per_block * (16ull * warp_table_buckets(tu) + kWarpMetaBytes);
+}
+size_t block_kernel_smem(const Tuning &tu) {
+    return slice_smem_bytes(tu.max_v) + 16ull * block_table_buckets(tu) +
+           (tu.block_filter_log2 ? (1ull << tu.block_filter_log2) / 8 : 0);
+}
 size_t hub_kernel_smem(const Tuning &tu) { return slice_smem_bytes(tu.max_v) + (1ull << tu.hub_filter_log2) / 8; }
 
 tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
@@ -635,7 +860,7 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         const size_t smem = 4ull * tu.tiny_cap * 256;
         TC_CUDA(ctx, cudaFuncSetAttribute(k_isect_tiny, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const uint32_t grid = std::min<uint32_t>((hi3 - lo3 + 255) / 256, (uint32_t)ctx->num_sms * 8u);
-        k_isect_tiny<<<grid, 256, smem, s>>>(b.rows[3], lo3, hi3, b.off2, b.adj2, b.hcnt, ctx->d_ctl, tu.tiny_cap,
+        k_isect_tiny<<<grid, 256, smem, s>>>(b.rows[3], lo3, hi3, b.rp, b.adj2, b.fcnt, b.gcnt, ctx->d_ctl, tu.tiny_cap,
                                              b.groups);
         note_launch(ctx);
     }
@@ -659,25 +884,27 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         uint64_t grid = (uint64_t)ctx->num_sms * per_sm;
         const uint64_t need = (hi0 - lo0 + tu.warps_per_block - 1) / tu.warps_per_block;
         if (grid > need) grid = need;
-        k_isect_warp<<<(unsigned)grid, 32 * tu.warps_per_block, smem, s>>>(b.tasks[0], b.rows[0], b.ntask[0], b.off2,
-                                                                            b.adj2, b.hcnt, ctx->d_ctl,
-                                                                            warp_table_buckets(tu), lo0, hi0, b.groups);
+        k_isect_warp<<<(unsigned)grid, 32 * tu.warps_per_block, smem, s>>>(b.tasks[0], b.rows[0], b.ntask[0], b.rp,
+                                                                            b.adj2, b.fcnt, b.eoff, b.erec, ctx->d_ctl,
+                                                                            warp_table_buckets(tu), tu.flat_cap, lo0, hi0,
+                                                                            b.groups);
         note_launch(ctx);
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[5], s));
     if (hi1 > lo1) {
         const size_t smem = block_kernel_smem(tu);
-        TC_CUDA(ctx, cudaFuncSetAttribute(k_isect_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        auto kern = tu.block_filter_log2 ? k_isect_block<FilteredTable> : k_isect_block<BucketTable>;
+        TC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
-        TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect_block, tu.block_threads, smem));
+        TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tu.block_threads, smem));
         if (per_sm < 1) per_sm = 1;
         uint64_t grid = (uint64_t)ctx->num_sms * per_sm;
         if (grid > hi1 - lo1) grid = hi1 - lo1;
         const unsigned long long chunk = std::max<unsigned long long>(1, (hi1 - lo1) / (grid * 8));
-        k_isect_block<<<(unsigned)grid, tu.block_threads, smem, s>>>(b.tasks[1], b.rows[1], b.ntask[1], b.off2, b.adj2,
-                                                                     b.hcnt, ctx->d_ctl, tu.max_v,
-                                                                     block_table_buckets(tu), chunk, lo1, hi1,
-                                                                     b.groups);
+        kern<<<(unsigned)grid, tu.block_threads, smem, s>>>(b.tasks[1], b.rows[1], b.ntask[1], b.rp, b.adj2, b.fcnt,
+                                                            b.eoff, b.erec, ctx->d_ctl, tu.max_v, block_table_buckets(tu),
+                                                            tu.block_filter_log2, chunk, lo1, hi1,
+                                                            b.groups);
         note_launch(ctx);
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[6], s));
@@ -699,13 +926,14 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
             if (first >= last) continue;  // none of this group's tasks is in this shard
             TC_CUDA(ctx, cudaMemsetAsync(b.hub_bits, 0, 4ull * b.hub_words * g, s));
             TC_CUDA(ctx, cudaMemsetAsync(&ctx->d_ctl->task_next[2], 0, sizeof(unsigned), s));
-            k_hub_set<<<(unsigned)ctx->num_sms * 4u, 256, 0, s>>>(b.rows[2], i0, g, b.off2, b.adj2, b.hub_bits,
+            k_hub_set<<<(unsigned)ctx->num_sms * 4u, 256, 0, s>>>(b.rows[2], i0, g, b.rp, b.fcnt, b.adj2, b.hub_bits,
                                                                  b.hub_words);
             uint64_t grid = (uint64_t)ctx->num_sms * per_sm;
             if (grid > last - first) grid = last - first;
             const unsigned long long chunk = std::max<unsigned long long>(1, (last - first) / (grid * 4));
             k_isect_hub<<<(unsigned)grid, tu.hub_threads, smem, s>>>(b.tasks[2], first, last, b.rows[2], b.ntask[2], i0,
-                                                                     b.off2, b.adj2, b.hcnt, ctx->d_ctl, b.hub_bits,
+                                                                     b.rp, b.adj2, b.fcnt, b.eoff, b.erec, ctx->d_ctl,
+                                                                     b.hub_bits,
                                                                      b.hub_words, tu.max_v, chunk, tu.hub_filter_log2,
                                                                      b.groups);
             note_launch(ctx, 2);

@@ -20,11 +20,25 @@ struct PipeBufs {
     uint64_t *fpref = nullptr;      // [n+1] their exclusive prefix
     uint32_t *R = nullptr;          // [n]   unvisited vertices after the first BFS
     uint32_t *parent = nullptr;     // [n]   hooking forest
-    // partition / orientation / compaction
-    uint32_t *hcnt = nullptr;       // [n]   |G0 out-list(x)|
-    uint32_t *scnt = nullptr;       // [n]   |G0 out-list(x)| + |G1(x)|
-    uint64_t *off2 = nullptr;       // [n+1] offsets of the compacted rows
-    uint32_t *adj2 = nullptr;       // [S]   rows [G0 out-list | G1 list], each part ascending
+    // ranks (position in the working order)
+    uint32_t *rank = nullptr;       // [n]   (degree order only; the id order uses the id)
+    uint2 *lv = nullptr;            // [n]   {rank, level}
+    uint32_t *lvp = nullptr;        // [n]   rank << 8 | level (only when n <= 2^24 and levels < 255)
+    unsigned long long *rkeys0 = nullptr, *rkeys1 = nullptr;  // [n] radix-sort keys
+    uint32_t *rcounts = nullptr;    // radix digit counts per tile
+    uint64_t *roffs = nullptr;      // their scan
+    // partition / orientation / rows: every vertex keeps its CSR slots
+    // [rp[x], rp[x+1]) rewritten as [ F(x) | A(x) | G1(x) ]
+    uint32_t *fcnt = nullptr;       // [n]   |F(x)|  horizontal out-neighbours (ids)
+    uint32_t *gcnt = nullptr;       // [n]   |G1(x)| level-spanning neighbours (ranks)
+    uint32_t *adj2 = nullptr;       // [S]   the rewritten rows; A(x) (ranks) is descending
+    uint32_t *big = nullptr;        // [n]   rows whose A part the block sorter sorts
+    uint4 *vmeta = nullptr;         // [n]   {A start lo, A start hi, |A(x)|, |G1(x)|}
+    uint32_t *chunk_row = nullptr;  // first row of every chunk of kRecChunk probe records
+    uint64_t *eoff = nullptr;       // [n+1] exclusive prefix of fcnt: first probe record of x
+    uint4 *erec = nullptr;          // [|E0|] probe record per oriented horizontal edge u -> v:
+                                    //        {start lo, start hi, length, split}
+    uint64_t erec_cap = 0;
     // intersection planning, per class c (0 warp, 1 block, 2 hub)
     uint32_t *rows[4] = {};         // [n]   rows u of class c (0 warp, 1 block, 2 hub, 3 tiny)
     uint32_t *ntask[3] = {};        // [n]   tasks per row
@@ -32,7 +46,7 @@ struct PipeBufs {
     uint2 *tasks[3] = {};           // {row index i, slice t} per task (carved after planning)
     uint2 *task_pool = nullptr;     // capacity task_cap
     uint64_t task_cap = 0;
-    uint32_t *hub_bits = nullptr;   // hub_group bitmaps of hub_words words each
+    uint32_t *hub_bits = nullptr;   // hub_group bitmaps of hub_words words each (indexed by rank)
     uint64_t hub_words = 0;
     uint64_t *scan_tmp = nullptr;
     // batched counting of a disjoint union
@@ -41,6 +55,8 @@ struct PipeBufs {
 
 tc_status compute_levels(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t slots);
 tc_status selftest_barrier(tc_ctx *ctx, uint32_t timeout_ms);
+// rank of every vertex in the working order, packed with its level (lv)
+tc_status compute_ranks(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_deg);
 // partition, orientation, compaction, classification and per-class task counts
 tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_deg);
 // scans of the per-class task counts (after the host has read the row counts)

@@ -1,111 +1,189 @@
 // rows.cu -- partition of E into E0 / E1, orientation of E0 by the working
-// order, and compaction into one row per vertex (Algorithm 4, partition loop).
+// order, and the rows the intersections read (Algorithm 4, partition loop).
 //
-// For every vertex x the compacted row is  [ H(x) | G1(x) ]  with
-//   H(x)  = { y in N(x) : L(y) == L(x), x precedes y }   (G0, oriented)
-//   G1(x) = { y in N(x) : L(y) != L(x) }                 (level-spanning)
-// each part ascending (the CSR row order is kept).  Because L(u) == L(v) on a
-// horizontal edge u -> v, a common element w of row(u) and row(v) lies in
-// H(u) and H(v) when L(w) == L(u) (a triangle inside G0, counted once at its
-// first edge: Algorithm 2 on G0) and in G1(u) and G1(v) otherwise (a triangle
-// with exactly one horizontal edge: the hashed G1 loop of Algorithm 4).  So
-// one intersection per horizontal edge counts both kinds, and the position of
-// w in row(v) (below or above |H(v)|) tells which kind it is.
+// Every vertex x keeps its CSR slots [rp[x], rp[x+1]); they are rewritten as
+//     [ F(x) | A(x) | G1(x) ]
+//   F(x)  = { y ~ x : L(y) == L(x), x precedes y }  horizontal out-neighbours, as vertex ids
+//   A(x)  = { y ~ x : L(y) == L(x), y precedes x }  horizontal in-neighbours, as ranks, descending
+//   G1(x) = { y ~ x : L(y) != L(x) }                level-spanning neighbours, as ranks
+// (rank = position in the working order).  A(x) is the set Algorithm 2 has
+// built for x once every row before x's is done.  For a horizontal edge u -> v
+// the intersections hash A(u) and G1(u) and probe the elements of A(v) ranked
+// below u -- which in descending order are the last ones of A(v) -- and all of
+// G1(v): one contiguous range at the end of v's slots.  k_records finds, for
+// every oriented edge, where that range starts (a binary search for rank(u) in
+// A(v)) and writes a probe record {start, length, split}.
 #include "pipeline.cuh"
 
 namespace tc {
 namespace {
 
-// Each lane owns one vertex x; rows of degree <= kSmallRow are handled by
-// their lane alone (sequential, in order), larger rows by the whole warp one
-// at a time (lanes stride over the row, ballots keep the order).
-constexpr uint32_t kSmallRow = 32;
+constexpr uint32_t kSmallRow = 32;    // rows of degree <= 32: one lane each
+constexpr uint32_t kWarpA = 1024;     // A parts up to this size: sorted by the warp in shared memory
+constexpr uint32_t kSortCap = 32768;  // A parts up to this size: sorted (larger: k_sort_big); beyond: unsorted
+constexpr int kFillThreads = 256;
 
-// Level and degree of a neighbour, either from the two arrays or from one
-// packed word (level << 24 | degree) when every level is < 255 and every
-// degree < 2^24: one random 4-byte read instead of two.
-struct LevelDeg {
-    const uint32_t *L, *deg, *packed;
-    __device__ __forceinline__ void get(uint32_t y, uint32_t &ly, uint32_t &dy) const {
-        if (packed) {
-            const uint32_t p = packed[y];
-            ly = p >> 24;
-            dy = p & 0xFFFFFFu;
-        } else {
-            ly = L[y];
-            dy = 0xFFFFFFFFu;  // loaded on demand
+// Sort buf[0..P) ascending (P a power of two) with one warp: bitonic network.
+__device__ __forceinline__ void warp_bitonic(uint32_t *buf, uint32_t P) {
+    const unsigned lane = lane_id();
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t i = lane; i < P; i += 32) {
+                const uint32_t l = i ^ j;
+                if (l > i) {
+                    const uint32_t a = buf[i], c = buf[l];
+                    if ((a > c) == ((i & k) == 0)) {
+                        buf[i] = c;
+                        buf[l] = a;
+                    }
+                }
+            }
+            __syncwarp();
         }
     }
-    __device__ __forceinline__ uint32_t degree(uint32_t y, uint32_t dy) const { return packed ? dy : deg[y]; }
-};
+}
 
-__device__ __forceinline__ bool is_h(uint32_t x, uint32_t dx, uint32_t lx, uint32_t y, const LevelDeg &ld,
-                                     uint32_t order, bool *is_g) {
-    uint32_t ly, dy;
-    ld.get(y, ly, dy);
-    if (ly != lx) {
-        *is_g = true;
-        return false;
+__device__ __forceinline__ uint32_t pow2_ceil(uint32_t a) {
+    uint32_t p = 1;
+    while (p < a) p <<= 1;
+    return p;
+}
+
+// One pass over every CSR row: F from the front, G1 from the back, A through
+// shared memory (sorted there) into the slots between them.  Rows of degree
+// <= 32 belong to one lane, which keeps A sorted by insertion in its own
+// column of the warp's buffer; longer rows are done by the whole warp, lanes
+// striding over the row and ballots keeping the order; their A part is sorted
+// in the warp's buffer when it fits, else written in CSR order and sorted
+// later by k_sort_big (or left unsorted beyond kSortCap).
+// Rank and level of a vertex: from the packed 4-byte word (rank << 8 |
+// level) when there is one, else from the {rank, level} pair.
+template <bool kPacked>
+__device__ __forceinline__ uint2 rank_level(const uint2 *__restrict__ lv, const uint32_t *__restrict__ lvp, uint32_t y) {
+    if constexpr (kPacked) {
+        const uint32_t p = lvp[y];
+        return make_uint2(p >> 8, p & 0xFFu);
+    } else {
+        return lv[y];
     }
-    *is_g = false;
-    return precedes(x, dx, y, ld.degree(y, dy), order);
 }
 
-__global__ void k_pack_level_deg(uint32_t n, const uint32_t *__restrict__ L, const uint32_t *__restrict__ deg,
-                                 uint32_t *__restrict__ packed) {
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
-        packed[v] = (L[v] << 24) | deg[v];
-}
-
-__global__ void k_row_count(uint32_t n, const uint64_t *__restrict__ rp, const uint32_t *__restrict__ col,
-                            const uint32_t *__restrict__ deg, const uint32_t *__restrict__ L, LevelDeg ld,
-                            uint32_t *__restrict__ hcnt, uint32_t *__restrict__ scnt, Ctl *ctl, uint32_t order) {
+template <bool kPacked>
+__global__ void __launch_bounds__(kFillThreads) k_row_fill(uint32_t n, const uint64_t *__restrict__ rp,
+                                                           const uint32_t *__restrict__ col,
+                                                           const uint2 *__restrict__ lv,
+                                                           const uint32_t *__restrict__ lvp, uint32_t *__restrict__ adj2,
+                                                           uint32_t *__restrict__ fcnt, uint32_t *__restrict__ gcnt,
+                                                           uint4 *__restrict__ vmeta, uint32_t *__restrict__ big,
+                                                           Ctl *ctl) {
+    __shared__ uint32_t sbuf[kFillThreads / 32][kWarpA];
     __shared__ unsigned long long s_e0;
     if (threadIdx.x == 0) s_e0 = 0;
     __syncthreads();
-    const unsigned lane = lane_id();
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t *buf = sbuf[warp];
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t n_round = ((uint64_t)n + 31) & ~uint64_t(31);
     unsigned long long e0 = 0;
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_round; x += stride) {
         const bool valid = x < n;
-        const uint32_t dx = valid ? deg[x] : 0;
-        const uint32_t lx = valid ? L[x] : 0;
         const uint64_t b = valid ? rp[x] : 0;
-        uint32_t h = 0, g = 0;
-        if (dx <= kSmallRow) {
+        const uint32_t dx = valid ? (uint32_t)(rp[x + 1] - b) : 0;
+        const uint2 me = valid ? rank_level<kPacked>(lv, lvp, (uint32_t)x) : make_uint2(0, 0);
+        if (valid && dx <= kSmallRow) {
+            uint32_t fp = 0, gp = 0, ap = 0;
             for (uint32_t j = 0; j < dx; ++j) {
-                bool isg;
-                if (is_h((uint32_t)x, dx, lx, col[b + j], ld, order, &isg)) ++h;
-                g += isg;
+                const uint32_t y = col[b + j];
+                const uint2 q = rank_level<kPacked>(lv, lvp, y);
+                if (q.y != me.y) {
+                    adj2[b + dx - 1 - gp++] = q.x;
+                } else if (me.x < q.x) {
+                    adj2[b + fp++] = y;
+                } else {  // insert into the lane's column, descending
+                    uint32_t i = ap++;
+                    while (i > 0 && buf[(i - 1) * 32 + lane] < q.x) {
+                        buf[i * 32 + lane] = buf[(i - 1) * 32 + lane];
+                        --i;
+                    }
+                    buf[i * 32 + lane] = q.x;
+                }
             }
+            for (uint32_t i = 0; i < ap; ++i) adj2[b + fp + i] = buf[i * 32 + lane];
+            fcnt[x] = fp;
+            gcnt[x] = gp;
+            const uint64_t as = b + fp;
+            vmeta[x] = make_uint4((uint32_t)as, (uint32_t)(as >> 32), ap, gp);
+            e0 += fp;
         }
-        unsigned big = __ballot_sync(0xFFFFFFFFu, dx > kSmallRow);
-        while (big) {
-            const int src = __ffs(big) - 1;
-            big &= big - 1;
+        __syncwarp();
+        unsigned pending = __ballot_sync(0xFFFFFFFFu, valid && dx > kSmallRow);
+        while (pending) {
+            const int src = __ffs(pending) - 1;
+            pending &= pending - 1;
             const uint32_t bx = (uint32_t)__shfl_sync(0xFFFFFFFFu, (unsigned long long)x, src);
             const uint32_t bd = __shfl_sync(0xFFFFFFFFu, dx, src);
-            const uint32_t bl = __shfl_sync(0xFFFFFFFFu, lx, src);
             const uint64_t bb = __shfl_sync(0xFFFFFFFFu, b, src);
-            uint32_t hh = 0, gg = 0;
-            for (uint32_t j = lane; j < bd; j += 32) {
-                bool isg;
-                if (is_h(bx, bd, bl, col[bb + j], ld, order, &isg)) ++hh;
-                gg += isg;
+            const uint32_t brx = __shfl_sync(0xFFFFFFFFu, me.x, src);
+            const uint32_t blx = __shfl_sync(0xFFFFFFFFu, me.y, src);
+            uint32_t fp = 0, gp = 0, ap = 0;
+            for (uint32_t j0 = 0; j0 < bd; j0 += 32) {
+                const uint32_t j = j0 + lane;
+                bool isF = false, isG = false, isA = false;
+                uint32_t y = 0, ry = 0;
+                if (j < bd) {
+                    y = col[bb + j];
+                    const uint2 q = rank_level<kPacked>(lv, lvp, y);
+                    ry = q.x;
+                    if (q.y != blx) isG = true;
+                    else if (brx < ry) isF = true;
+                    else isA = true;
+                }
+                const unsigned mF = __ballot_sync(0xFFFFFFFFu, isF);
+                const unsigned mG = __ballot_sync(0xFFFFFFFFu, isG);
+                const unsigned mA = __ballot_sync(0xFFFFFFFFu, isA);
+                if (isF) adj2[bb + fp + __popc(mF & lt)] = y;
+                if (isG) adj2[bb + bd - 1 - (gp + __popc(mG & lt))] = ry;
+                if (isA) {
+                    const uint32_t pos = ap + __popc(mA & lt);
+                    if (pos < kWarpA) buf[pos] = ry;
+                }
+                fp += __popc(mF);
+                gp += __popc(mG);
+                ap += __popc(mA);
             }
-            hh = warp_sum(hh);
-            gg = warp_sum(gg);
-            if ((int)lane == src) {
-                h = hh;
-                g = gg;
+            __syncwarp();
+            if (ap <= kWarpA) {
+                const uint32_t P = pow2_ceil(ap);
+                for (uint32_t i = ap + lane; i < P; i += 32) buf[i] = kEmpty;
+                __syncwarp();
+                warp_bitonic(buf, P);
+                for (uint32_t i = lane; i < ap; i += 32) adj2[bb + fp + i] = buf[ap - 1 - i];
+            } else {  // A in CSR order now; sorted by k_sort_big if it is not too long
+                uint32_t apos = 0;
+                for (uint32_t j0 = 0; j0 < bd; j0 += 32) {
+                    const uint32_t j = j0 + lane;
+                    bool isA = false;
+                    uint32_t ry = 0;
+                    if (j < bd) {
+                        const uint2 q = rank_level<kPacked>(lv, lvp, col[bb + j]);
+                        ry = q.x;
+                        isA = q.y == blx && ry < brx;
+                    }
+                    const unsigned mA = __ballot_sync(0xFFFFFFFFu, isA);
+                    if (isA) adj2[bb + fp + apos + __popc(mA & lt)] = ry;
+                    apos += __popc(mA);
+                }
+                if (lane == 0 && ap <= kSortCap) big[atomicAdd(&ctl->n_big, 1u)] = bx;
             }
-        }
-        if (valid) {
-            hcnt[x] = h;
-            scnt[x] = h + g;
-            e0 += h;
+            __syncwarp();
+            if (lane == 0) {
+                fcnt[bx] = fp;
+                gcnt[bx] = gp;
+                const uint64_t as = bb + fp;
+                vmeta[bx] = make_uint4((uint32_t)as, (uint32_t)(as >> 32), ap, gp);
+                e0 += fp;
+            }
         }
     }
     e0 = warp_sum(e0);
@@ -114,75 +192,61 @@ __global__ void k_row_count(uint32_t n, const uint64_t *__restrict__ rp, const u
     if (threadIdx.x == 0 && s_e0) atomicAdd(&ctl->e0, s_e0);
 }
 
-__global__ void k_row_fill(uint32_t n, const uint64_t *__restrict__ rp, const uint32_t *__restrict__ col,
-                           const uint32_t *__restrict__ deg, const uint32_t *__restrict__ L, LevelDeg ld,
-                           const uint32_t *__restrict__ hcnt, const uint64_t *__restrict__ off2,
-                           uint32_t *__restrict__ adj2, uint32_t order) {
-    const unsigned lane = lane_id();
-    const unsigned lt = (1u << lane) - 1u;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t n_round = ((uint64_t)n + 31) & ~uint64_t(31);
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_round; x += stride) {
-        const bool valid = x < n;
-        const uint32_t dx = valid ? deg[x] : 0;
-        const uint32_t lx = valid ? L[x] : 0;
-        const uint64_t b = valid ? rp[x] : 0;
-        const uint64_t base = valid && dx ? off2[x] : 0;
-        const uint32_t hx = valid && dx ? hcnt[x] : 0;
-        if (dx <= kSmallRow) {
-            uint32_t hp = 0, gp = 0;
-            for (uint32_t j = 0; j < dx; ++j) {
-                const uint32_t y = col[b + j];
-                bool isg;
-                if (is_h((uint32_t)x, dx, lx, y, ld, order, &isg)) adj2[base + hp++] = y;
-                else if (isg) adj2[base + hx + gp++] = y;
-            }
+// A parts longer than kWarpA (and at most kSortCap): one block per row sorts
+// it in shared memory (bitonic, padded with kEmpty) and writes it back
+// descending.  Persistent: blocks stride over the list the fill kernel built.
+__global__ void __launch_bounds__(1024) k_sort_big(const uint32_t *__restrict__ big, Ctl *ctl,
+                                                   const uint64_t *__restrict__ rp, const uint32_t *__restrict__ fcnt,
+                                                   const uint32_t *__restrict__ gcnt, uint32_t *__restrict__ adj2) {
+    extern __shared__ uint32_t sb[];  // kSortCap words
+    const uint32_t nb = ctl->n_big;
+    for (uint32_t i = blockIdx.x; i < nb; i += gridDim.x) {
+        const uint32_t x = big[i];
+        const uint64_t b = rp[x] + fcnt[x];
+        const uint32_t a = (uint32_t)(rp[x + 1] - b) - gcnt[x];
+        if (a > kSortCap) {  // not a row the fill kernel listed: report, leave it
+            if (threadIdx.x == 0) atomicOr(&ctl->error, 0x100u);
+            continue;
         }
-        unsigned big = __ballot_sync(0xFFFFFFFFu, dx > kSmallRow);
-        while (big) {
-            const int src = __ffs(big) - 1;
-            big &= big - 1;
-            const uint32_t bx = (uint32_t)__shfl_sync(0xFFFFFFFFu, (unsigned long long)x, src);
-            const uint32_t bd = __shfl_sync(0xFFFFFFFFu, dx, src);
-            const uint32_t bl = __shfl_sync(0xFFFFFFFFu, lx, src);
-            const uint64_t bb = __shfl_sync(0xFFFFFFFFu, b, src);
-            const uint64_t bbase = __shfl_sync(0xFFFFFFFFu, base, src);
-            const uint32_t bh = __shfl_sync(0xFFFFFFFFu, hx, src);
-            uint32_t hp = 0, gp = 0;
-            for (uint32_t j0 = 0; j0 < bd; j0 += 32) {
-                const uint32_t j = j0 + lane;
-                bool isH = false, isG = false;
-                uint32_t y = 0;
-                if (j < bd) {
-                    y = col[bb + j];
-                    isH = is_h(bx, bd, bl, y, ld, order, &isG);
+        const uint32_t P = pow2_ceil(a);
+        for (uint32_t t = threadIdx.x; t < P; t += blockDim.x) sb[t] = t < a ? adj2[b + t] : kEmpty;
+        __syncthreads();
+        for (uint32_t k = 2; k <= P; k <<= 1) {
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                for (uint32_t t = threadIdx.x; t < P; t += blockDim.x) {
+                    const uint32_t l = t ^ j;
+                    if (l > t) {
+                        const uint32_t p = sb[t], q = sb[l];
+                        if ((p > q) == ((t & k) == 0)) {
+                            sb[t] = q;
+                            sb[l] = p;
+                        }
+                    }
                 }
-                const unsigned mh = __ballot_sync(0xFFFFFFFFu, isH);
-                const unsigned mg = __ballot_sync(0xFFFFFFFFu, isG);
-                if (isH) adj2[bbase + hp + __popc(mh & lt)] = y;
-                if (isG) adj2[bbase + bh + gp + __popc(mg & lt)] = y;
-                hp += __popc(mh);
-                gp += __popc(mg);
+                __syncthreads();
             }
         }
+        for (uint32_t t = threadIdx.x; t < a; t += blockDim.x) adj2[b + t] = sb[a - 1 - t];
+        __syncthreads();
     }
 }
 
 // Rows with at least one oriented horizontal edge are the hashed side of the
-// intersections; split them by the size s(u) of their compacted row:
-// class 3 (tiny) s <= tiny_cap and degree <= 4 tiny_cap, class 0 (warp)
+// intersections; split them by the size s(u) = |A(u)| + |G1(u)| of the hashed
+// set: class 3 (tiny) s <= tiny_cap and degree <= 4 tiny_cap, class 0 (warp)
 // s <= warp_cap, class 1 (block) s <= block_cap, class 2 (hub).
 // The lists are built by a stable scan, so they (and the task lists made from
 // them) are in vertex order on every run: shards of a count agree on them.
-__global__ void k_class_flags(uint32_t n, const uint32_t *__restrict__ hcnt, const uint32_t *__restrict__ scnt,
-                              const uint32_t *__restrict__ deg, uint32_t *__restrict__ cls, Ctl *ctl,
-                              uint32_t warp_cap, uint32_t block_cap, uint32_t tiny_cap) {
+__global__ void k_class_flags(uint32_t n, const uint32_t *__restrict__ fcnt, const uint32_t *__restrict__ deg,
+                              uint32_t *__restrict__ cls, Ctl *ctl, uint32_t warp_cap, uint32_t block_cap,
+                              uint32_t tiny_cap) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     unsigned my_max = 0;
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
         uint32_t c = 4;  // no oriented horizontal edge: nothing to intersect
-        if (hcnt[x] > 0) {
-            const uint32_t s = scnt[x];
+        const uint32_t f = fcnt[x];
+        if (f > 0) {
+            const uint32_t s = deg[x] - f;
             c = s <= warp_cap ? 0u : (s <= block_cap ? 1u : 2u);
             if (s <= tiny_cap && deg[x] <= 4 * tiny_cap) c = 3;
             if (c == 1 || c == 2) my_max = s > my_max ? s : my_max;
@@ -211,33 +275,99 @@ __global__ void k_class_scatter(uint32_t n, const uint32_t *__restrict__ cls, ui
     if (blockIdx.x == 0 && threadIdx.x == 0) *n_rows = (unsigned int)pos[n];
 }
 
-// Split every hashed row u of class c into tasks (contiguous slices of H(u))
-// of about `target` probes: work(u) = sum of s(v) over v in H(u),
-// ntask = ceil(work(u) / max(task_work, min_mult * s(u))), at least
-// ceil(|H(u)| / max_v) (shared-memory metadata of one task), at most |H(u)|.
+// Probe records are made edge-parallel: the oriented edges u -> v are
+// numbered e = eoff[u] + k (v = F(u)[k]) and cut into chunks of kRecChunk;
+// chunk_row[c] is the row holding edge c * kRecChunk.
+constexpr uint32_t kRecChunk = 256;
+
+__global__ void k_chunk_rows(uint32_t n, const uint64_t *__restrict__ eoff, uint32_t *__restrict__ chunk_row) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+        const uint64_t lo = eoff[u], hi = eoff[u + 1];
+        for (uint64_t c = (lo + kRecChunk - 1) / kRecChunk; c * kRecChunk < hi; ++c) chunk_row[c] = (uint32_t)u;
+    }
+}
+
+// For every oriented edge u -> v: the number p of elements of A(v) ranked
+// below u (binary search in the descending A(v); all of A(v) when it was left
+// unsorted), and the probe record {start, length = |G1(v)| + p, split = p}
+// of the range at the end of v's slots.  One warp per chunk; every lane walks
+// from the chunk's first row to the rows of its own edges.
+__global__ void k_records(uint32_t n, const uint64_t *__restrict__ eoff, const uint32_t *__restrict__ chunk_row,
+                          const uint64_t *__restrict__ rp, const uint32_t *__restrict__ adj2,
+                          const uint2 *__restrict__ lv, const uint4 *__restrict__ vmeta, uint4 *__restrict__ erec) {
+    const unsigned lane = lane_id();
+    const uint64_t E = eoff[n];
+    const uint64_t chunks = (E + kRecChunk - 1) / kRecChunk;
+    const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t c = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < chunks; c += warps) {
+        const uint64_t e_lo = c * kRecChunk, e_hi = min(E, e_lo + kRecChunk);
+        uint32_t u = chunk_row[c];
+        uint64_t u_lo = eoff[u], u_hi = eoff[u + 1], fb = rp[u];
+        uint32_t ru = lv[u].x;
+        for (uint64_t e = e_lo + lane; e < e_hi; e += 32) {
+            while (e >= u_hi) {  // rows of no edge have u_lo == u_hi and are skipped
+                ++u;
+                u_lo = u_hi;
+                u_hi = eoff[u + 1];
+                fb = rp[u];
+                ru = lv[u].x;
+            }
+            const uint32_t v = adj2[fb + (e - u_lo)];
+            const uint4 m = vmeta[v];
+            const uint64_t as = ((uint64_t)m.y << 32) | m.x;
+            const uint32_t av = m.z, gv = m.w;
+            uint32_t p = av;
+            if (av <= kSortCap) {
+                const uint32_t *A = adj2 + as;
+                uint32_t lo = 0, hi = av;  // first position holding a rank below ru
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (A[mid] < ru) hi = mid; else lo = mid + 1;
+                }
+                p = av - lo;
+            }
+            const uint64_t start = as + av - p;
+            erec[e] = make_uint4((uint32_t)start, (uint32_t)(start >> 32), gv + p, p);
+        }
+    }
+}
+
+// Cut the out-edges of every row u of class c (one warp each) into tasks
+// (contiguous slices of F(u)) of about `target` probes: work(u) = sum of the
+// record lengths, ntask = ceil(work(u) / max(task_work, min_mult * s(u))), at
+// least ceil(|F(u)| / max_v) (shared-memory metadata of one task), at most
+// |F(u)|.
 __global__ void k_plan(const uint32_t *__restrict__ rows, const unsigned int *__restrict__ n_rows,
-                       const uint64_t *__restrict__ off2, const uint32_t *__restrict__ adj2,
-                       const uint32_t *__restrict__ hcnt, const uint32_t *__restrict__ scnt,
+                       const uint64_t *__restrict__ rp, const uint32_t *__restrict__ fcnt,
+                       const uint64_t *__restrict__ eoff, const uint4 *__restrict__ erec,
                        uint32_t *__restrict__ ntask, uint32_t task_work, uint32_t min_mult, uint32_t max_v) {
     const unsigned lane = lane_id();
     const uint32_t nr = *n_rows;
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < nr; i += warps) {
         const uint32_t u = rows[i];
-        const uint64_t b = off2[u];
-        const uint32_t hu = hcnt[u];
-        unsigned long long work = 0;
-        for (uint32_t k = lane; k < hu; k += 32) work += scnt[adj2[b + k]];
-        work = warp_sum(work);
+        const uint32_t fu = fcnt[u];
+        const uint4 *rec = erec + eoff[u];
+        unsigned long long w0 = 0, w1 = 0, w2 = 0, w3 = 0;
+        uint32_t k = lane;
+        for (; k + 96 < fu; k += 128) {  // four independent loads in flight
+            w0 += rec[k].z;
+            w1 += rec[k + 32].z;
+            w2 += rec[k + 64].z;
+            w3 += rec[k + 96].z;
+        }
+        for (; k < fu; k += 32) w0 += rec[k].z;
+        const unsigned long long work = warp_sum(w0 + w1 + w2 + w3);
         if (lane == 0) {
-            const unsigned long long su = scnt[u];
+            const unsigned long long su = (rp[u + 1] - rp[u]) - fu;
             const unsigned long long floor_t = (unsigned long long)min_mult * su;
             const unsigned long long target = floor_t > task_work ? floor_t : task_work;
             unsigned long long nt = (work + target - 1) / target;
-            const unsigned long long by_v = (hu + max_v - 1) / max_v;
+            const unsigned long long by_v = (fu + max_v - 1) / max_v;
             if (nt < by_v) nt = by_v;
             if (nt < 1) nt = 1;
-            if (nt > hu) nt = hu;
+            if (nt > fu) nt = fu;
             ntask[i] = (uint32_t)nt;
         }
     }
@@ -272,25 +402,28 @@ unsigned grid_for(uint64_t work, unsigned threads, unsigned cap) {
 tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_deg) {
     cudaStream_t s = ctx->stream;
     const unsigned cap = (unsigned)ctx->num_sms * 16u;
-    const uint32_t order = ctx->opt.order;
     const Tuning &tu = ctx->tune;
     if (n == 0) return TC_OK;
-    // pack (level, degree) into one word when both fit (q0 is free after the levels)
-    LevelDeg ld{b.L, b.deg, nullptr};
-    uint32_t launches = 0;
-    if (ctx->h_ctl->max_level < 255 && max_deg < (1u << 24)) {
-        k_pack_level_deg<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.L, b.deg, b.q0);
-        ld.packed = b.q0;
+    uint32_t launches = 1;
+    if (b.lvp)
+        k_row_fill<true><<<grid_for(n, kFillThreads, cap), kFillThreads, 0, s>>>(
+            n, b.rp, b.col, b.lv, b.lvp, b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big, ctx->d_ctl);
+    else
+        k_row_fill<false><<<grid_for(n, kFillThreads, cap), kFillThreads, 0, s>>>(
+            n, b.rp, b.col, b.lv, b.lvp, b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big, ctx->d_ctl);
+    if (max_deg > kWarpA) {
+        const int smem = (int)(4 * kSortCap);
+        TC_CUDA(ctx, cudaFuncSetAttribute(k_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        k_sort_big<<<(unsigned)ctx->num_sms, 1024, smem, s>>>(b.big, ctx->d_ctl, b.rp, b.fcnt, b.gcnt, b.adj2);
         ++launches;
     }
-    k_row_count<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.rp, b.col, b.deg, b.L, ld, b.hcnt, b.scnt, ctx->d_ctl,
-                                                      order);
-    launches += 1 + scan_u32_to_u64(b.scnt, b.off2, n, b.scan_tmp, s);
-    k_row_fill<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.rp, b.col, b.deg, b.L, ld, b.hcnt, b.off2, b.adj2, order);
+    launches += scan_u32_to_u64(b.fcnt, b.eoff, n, b.scan_tmp, s);
+    k_chunk_rows<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.eoff, b.chunk_row);
+    k_records<<<cap, 256, 0, s>>>(n, b.eoff, b.chunk_row, b.rp, b.adj2, b.lv, b.vmeta, b.erec);
     // fdeg and R are free after the levels: class of every vertex, 0/1 indicator
-    k_class_flags<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.hcnt, b.scnt, b.deg, b.fdeg, ctx->d_ctl, tu.warp_cap,
-                                                        tu.block_cap, tu.tiny_cap);
-    launches += 2;
+    k_class_flags<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.fcnt, b.deg, b.fdeg, ctx->d_ctl, tu.warp_cap, tu.block_cap,
+                                                        tu.tiny_cap);
+    launches += 3;
     for (uint32_t c = 0; c < 4; ++c) {
         k_class_indicator<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.fdeg, c, b.R);
         launches += 2 + scan_u32_to_u64(b.R, b.fpref, n, b.scan_tmp, s);
@@ -301,8 +434,8 @@ tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_de
     const uint32_t mult[3] = {1, 2, 2};
     const uint32_t maxv[3] = {0xFFFFFFFFu, tu.max_v, tu.max_v};
     for (int c = 0; c < 3; ++c) {
-        k_plan<<<grid_for((uint64_t)n * 32, 256, cap), 256, 0, s>>>(b.rows[c], &ctx->d_ctl->n_rows[c], b.off2, b.adj2,
-                                                                    b.hcnt, b.scnt, b.ntask[c], work[c], mult[c],
+        k_plan<<<grid_for((uint64_t)n * 32, 256, cap), 256, 0, s>>>(b.rows[c], &ctx->d_ctl->n_rows[c], b.rp, b.fcnt,
+                                                                    b.eoff, b.erec, b.ntask[c], work[c], mult[c],
                                                                     maxv[c]);
         ++launches;
     }

@@ -21,8 +21,8 @@ constexpr uint32_t kUnvisited = 0xFFFFFFFFu;
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 
 // ----------------------------------------------------------------------------- tuning
-// Class boundaries of the intersection stage by the size s(u) of the hashed
-// row [G0 out-list | G1 list] of the higher-ranked endpoint u.
+// Class boundaries of the intersection stage by the size s(u) = |A(u)| +
+// |G1(u)| of the hashed set of the earlier endpoint u of a horizontal edge.
 struct Tuning {
     uint32_t warp_cap = 1024;        // s(u) <= warp_cap: warp tasks, per-warp smem table
     uint32_t block_cap = 16384;      // s(u) <= block_cap: block tasks, smem table; larger: hub tasks
@@ -36,6 +36,8 @@ struct Tuning {
     uint32_t hub_threads = 1024;     // hub kernel threads
     uint32_t hub_filter_log2 = 20;   // hub prefilter bits (log2)
     uint32_t tiny_cap = 16;          // s(u) <= tiny_cap and deg(u) <= 4 tiny_cap: thread-per-row merges (0: off)
+    uint32_t block_filter_log2 = 0;  // block-class shared filter bits (log2) in front of the table (0: none)
+    uint32_t flat_cap = 64;          // warp class: probe ranges shorter than this are concatenated across lanes
 };
 
 // Control block in device memory: counters the kernels update and the host
@@ -65,7 +67,8 @@ struct Ctl {
     unsigned int max_s2;             // largest hashed row among block-class rows / max degree
     unsigned int p_slot, p_queue, p_level;  // where the persistent BFS stopped
     unsigned int bar_count, bar_gen;        // grid barrier of the persistent BFS
-    unsigned int pad[4];
+    unsigned int n_big;              // rows whose A part the block sorter sorts
+    unsigned int pad[3];
 };
 
 // ----------------------------------------------------------------------------- arena
@@ -144,6 +147,15 @@ size_t scan_tmp_elems(uint64_t count);
 uint32_t scan_u32_to_u64(const uint32_t *in, uint64_t *out, uint64_t count, uint64_t *tmp, cudaStream_t s);
 // Same for uint64 inputs.
 uint32_t scan_u64(const uint64_t *in, uint64_t *out, uint64_t count, uint64_t *tmp, cudaStream_t s);
+
+// Stable LSD radix sort of `count` 64-bit keys over the 8-bit digits starting
+// at shifts[0..nshifts) (least significant first); *cur holds the keys and on
+// return the sorted keys (the two buffers are swapped once per pass).  counts
+// needs 256 * radix_tiles(count) + 1 entries, coffs two more, tmp
+// scan_tmp_elems(256 * radix_tiles(count) + 1).  Returns the kernels launched.
+uint64_t radix_tiles(uint64_t count);
+uint32_t radix_sort_u64(unsigned long long **cur, unsigned long long **alt, uint64_t count, const int *shifts,
+                        int nshifts, uint32_t *counts, uint64_t *coffs, uint64_t *tmp, cudaStream_t s);
 
 // Pipeline entry (count.cu).  levels_out: device uint32[n] or nullptr.
 // group_of / n_groups / group_counts: optional per-group accumulation
