@@ -53,6 +53,7 @@ struct Acc {
 struct BucketTable {
     static constexpr int kUnroll = 8;  // ids in flight per lane
     static constexpr int kBatch = 4;   // lookups resolved together
+    static constexpr uint32_t kPad = kEmpty;  // probe padding (lookups reject it)
     uint4 *bk;
     uint32_t shift, mask;  // home bucket = hash >> shift; mask = buckets - 1
     unsigned int *err;     // device error word: a walk longer than the table sets kGuardTable
@@ -123,14 +124,30 @@ __device__ __forceinline__ bool filter_test(const uint32_t *filter, uint32_t w, 
     return (filter[f >> 5] >> (f & 31)) & 1u;
 }
 
-// Block rows: shared filter (2^block_filter_log2 bits) in front of the bucket
-// table; most probes miss and end at the filter with one 32-bit shared load.
-struct FilteredTable {
+// Block rows: two-choice cuckoo hashing.  Every key sits in T0[h0(w)] or in
+// T1[h1(w)] (one 32-bit slot each; h = top bits of w times an odd
+// multiplier), so a lookup is two independent 32-bit shared loads and two
+// compares, with no branch.  The tables hold at most 0.4 keys per slot; a key
+// that finds no place after kCuckooIters displacements goes to a small
+// stash, which lookups read only when it is not empty (a block-wide
+// condition).  If the stash overflows, the table is rebuilt with the next
+// pair of multipliers.
+constexpr uint32_t kNone = 0xFFFFFFFEu;  // probe padding: never a rank (n <= 2^32 - 2), never stored
+constexpr int kCuckooIters = 64;
+constexpr uint32_t kStash = 64;
+constexpr int kCuckooAttempts = 4;
+__device__ __constant__ uint32_t kCuckooMul[2 * kCuckooAttempts] = {
+    0x9E3779B1u, 0x85EBCA77u, 0xC2B2AE3Du, 0x27D4EB2Fu, 0x165667B1u, 0xD3A2646Du, 0xFD7046C5u, 0xB55A4F09u};
+
+struct CuckooTable {
     static constexpr int kUnroll = 8;
     static constexpr int kBatch = 8;
-    BucketTable T;
-    const uint32_t *filter;
-    uint32_t fshift;
+    static constexpr uint32_t kPad = kNone;
+    uint32_t *t;            // 2m slots: T0 = t[0, m), T1 = t[m, 2m)
+    const uint32_t *stash;  // shared, nstash entries
+    uint32_t m, shift;      // m slots per table, shift = 32 - log2 m
+    uint32_t k0, k1;        // multipliers of this build
+    uint32_t nstash;
 };
 
 // Hub rows: shared prefilter (2^hub_filter_log2 bits) in front of the exact
@@ -138,6 +155,7 @@ struct FilteredTable {
 struct HubSet {
     static constexpr int kUnroll = 8;  // ids in flight per lane
     static constexpr int kBatch = 8;   // prefilter tests, then all bitmap loads together
+    static constexpr uint32_t kPad = kEmpty;  // probe padding (lookups reject it)
     const uint32_t *filter;  // shared
     const uint32_t *bits;    // global, read-only while probing
     uint32_t fshift;
@@ -162,20 +180,23 @@ __device__ __forceinline__ void lookup_batch(const BucketTable &T, const uint32_
     }
 }
 
-// Filter tests for all N elements, then the table for the positive ones.
+// Both candidate slots of all N elements, then the compares; the stash only
+// when it is not empty.
 template <int N>
-__device__ __forceinline__ void lookup_batch(const FilteredTable &F, const uint32_t (&w)[N], bool (&hit)[N]) {
-    bool pos[N];
-#pragma unroll
-    for (int i = 0; i < N; ++i) pos[i] = w[i] != kEmpty && filter_test(F.filter, w[i], F.fshift);
+__device__ __forceinline__ void lookup_batch(const CuckooTable &C, const uint32_t (&w)[N], bool (&hit)[N]) {
+    uint32_t a[N], b[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        hit[i] = false;
-        if (pos[i]) {
-            const uint32_t home = hash_slot(w[i], F.T.shift);
-            const uint4 q = F.T.bk[home];
-            hit[i] = q.x == w[i] || q.y == w[i] || q.z == w[i] || q.w == w[i];
-            if (!hit[i] && q.w != kEmpty) hit[i] = table_find_rest(F.T, home, w[i]);
+        a[i] = C.t[(w[i] * C.k0) >> C.shift];
+        b[i] = C.t[C.m + ((w[i] * C.k1) >> C.shift)];
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) hit[i] = a[i] == w[i] || b[i] == w[i];
+    if (C.nstash) {
+        for (uint32_t k = 0; k < C.nstash; ++k) {
+            const uint32_t x = C.stash[k];
+#pragma unroll
+            for (int i = 0; i < N; ++i) hit[i] = hit[i] || x == w[i];
         }
     }
 }
@@ -240,7 +261,7 @@ __device__ __forceinline__ void probe_row(const Set &set, const uint32_t *__rest
 #pragma unroll
         for (int i = 0; i < U; ++i) {
             const uint32_t j = j0 + (uint32_t)i * 32u + lane;
-            w[i] = j < j_hi ? __ldg(row + j) : kEmpty;
+            w[i] = j < j_hi ? __ldg(row + j) : Set::kPad;
         }
         constexpr int B = Set::kBatch;
 #pragma unroll
@@ -300,7 +321,7 @@ __device__ __forceinline__ void probe_flat(const Set &set, const uint32_t *__res
                     split = lo + ssplit[r];
                 }
             }
-            w[i] = valid ? __ldg(adj2 + base + q) : kEmpty;
+            w[i] = valid ? __ldg(adj2 + base + q) : Set::kPad;
             in_a[i] = q < split;
         }
         lookup_all(set, w, in_a, hits);
@@ -658,23 +679,57 @@ __device__ __forceinline__ void init_task_smem(TaskSmem *ts) {
     }
 }
 
-// Block rows: shared bucket table, optionally behind a shared filter
-// (block_filter_log2 > 0).
-template <class Set>
-__device__ __forceinline__ Set make_block_set(uint4 *bk, uint32_t *filter, uint32_t filter_log2, unsigned int *err);
-template <>
-__device__ __forceinline__ BucketTable make_block_set<BucketTable>(uint4 *bk, uint32_t *, uint32_t, unsigned int *err) {
-    return BucketTable{bk, 0, 0, err};
-}
-template <>
-__device__ __forceinline__ FilteredTable make_block_set<FilteredTable>(uint4 *bk, uint32_t *filter, uint32_t filter_log2,
-                                                                       unsigned int *err) {
-    return FilteredTable{BucketTable{bk, 0, 0, err}, filter, 32u - filter_log2};
-}
-__device__ __forceinline__ BucketTable &table_of(BucketTable &s) { return s; }
-__device__ __forceinline__ BucketTable &table_of(FilteredTable &s) { return s.T; }
+// Build the cuckoo table of a hashed set row[0..s) (all threads of the block
+// call it): clear 2m slots, insert every key by displacement, stash the keys
+// that found no place; rebuild with the next multipliers if the stash
+// overflowed.  m = the smallest power of two >= 1.25 s (at most m_cap): at
+// most 0.4 keys per slot.
+struct CuckooShared {
+    uint32_t stash[kStash];
+    unsigned int nstash;
+};
 
-template <class Set>
+__device__ __forceinline__ void cuckoo_insert(const CuckooTable &C, uint32_t key, CuckooShared *cs) {
+    uint32_t which = 0, pos = (key * C.k0) >> C.shift;
+    for (int it = 0; it < kCuckooIters; ++it) {
+        const uint32_t old = atomicExch(C.t + which * C.m + pos, key);
+        if (old == kEmpty) return;
+        key = old;
+        which ^= 1u;
+        pos = (key * (which ? C.k1 : C.k0)) >> C.shift;
+    }
+    const unsigned k = atomicAdd(&cs->nstash, 1u);
+    if (k < kStash) cs->stash[k] = key;
+}
+
+__device__ __forceinline__ CuckooTable cuckoo_build(uint32_t *t, uint32_t m_cap, const uint32_t *__restrict__ row,
+                                                    uint32_t s, CuckooShared *cs, unsigned int *err) {
+    uint32_t m = 64;
+    while (m < s + s / 4 && m < m_cap) m <<= 1;
+    CuckooTable C{t, cs->stash, m, (uint32_t)__clz(m) + 1u, 0, 0, 0};
+    for (int attempt = 0; attempt < kCuckooAttempts; ++attempt) {
+        C.k0 = kCuckooMul[2 * attempt];
+        C.k1 = kCuckooMul[2 * attempt + 1];
+        for (uint32_t j = threadIdx.x; j < 2 * m; j += blockDim.x) t[j] = kEmpty;
+        if (threadIdx.x == 0) cs->nstash = 0;
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < s; j += blockDim.x) cuckoo_insert(C, row[j], cs);
+        __syncthreads();
+        const unsigned ns = cs->nstash;
+        __syncthreads();  // everyone has read it before a rebuild clears it
+        if (ns <= kStash) {
+            C.nstash = ns;
+            return C;
+        }
+    }
+    if (threadIdx.x == 0) atomicOr(err, kGuardInsert);  // keys were dropped: the count reports an error
+    C.nstash = kStash;
+    return C;
+}
+
+// Block class.  The hashed set lives in shared memory: a cuckoo table
+// (block_table = 0) or the bucketed table (block_table = 1).
+template <bool kCuckoo>
 __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict__ tasks, const uint32_t *__restrict__ rows,
                                                       const uint32_t *__restrict__ ntask,
                                                       const uint64_t *__restrict__ rp,
@@ -682,22 +737,20 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
                                                       const uint32_t *__restrict__ fcnt,
                                                       const uint64_t *__restrict__ eoff,
                                                       const uint4 *__restrict__ erec, Ctl *ctl, uint32_t max_v,
-                                                      uint32_t table_buckets, uint32_t filter_log2,
-                                                      unsigned long long chunk, unsigned long long first,
-                                                      unsigned long long last, GroupSpec groups) {
-    constexpr bool kFiltered = sizeof(Set) != sizeof(BucketTable);
+                                                      uint32_t table_units, unsigned long long chunk,
+                                                      unsigned long long first, unsigned long long last,
+                                                      GroupSpec groups) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TaskSmem ts;
+    __shared__ CuckooShared cs;
     const unsigned lane = lane_id();
     const SliceSmem S = carve_slice(smem_raw, max_v);
-    uint4 *bk = reinterpret_cast<uint4 *>(smem_raw + slice_smem_bytes(max_v));
-    uint32_t *filter = reinterpret_cast<uint32_t *>(bk + table_buckets);
-    const uint32_t filter_words = kFiltered ? 1u << (filter_log2 - 5) : 0u;
-    const uint32_t fshift = 32u - filter_log2;
+    unsigned char *tab = smem_raw + slice_smem_bytes(max_v);
     Acc acc;
     unsigned long long build = 0, done = 0, inserts = 0;
     uint32_t cur_row = 0xFFFFFFFFu;
-    Set set = make_block_set<Set>(bk, filter, filter_log2, &ctl->error);
+    CuckooTable C{reinterpret_cast<uint32_t *>(tab), cs.stash, 64, 26, 0, 0, 0};
+    BucketTable T{reinterpret_cast<uint4 *>(tab), 0, 0, &ctl->error};
     init_task_smem(&ts);
     const long long t_start = clock64();
     while (next_task(ctl, 1, first, last, chunk, tasks, &ts, t_start)) {
@@ -708,24 +761,18 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
         const uint32_t su = (uint32_t)(rp[u + 1] - hb);
         const uint32_t k_lo = (uint32_t)((uint64_t)task.y * fu / nt), k_hi = (uint32_t)((uint64_t)(task.y + 1) * fu / nt);
         const bool rebuild = task.x != cur_row;
-        if (rebuild) {
-            table_of(set) = clear_table(bk, su, table_buckets, threadIdx.x, blockDim.x, &ctl->error);
-            if constexpr (kFiltered)
-                for (uint32_t j = threadIdx.x; j < filter_words; j += blockDim.x) filter[j] = 0u;
-        }
+        if constexpr (!kCuckoo)
+            if (rebuild) T = clear_table(T.bk, su, table_units, threadIdx.x, blockDim.x, &ctl->error);
         load_slice(S, erec + eoff[u], k_lo, k_hi);
         __syncthreads();
         scan_segments(S.len, S.seg, k_hi - k_lo);
         if (rebuild) {
-            for (uint32_t j = threadIdx.x; j < su; j += blockDim.x) {
-                const uint32_t w = adj2[hb + j];
-                table_insert(table_of(set), w);
-                if constexpr (kFiltered) {
-                    const uint32_t f = filter_bit(w, fshift);
-                    atomicOr(filter + (f >> 5), 1u << (f & 31));
-                }
+            if constexpr (kCuckoo) {
+                C = cuckoo_build(C.t, table_units, adj2 + hb, su, &cs, &ctl->error);
+            } else {
+                fill_table(T, adj2 + hb, su, threadIdx.x, blockDim.x);
+                __syncthreads();
             }
-            __syncthreads();
             cur_row = task.x;
             if (threadIdx.x == 0) inserts += su;
         }
@@ -734,7 +781,8 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
             ++done;
         }
         const unsigned long long before = acc.same + acc.cross;
-        probe_slice(set, S, k_hi - k_lo, adj2, &ts.next, acc);
+        if constexpr (kCuckoo) probe_slice(C, S, k_hi - k_lo, adj2, &ts.next, acc);
+        else probe_slice(T, S, k_hi - k_lo, adj2, &ts.next, acc);
         if (groups.n_groups) {
             const unsigned long long found = warp_sum(acc.same + acc.cross - before);
             if (lane == 0 && found) atomicAdd(&ts.found, found);
@@ -835,13 +883,16 @@ uint32_t pow2_at_least(uint64_t x, uint32_t lo) {
 
 // Buckets per table: enough for load factor 1/2 at the class cap.
 uint32_t warp_table_buckets(const Tuning &tu) { return pow2_at_least((tu.warp_cap + 1) / 2, 16); }
-uint32_t block_table_buckets(const Tuning &tu) { return pow2_at_least((tu.block_cap + 1) / 2, 16); }
+// Block class: cuckoo slots per table (>= 1.25 block_cap), or buckets.
+uint32_t block_table_units(const Tuning &tu) {
+    return tu.block_table == 0 ? pow2_at_least((uint64_t)tu.block_cap + tu.block_cap / 4, 64)
+                               : pow2_at_least((tu.block_cap + 1) / 2, 16);
+}
 size_t warp_kernel_smem(const Tuning &tu) {
     return (size_t)tu.warps_per_block * (16ull * warp_table_buckets(tu) + kWarpMetaBytes);
 }
 size_t block_kernel_smem(const Tuning &tu) {
-    return slice_smem_bytes(tu.max_v) + 16ull * block_table_buckets(tu) +
-           (tu.block_filter_log2 ? (1ull << tu.block_filter_log2) / 8 : 0);
+    return slice_smem_bytes(tu.max_v) + (tu.block_table == 0 ? 8ull : 16ull) * block_table_units(tu);
 }
 size_t hub_kernel_smem(const Tuning &tu) { return slice_smem_bytes(tu.max_v) + (1ull << tu.hub_filter_log2) / 8; }
 
@@ -893,7 +944,7 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[5], s));
     if (hi1 > lo1) {
         const size_t smem = block_kernel_smem(tu);
-        auto kern = tu.block_filter_log2 ? k_isect_block<FilteredTable> : k_isect_block<BucketTable>;
+        auto kern = tu.block_table == 0 ? k_isect_block<true> : k_isect_block<false>;
         TC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
         TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tu.block_threads, smem));
@@ -902,9 +953,8 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         if (grid > hi1 - lo1) grid = hi1 - lo1;
         const unsigned long long chunk = std::max<unsigned long long>(1, (hi1 - lo1) / (grid * 8));
         kern<<<(unsigned)grid, tu.block_threads, smem, s>>>(b.tasks[1], b.rows[1], b.ntask[1], b.rp, b.adj2, b.fcnt,
-                                                            b.eoff, b.erec, ctx->d_ctl, tu.max_v, block_table_buckets(tu),
-                                                            tu.block_filter_log2, chunk, lo1, hi1,
-                                                            b.groups);
+                                                            b.eoff, b.erec, ctx->d_ctl, tu.max_v, block_table_units(tu),
+                                                            chunk, lo1, hi1, b.groups);
         note_launch(ctx);
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[6], s));
