@@ -114,7 +114,7 @@ typedef struct tc_stats {
 typedef struct tc_tuning {
     uint32_t warp_cap;         /* s(u) <= warp_cap: one warp per task, per-warp shared table (1..4096) */
     uint32_t block_cap;        /* s(u) <= block_cap: one block per task, shared table (warp_cap..16384, see
-                                  block_table);
+                                  table_kind);
                                   larger rows are hub rows (L2 bitmaps + shared prefilter) */
     uint32_t task_work;        /* target probes per block task (large rows are split) */
     uint32_t warps_per_block;  /* warp-class kernel block size in warps (1..8) */
@@ -128,9 +128,9 @@ typedef struct tc_tuning {
     uint32_t tiny_cap;         /* s(u) <= tiny_cap (and degree <= 4 tiny_cap): one thread per row, sorted
                                   merges instead of a table; takes precedence over the classes above
                                   (0..64; 0 turns it off) */
-    uint32_t block_table;       /* block-class set in shared memory: 0 two-choice cuckoo table (two 32-bit
-                                   loads per lookup; block_cap up to 13107), 1 bucketed table (block_cap up
-                                   to 16384) */
+    uint32_t table_kind;        /* shared-memory sets of the warp and block classes: 0 two-choice cuckoo
+                                   tables (two 32-bit loads per lookup; block_cap up to 13107), 1 bucketed
+                                   tables (block_cap up to 16384) */
     uint32_t flat_cap;          /* warp class: probe ranges shorter than this are concatenated so that every
                                    lane of a warp has work; longer ones are walked range by range (0..4096) */
     uint32_t reserved[2];

@@ -34,7 +34,7 @@ CANDIDATES = [
     {"task_work": 65536, "hub_task_work": 131072},
     {"task_work": 524288, "hub_task_work": 1048576},
     {"block_threads": 512, "hub_threads": 512, "block_cap": 8192, "max_v": 1024, "hub_filter_log2": 19},
-    {"block_table": 1, "block_cap": 16384},
+    {"table_kind": 1, "block_cap": 16384},
     {"block_cap": 13107},
     {"flat_cap": 0},
     {"flat_cap": 256},

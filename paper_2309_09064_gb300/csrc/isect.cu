@@ -363,6 +363,86 @@ __device__ __forceinline__ unsigned long long rec_start(const uint4 &r) {
 // (probe_flat) so that every lane has work.
 constexpr uint32_t kSeg = 512;
 
+// Build the cuckoo table of a hashed set row[0..s) (all threads of a block,
+// or of a warp, call it): clear 2m slots, insert every key by displacement, stash the keys
+// that found no place; rebuild with the next multipliers if the stash
+// overflowed.  m = the smallest power of two >= 1.25 s (at most m_cap): at
+// most 0.4 keys per slot.
+struct CuckooShared {
+    uint32_t stash[kStash];
+    unsigned int nstash;
+};
+
+__device__ __forceinline__ void cuckoo_insert(const CuckooTable &C, uint32_t key, CuckooShared *cs) {
+    uint32_t which = 0, pos = (key * C.k0) >> C.shift;
+    for (int it = 0; it < kCuckooIters; ++it) {
+        const uint32_t old = atomicExch(C.t + which * C.m + pos, key);
+        if (old == kEmpty) return;
+        key = old;
+        which ^= 1u;
+        pos = (key * (which ? C.k1 : C.k0)) >> C.shift;
+    }
+    const unsigned k = atomicAdd(&cs->nstash, 1u);
+    if (k < kStash) cs->stash[k] = key;
+}
+
+__device__ __forceinline__ uint32_t cuckoo_slots_for(uint32_t s, uint32_t m_cap) {
+    uint32_t m = 64;
+    while (m < s + s / 4 && m < m_cap) m <<= 1;
+    return m;
+}
+
+// Block-wide build (all threads of the block call it).
+__device__ __forceinline__ CuckooTable cuckoo_build(uint32_t *t, uint32_t m_cap, const uint32_t *__restrict__ row,
+                                                    uint32_t s, CuckooShared *cs, unsigned int *err) {
+    const uint32_t m = cuckoo_slots_for(s, m_cap);
+    CuckooTable C{t, cs->stash, m, (uint32_t)__clz(m) + 1u, 0, 0, 0};
+    for (int attempt = 0; attempt < kCuckooAttempts; ++attempt) {
+        C.k0 = kCuckooMul[2 * attempt];
+        C.k1 = kCuckooMul[2 * attempt + 1];
+        for (uint32_t j = threadIdx.x; j < 2 * m; j += blockDim.x) t[j] = kEmpty;
+        if (threadIdx.x == 0) cs->nstash = 0;
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < s; j += blockDim.x) cuckoo_insert(C, row[j], cs);
+        __syncthreads();
+        const unsigned ns = cs->nstash;
+        __syncthreads();  // everyone has read it before a rebuild clears it
+        if (ns <= kStash) {
+            C.nstash = ns;
+            return C;
+        }
+    }
+    if (threadIdx.x == 0) atomicOr(err, kGuardInsert);  // keys were dropped: the count reports an error
+    C.nstash = kStash;
+    return C;
+}
+
+// Warp-wide build (all lanes of the warp call it).
+__device__ __forceinline__ CuckooTable warp_cuckoo_build(uint32_t *t, uint32_t m_cap, const uint32_t *__restrict__ row,
+                                                         uint32_t s, CuckooShared *cs, unsigned int *err) {
+    const unsigned lane = lane_id();
+    const uint32_t m = cuckoo_slots_for(s, m_cap);
+    CuckooTable C{t, cs->stash, m, (uint32_t)__clz(m) + 1u, 0, 0, 0};
+    for (int attempt = 0; attempt < kCuckooAttempts; ++attempt) {
+        C.k0 = kCuckooMul[2 * attempt];
+        C.k1 = kCuckooMul[2 * attempt + 1];
+        for (uint32_t j = lane; j < 2 * m; j += 32) t[j] = kEmpty;
+        if (lane == 0) cs->nstash = 0;
+        __syncwarp();
+        for (uint32_t j = lane; j < s; j += 32) cuckoo_insert(C, row[j], cs);
+        __syncwarp();
+        const unsigned ns = cs->nstash;
+        __syncwarp();
+        if (ns <= kStash) {
+            C.nstash = ns;
+            return C;
+        }
+    }
+    if (lane == 0) atomicOr(err, kGuardInsert);
+    C.nstash = kStash;
+    return C;
+}
+
 // ---------------------------------------------------------------------------- warp class
 
 // Per-warp shared metadata of the 32 probe records a warp holds at a time.
@@ -373,24 +453,33 @@ struct WarpMeta {
 };
 constexpr size_t kWarpMetaBytes = (sizeof(WarpMeta) + 15) & ~size_t(15);
 
+// Shared memory of one warp: its set (cuckoo table and stash, or buckets),
+// then the metadata of the 32 records it holds.
+__host__ __device__ constexpr size_t warp_set_bytes(bool cuckoo, uint32_t units) {
+    return cuckoo ? ((8ull * units + sizeof(CuckooShared) + 15) & ~15ull) : 16ull * units;
+}
+
+template <bool kCuckoo>
 __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__ tasks, const uint32_t *__restrict__ rows,
                                                      const uint32_t *__restrict__ ntask,
                                                      const uint64_t *__restrict__ rp,
                                                      const uint32_t *__restrict__ adj2,
                                                      const uint32_t *__restrict__ fcnt,
                                                      const uint64_t *__restrict__ eoff,
-                                                     const uint4 *__restrict__ erec, Ctl *ctl, uint32_t table_buckets,
+                                                     const uint4 *__restrict__ erec, Ctl *ctl, uint32_t table_units,
                                                      uint32_t flat_cap, unsigned long long first,
                                                      unsigned long long last, GroupSpec groups) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
-    unsigned char *mine = smem_raw + (size_t)warp * (16ull * table_buckets + kWarpMetaBytes);
-    uint4 *bk = reinterpret_cast<uint4 *>(mine);
-    WarpMeta *meta = reinterpret_cast<WarpMeta *>(mine + 16ull * table_buckets);
+    const size_t set_bytes = warp_set_bytes(kCuckoo, table_units);
+    unsigned char *mine = smem_raw + (size_t)warp * (set_bytes + kWarpMetaBytes);
+    WarpMeta *meta = reinterpret_cast<WarpMeta *>(mine + set_bytes);
+    CuckooShared *cs = reinterpret_cast<CuckooShared *>(mine + 8ull * table_units);
     Acc acc;
     unsigned long long build = 0, done = 0, inserts = 0;
     uint32_t cur_row = 0xFFFFFFFFu;
-    BucketTable T{bk, 0, 0, &ctl->error};
+    BucketTable T{reinterpret_cast<uint4 *>(mine), 0, 0, &ctl->error};
+    CuckooTable C{reinterpret_cast<uint32_t *>(mine), cs->stash, 64, 26, 0, 0, 0};
     const long long t_start = clock64();
     for (;;) {
         unsigned long long k = 0;
@@ -412,10 +501,14 @@ __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__
         const uint32_t k_lo = (uint32_t)((uint64_t)task.y * fu / nt), k_hi = (uint32_t)((uint64_t)(task.y + 1) * fu / nt);
         if (task.x != cur_row) {  // tasks of one row reuse its table
             __syncwarp();
-            T = clear_table(bk, su, table_buckets, lane, 32, &ctl->error);
-            __syncwarp();
-            fill_table(T, adj2 + hb, su, lane, 32);
-            __syncwarp();
+            if constexpr (kCuckoo) {
+                C = warp_cuckoo_build(C.t, table_units, adj2 + hb, su, cs, &ctl->error);
+            } else {
+                T = clear_table(T.bk, su, table_units, lane, 32, &ctl->error);
+                __syncwarp();
+                fill_table(T, adj2 + hb, su, lane, 32);
+                __syncwarp();
+            }
             cur_row = task.x;
             inserts += su;
         }
@@ -437,7 +530,8 @@ __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__
                 const unsigned long long bt = __shfl_sync(0xFFFFFFFFu, b, t);
                 const uint32_t lt = __shfl_sync(0xFFFFFFFFu, r.z, t);
                 const uint32_t ht = __shfl_sync(0xFFFFFFFFu, r.w, t);
-                probe_row<BucketTable::kUnroll>(T, adj2, bt, 0, lt, ht, acc);
+                if constexpr (kCuckoo) probe_row<CuckooTable::kUnroll>(C, adj2, bt, 0, lt, ht, acc);
+                else probe_row<BucketTable::kUnroll>(T, adj2, bt, 0, lt, ht, acc);
             }
             // short ranges: concatenated
             const uint32_t sl = longr ? 0u : r.z;
@@ -454,8 +548,12 @@ __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__
                 meta->split[lane] = r.w;
                 if (lane == 31) meta->pre[32] = total;
                 __syncwarp();
-                probe_flat<BucketTable::kUnroll>(T, adj2, meta->b, meta->pre, meta->split, 32, 0, total, acc,
-                                                 &ctl->error);
+                if constexpr (kCuckoo)
+                    probe_flat<CuckooTable::kUnroll>(C, adj2, meta->b, meta->pre, meta->split, 32, 0, total, acc,
+                                                     &ctl->error);
+                else
+                    probe_flat<BucketTable::kUnroll>(T, adj2, meta->b, meta->pre, meta->split, 32, 0, total, acc,
+                                                     &ctl->error);
                 __syncwarp();
             }
         }
@@ -679,56 +777,8 @@ __device__ __forceinline__ void init_task_smem(TaskSmem *ts) {
     }
 }
 
-// Build the cuckoo table of a hashed set row[0..s) (all threads of the block
-// call it): clear 2m slots, insert every key by displacement, stash the keys
-// that found no place; rebuild with the next multipliers if the stash
-// overflowed.  m = the smallest power of two >= 1.25 s (at most m_cap): at
-// most 0.4 keys per slot.
-struct CuckooShared {
-    uint32_t stash[kStash];
-    unsigned int nstash;
-};
-
-__device__ __forceinline__ void cuckoo_insert(const CuckooTable &C, uint32_t key, CuckooShared *cs) {
-    uint32_t which = 0, pos = (key * C.k0) >> C.shift;
-    for (int it = 0; it < kCuckooIters; ++it) {
-        const uint32_t old = atomicExch(C.t + which * C.m + pos, key);
-        if (old == kEmpty) return;
-        key = old;
-        which ^= 1u;
-        pos = (key * (which ? C.k1 : C.k0)) >> C.shift;
-    }
-    const unsigned k = atomicAdd(&cs->nstash, 1u);
-    if (k < kStash) cs->stash[k] = key;
-}
-
-__device__ __forceinline__ CuckooTable cuckoo_build(uint32_t *t, uint32_t m_cap, const uint32_t *__restrict__ row,
-                                                    uint32_t s, CuckooShared *cs, unsigned int *err) {
-    uint32_t m = 64;
-    while (m < s + s / 4 && m < m_cap) m <<= 1;
-    CuckooTable C{t, cs->stash, m, (uint32_t)__clz(m) + 1u, 0, 0, 0};
-    for (int attempt = 0; attempt < kCuckooAttempts; ++attempt) {
-        C.k0 = kCuckooMul[2 * attempt];
-        C.k1 = kCuckooMul[2 * attempt + 1];
-        for (uint32_t j = threadIdx.x; j < 2 * m; j += blockDim.x) t[j] = kEmpty;
-        if (threadIdx.x == 0) cs->nstash = 0;
-        __syncthreads();
-        for (uint32_t j = threadIdx.x; j < s; j += blockDim.x) cuckoo_insert(C, row[j], cs);
-        __syncthreads();
-        const unsigned ns = cs->nstash;
-        __syncthreads();  // everyone has read it before a rebuild clears it
-        if (ns <= kStash) {
-            C.nstash = ns;
-            return C;
-        }
-    }
-    if (threadIdx.x == 0) atomicOr(err, kGuardInsert);  // keys were dropped: the count reports an error
-    C.nstash = kStash;
-    return C;
-}
-
 // Block class.  The hashed set lives in shared memory: a cuckoo table
-// (block_table = 0) or the bucketed table (block_table = 1).
+// (table_kind = 0) or the bucketed table (table_kind = 1).
 template <bool kCuckoo>
 __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict__ tasks, const uint32_t *__restrict__ rows,
                                                       const uint32_t *__restrict__ ntask,
@@ -881,18 +931,21 @@ uint32_t pow2_at_least(uint64_t x, uint32_t lo) {
 
 }  // namespace
 
-// Buckets per table: enough for load factor 1/2 at the class cap.
-uint32_t warp_table_buckets(const Tuning &tu) { return pow2_at_least((tu.warp_cap + 1) / 2, 16); }
-// Block class: cuckoo slots per table (>= 1.25 block_cap), or buckets.
+// Shared-memory sets of the warp and block classes (table_kind 0: cuckoo
+// slots per table, >= 1.25 x the class cap; 1: buckets, load <= 1/2).
+uint32_t warp_table_units(const Tuning &tu) {
+    return tu.table_kind == 0 ? pow2_at_least((uint64_t)tu.warp_cap + tu.warp_cap / 4, 64)
+                              : pow2_at_least((tu.warp_cap + 1) / 2, 16);
+}
 uint32_t block_table_units(const Tuning &tu) {
-    return tu.block_table == 0 ? pow2_at_least((uint64_t)tu.block_cap + tu.block_cap / 4, 64)
-                               : pow2_at_least((tu.block_cap + 1) / 2, 16);
+    return tu.table_kind == 0 ? pow2_at_least((uint64_t)tu.block_cap + tu.block_cap / 4, 64)
+                              : pow2_at_least((tu.block_cap + 1) / 2, 16);
 }
 size_t warp_kernel_smem(const Tuning &tu) {
-    return (size_t)tu.warps_per_block * (16ull * warp_table_buckets(tu) + kWarpMetaBytes);
+    return (size_t)tu.warps_per_block * (warp_set_bytes(tu.table_kind == 0, warp_table_units(tu)) + kWarpMetaBytes);
 }
 size_t block_kernel_smem(const Tuning &tu) {
-    return slice_smem_bytes(tu.max_v) + (tu.block_table == 0 ? 8ull : 16ull) * block_table_units(tu);
+    return slice_smem_bytes(tu.max_v) + (tu.table_kind == 0 ? 8ull : 16ull) * block_table_units(tu);
 }
 size_t hub_kernel_smem(const Tuning &tu) { return slice_smem_bytes(tu.max_v) + (1ull << tu.hub_filter_log2) / 8; }
 
@@ -928,23 +981,24 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[4], s));
     if (hi0 > lo0) {
         const size_t smem = warp_kernel_smem(tu);
-        TC_CUDA(ctx, cudaFuncSetAttribute(k_isect_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        auto kern = tu.table_kind == 0 ? k_isect_warp<true> : k_isect_warp<false>;
+        TC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
-        TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect_warp, 32 * tu.warps_per_block, smem));
+        TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * tu.warps_per_block, smem));
         if (per_sm < 1) per_sm = 1;
         uint64_t grid = (uint64_t)ctx->num_sms * per_sm;
         const uint64_t need = (hi0 - lo0 + tu.warps_per_block - 1) / tu.warps_per_block;
         if (grid > need) grid = need;
-        k_isect_warp<<<(unsigned)grid, 32 * tu.warps_per_block, smem, s>>>(b.tasks[0], b.rows[0], b.ntask[0], b.rp,
-                                                                            b.adj2, b.fcnt, b.eoff, b.erec, ctx->d_ctl,
-                                                                            warp_table_buckets(tu), tu.flat_cap, lo0, hi0,
-                                                                            b.groups);
+        kern<<<(unsigned)grid, 32 * tu.warps_per_block, smem, s>>>(b.tasks[0], b.rows[0], b.ntask[0], b.rp, b.adj2,
+                                                                   b.fcnt, b.eoff, b.erec, ctx->d_ctl,
+                                                                   warp_table_units(tu), tu.flat_cap, lo0, hi0,
+                                                                   b.groups);
         note_launch(ctx);
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[5], s));
     if (hi1 > lo1) {
         const size_t smem = block_kernel_smem(tu);
-        auto kern = tu.block_table == 0 ? k_isect_block<true> : k_isect_block<false>;
+        auto kern = tu.table_kind == 0 ? k_isect_block<true> : k_isect_block<false>;
         TC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
         TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tu.block_threads, smem));

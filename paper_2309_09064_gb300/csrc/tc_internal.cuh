@@ -24,7 +24,7 @@ constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 // Class boundaries of the intersection stage by the size s(u) = |A(u)| +
 // |G1(u)| of the hashed set of the earlier endpoint u of a horizontal edge.
 struct Tuning {
-    uint32_t warp_cap = 1024;        // s(u) <= warp_cap: warp tasks, per-warp smem table
+    uint32_t warp_cap = 768;         // s(u) <= warp_cap: warp tasks, per-warp smem table
     uint32_t block_cap = 13107;      // s(u) <= block_cap: block tasks, smem table; larger: hub tasks
     uint32_t task_work = 131072;     // target probes per block task (at least 2 s(u))
     uint32_t warps_per_block = 8;    // warp-class kernel: warps per block
@@ -36,8 +36,8 @@ struct Tuning {
     uint32_t hub_threads = 1024;     // hub kernel threads
     uint32_t hub_filter_log2 = 20;   // hub prefilter bits (log2)
     uint32_t tiny_cap = 16;          // s(u) <= tiny_cap and deg(u) <= 4 tiny_cap: thread-per-row merges (0: off)
-    uint32_t block_table = 0;        // block-class set: 0 two-choice cuckoo table, 1 bucketed table
-    uint32_t flat_cap = 64;          // warp class: probe ranges shorter than this are concatenated across lanes
+    uint32_t table_kind = 0;         // warp/block-class sets: 0 two-choice cuckoo tables, 1 bucketed tables
+    uint32_t flat_cap = 128;         // warp class: probe ranges shorter than this are concatenated across lanes
 };
 
 // Control block in device memory: counters the kernels update and the host
