@@ -148,7 +148,17 @@ struct CuckooTable {
     uint32_t m, shift;      // m slots per table, shift = 32 - log2 m
     uint32_t k0, k1;        // multipliers of this build
     uint32_t nstash;
+    uint32_t a0, a1;        // shared-window byte addresses of T0 and T1 (lookups use 32-bit addressing)
 };
+
+// 32-bit load from the shared window at byte address addr.
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t shared_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Hub rows: shared prefilter (2^hub_filter_log2 bits) in front of the exact
 // n-bit bitmap (by rank) in global memory.
@@ -187,8 +197,8 @@ __device__ __forceinline__ void lookup_batch(const CuckooTable &C, const uint32_
     uint32_t a[N], b[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        a[i] = C.t[(w[i] * C.k0) >> C.shift];
-        b[i] = C.t[C.m + ((w[i] * C.k1) >> C.shift)];
+        a[i] = lds_u32(C.a0 + (((w[i] * C.k0) >> C.shift) << 2));
+        b[i] = lds_u32(C.a1 + (((w[i] * C.k1) >> C.shift) << 2));
     }
 #pragma unroll
     for (int i = 0; i < N; ++i) hit[i] = a[i] == w[i] || b[i] == w[i];
@@ -254,28 +264,54 @@ template <int U, class Set>
 __device__ __forceinline__ void probe_row(const Set &set, const uint32_t *__restrict__ adj2, unsigned long long b,
                                           uint32_t j_lo, uint32_t j_hi, uint32_t split, Acc &acc) {
     const unsigned lane = lane_id();
-    const uint32_t *row = adj2 + b;
-    Hits hits;
+    const uint32_t *row = adj2 + b + lane;
+    uint32_t same = 0, cross = 0;
     for (uint32_t j0 = j_lo; j0 < j_hi; j0 += 32u * U) {
         uint32_t w[U];
+        if (j0 + 32u * U <= j_hi) {  // full step: no bounds checks
 #pragma unroll
-        for (int i = 0; i < U; ++i) {
-            const uint32_t j = j0 + (uint32_t)i * 32u + lane;
-            w[i] = j < j_hi ? __ldg(row + j) : Set::kPad;
+            for (int i = 0; i < U; ++i) w[i] = __ldg(row + j0 + (uint32_t)i * 32u);
+        } else {
+#pragma unroll
+            for (int i = 0; i < U; ++i) {
+                const uint32_t j = j0 + (uint32_t)i * 32u;
+                w[i] = j + lane < j_hi ? __ldg(row + j) : Set::kPad;
+            }
         }
+        bool hit[U];
         constexpr int B = Set::kBatch;
 #pragma unroll
         for (int half = 0; half < U; half += B) {
             uint32_t ww[B];
-            bool hit[B];
+            bool hh[B];
 #pragma unroll
             for (int i = 0; i < B; ++i) ww[i] = w[half + i];
-            lookup_batch(set, ww, hit);
+            lookup_batch(set, ww, hh);
 #pragma unroll
-            for (int i = 0; i < B; ++i) hits.add(hit[i], j0 + (uint32_t)(half + i) * 32u + lane < split);
+            for (int i = 0; i < B; ++i) hit[half + i] = hh[i];
+        }
+        // the split (end of the A part) is the same for the whole warp: most
+        // steps lie wholly on one side of it
+        uint32_t c = 0;
+        if (j0 + 32u * U <= split) {
+#pragma unroll
+            for (int i = 0; i < U; ++i) c += hit[i];
+            same += c;
+        } else if (j0 >= split) {
+#pragma unroll
+            for (int i = 0; i < U; ++i) c += hit[i];
+            cross += c;
+        } else {
+#pragma unroll
+            for (int i = 0; i < U; ++i) {
+                const bool in_a = j0 + (uint32_t)i * 32u + lane < split;
+                same += hit[i] && in_a;
+                cross += hit[i] && !in_a;
+            }
         }
     }
-    hits.flush(acc);
+    acc.same += same;
+    acc.cross += cross;
 }
 
 // Short probe ranges, concatenated: range r covers positions
@@ -396,7 +432,7 @@ __device__ __forceinline__ uint32_t cuckoo_slots_for(uint32_t s, uint32_t m_cap)
 __device__ __forceinline__ CuckooTable cuckoo_build(uint32_t *t, uint32_t m_cap, const uint32_t *__restrict__ row,
                                                     uint32_t s, CuckooShared *cs, unsigned int *err) {
     const uint32_t m = cuckoo_slots_for(s, m_cap);
-    CuckooTable C{t, cs->stash, m, (uint32_t)__clz(m) + 1u, 0, 0, 0};
+    CuckooTable C{t, cs->stash, m, (uint32_t)__clz(m) + 1u, 0, 0, 0, shared_addr(t), shared_addr(t + m)};
     for (int attempt = 0; attempt < kCuckooAttempts; ++attempt) {
         C.k0 = kCuckooMul[2 * attempt];
         C.k1 = kCuckooMul[2 * attempt + 1];
@@ -422,7 +458,7 @@ __device__ __forceinline__ CuckooTable warp_cuckoo_build(uint32_t *t, uint32_t m
                                                          uint32_t s, CuckooShared *cs, unsigned int *err) {
     const unsigned lane = lane_id();
     const uint32_t m = cuckoo_slots_for(s, m_cap);
-    CuckooTable C{t, cs->stash, m, (uint32_t)__clz(m) + 1u, 0, 0, 0};
+    CuckooTable C{t, cs->stash, m, (uint32_t)__clz(m) + 1u, 0, 0, 0, shared_addr(t), shared_addr(t + m)};
     for (int attempt = 0; attempt < kCuckooAttempts; ++attempt) {
         C.k0 = kCuckooMul[2 * attempt];
         C.k1 = kCuckooMul[2 * attempt + 1];
@@ -479,7 +515,7 @@ __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__
     unsigned long long build = 0, done = 0, inserts = 0;
     uint32_t cur_row = 0xFFFFFFFFu;
     BucketTable T{reinterpret_cast<uint4 *>(mine), 0, 0, &ctl->error};
-    CuckooTable C{reinterpret_cast<uint32_t *>(mine), cs->stash, 64, 26, 0, 0, 0};
+    CuckooTable C{reinterpret_cast<uint32_t *>(mine), cs->stash, 64, 26, 0, 0, 0, 0, 0};
     const long long t_start = clock64();
     for (;;) {
         unsigned long long k = 0;
@@ -799,7 +835,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
     Acc acc;
     unsigned long long build = 0, done = 0, inserts = 0;
     uint32_t cur_row = 0xFFFFFFFFu;
-    CuckooTable C{reinterpret_cast<uint32_t *>(tab), cs.stash, 64, 26, 0, 0, 0};
+    CuckooTable C{reinterpret_cast<uint32_t *>(tab), cs.stash, 64, 26, 0, 0, 0, 0, 0};
     BucketTable T{reinterpret_cast<uint4 *>(tab), 0, 0, &ctl->error};
     init_task_smem(&ts);
     const long long t_start = clock64();

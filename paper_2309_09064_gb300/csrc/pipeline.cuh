@@ -33,6 +33,7 @@ struct PipeBufs {
     uint32_t *gcnt = nullptr;       // [n]   |G1(x)| level-spanning neighbours (ranks)
     uint32_t *adj2 = nullptr;       // [S]   the rewritten rows; A(x) (ranks) is descending
     uint32_t *big = nullptr;        // [n]   rows whose A part the block sorter sorts
+    uint32_t *huge = nullptr;       // [n]   rows of very high degree (filled by a block each)
     uint4 *vmeta = nullptr;         // [n]   {A start lo, A start hi, |A(x)|, |G1(x)|}
     uint32_t *chunk_row = nullptr;  // first row of every chunk of kRecChunk probe records
     uint64_t *eoff = nullptr;       // [n+1] exclusive prefix of fcnt: first probe record of x

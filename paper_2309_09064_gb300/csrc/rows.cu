@@ -21,6 +21,7 @@ namespace {
 constexpr uint32_t kSmallRow = 32;    // rows of degree <= 32: one lane each
 constexpr uint32_t kWarpA = 1024;     // A parts up to this size: sorted by the warp in shared memory
 constexpr uint32_t kSortCap = 32768;  // A parts up to this size: sorted (larger: k_sort_big); beyond: unsorted
+constexpr uint32_t kHugeRow = 8192;   // rows of higher degree: one block each (k_row_fill_huge)
 constexpr int kFillThreads = 256;
 
 // Sort buf[0..P) ascending (P a power of two) with one warp: bitonic network.
@@ -75,17 +76,13 @@ __global__ void __launch_bounds__(kFillThreads) k_row_fill(uint32_t n, const uin
                                                            const uint32_t *__restrict__ lvp, uint32_t *__restrict__ adj2,
                                                            uint32_t *__restrict__ fcnt, uint32_t *__restrict__ gcnt,
                                                            uint4 *__restrict__ vmeta, uint32_t *__restrict__ big,
-                                                           Ctl *ctl) {
+                                                           uint32_t *__restrict__ huge, Ctl *ctl) {
     __shared__ uint32_t sbuf[kFillThreads / 32][kWarpA];
-    __shared__ unsigned long long s_e0;
-    if (threadIdx.x == 0) s_e0 = 0;
-    __syncthreads();
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     uint32_t *buf = sbuf[warp];
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t n_round = ((uint64_t)n + 31) & ~uint64_t(31);
-    unsigned long long e0 = 0;
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_round; x += stride) {
         const bool valid = x < n;
         const uint64_t b = valid ? rp[x] : 0;
@@ -114,10 +111,12 @@ __global__ void __launch_bounds__(kFillThreads) k_row_fill(uint32_t n, const uin
             gcnt[x] = gp;
             const uint64_t as = b + fp;
             vmeta[x] = make_uint4((uint32_t)as, (uint32_t)(as >> 32), ap, gp);
-            e0 += fp;
         }
         __syncwarp();
-        unsigned pending = __ballot_sync(0xFFFFFFFFu, valid && dx > kSmallRow);
+        // rows of degree above kHugeRow go to k_row_fill_huge (a block each)
+        const unsigned huge_m = __ballot_sync(0xFFFFFFFFu, valid && dx > kHugeRow);
+        if (valid && dx > kHugeRow) huge[atomicAdd(&ctl->n_huge, 1u)] = (uint32_t)x;
+        unsigned pending = __ballot_sync(0xFFFFFFFFu, valid && dx > kSmallRow) & ~huge_m;
         while (pending) {
             const int src = __ffs(pending) - 1;
             pending &= pending - 1;
@@ -182,14 +181,86 @@ __global__ void __launch_bounds__(kFillThreads) k_row_fill(uint32_t n, const uin
                 gcnt[bx] = gp;
                 const uint64_t as = bb + fp;
                 vmeta[bx] = make_uint4((uint32_t)as, (uint32_t)(as >> 32), ap, gp);
-                e0 += fp;
             }
         }
     }
-    e0 = warp_sum(e0);
-    if (lane == 0 && e0) atomicAdd(&s_e0, e0);
-    __syncthreads();
-    if (threadIdx.x == 0 && s_e0) atomicAdd(&ctl->e0, s_e0);
+}
+
+// Rows of degree above kHugeRow, one block each (persistent over the list the
+// fill kernel built): a counting pass, then a writing pass with warp-
+// aggregated slot counters.  F and G1 come out in no particular order (the
+// intersections need none); A is written unsorted and listed for k_sort_big
+// (or left unsorted beyond kSortCap).
+template <bool kPacked>
+__global__ void __launch_bounds__(1024) k_row_fill_huge(const uint32_t *__restrict__ huge, Ctl *ctl,
+                                                        const uint64_t *__restrict__ rp,
+                                                        const uint32_t *__restrict__ col,
+                                                        const uint2 *__restrict__ lv,
+                                                        const uint32_t *__restrict__ lvp, uint32_t *__restrict__ adj2,
+                                                        uint32_t *__restrict__ fcnt, uint32_t *__restrict__ gcnt,
+                                                        uint4 *__restrict__ vmeta, uint32_t *__restrict__ big) {
+    __shared__ unsigned int cnt[3], pos[3];
+    const unsigned lane = lane_id();
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t nh = ctl->n_huge;
+    for (uint32_t i = blockIdx.x; i < nh; i += gridDim.x) {
+        const uint32_t x = huge[i];
+        const uint64_t b = rp[x];
+        const uint32_t d = (uint32_t)(rp[x + 1] - b);
+        const uint2 me = rank_level<kPacked>(lv, lvp, x);
+        if (threadIdx.x < 3) cnt[threadIdx.x] = pos[threadIdx.x] = 0;
+        __syncthreads();
+        uint32_t f = 0, g = 0;
+        for (uint32_t j = threadIdx.x; j < d; j += blockDim.x) {
+            const uint2 q = rank_level<kPacked>(lv, lvp, col[b + j]);
+            if (q.y != me.y) ++g;
+            else if (me.x < q.x) ++f;
+        }
+        f = warp_sum(f);
+        g = warp_sum(g);
+        if (lane == 0) {
+            atomicAdd(&cnt[0], f);
+            atomicAdd(&cnt[1], g);
+        }
+        __syncthreads();
+        const uint32_t F = cnt[0], G = cnt[1], A = d - F - G;
+        const uint32_t j_end = (d + 31) & ~31u;
+        for (uint32_t j = threadIdx.x; j < j_end; j += blockDim.x) {  // whole warps take part
+            bool isF = false, isG = false, isA = false;
+            uint32_t y = 0, ry = 0;
+            if (j < d) {
+                y = col[b + j];
+                const uint2 q = rank_level<kPacked>(lv, lvp, y);
+                ry = q.x;
+                if (q.y != me.y) isG = true;
+                else if (me.x < ry) isF = true;
+                else isA = true;
+            }
+            const unsigned mF = __ballot_sync(0xFFFFFFFFu, isF);
+            const unsigned mG = __ballot_sync(0xFFFFFFFFu, isG);
+            const unsigned mA = __ballot_sync(0xFFFFFFFFu, isA);
+            uint32_t bF = 0, bG = 0, bA = 0;
+            if (lane == 0) {
+                if (mF) bF = atomicAdd(&pos[0], __popc(mF));
+                if (mG) bG = atomicAdd(&pos[1], __popc(mG));
+                if (mA) bA = atomicAdd(&pos[2], __popc(mA));
+            }
+            bF = __shfl_sync(0xFFFFFFFFu, bF, 0);
+            bG = __shfl_sync(0xFFFFFFFFu, bG, 0);
+            bA = __shfl_sync(0xFFFFFFFFu, bA, 0);
+            if (isF) adj2[b + bF + __popc(mF & lt)] = y;
+            if (isA) adj2[b + F + bA + __popc(mA & lt)] = ry;
+            if (isG) adj2[b + d - 1 - (bG + __popc(mG & lt))] = ry;
+        }
+        if (threadIdx.x == 0) {
+            fcnt[x] = F;
+            gcnt[x] = G;
+            const uint64_t as = b + F;
+            vmeta[x] = make_uint4((uint32_t)as, (uint32_t)(as >> 32), A, G);
+            if (A > 1 && A <= kSortCap) big[atomicAdd(&ctl->n_big, 1u)] = x;
+        }
+        __syncthreads();
+    }
 }
 
 // A parts longer than kWarpA (and at most kSortCap): one block per row sorts
@@ -292,12 +363,18 @@ __global__ void k_chunk_rows(uint32_t n, const uint64_t *__restrict__ eoff, uint
 // below u (binary search in the descending A(v); all of A(v) when it was left
 // unsorted), and the probe record {start, length = |G1(v)| + p, split = p}
 // of the range at the end of v's slots.  One warp per chunk; every lane walks
-// from the chunk's first row to the rows of its own edges.
+// from the chunk's first row to the rows of its own edges, and runs the
+// binary searches of kRecBatch edges in lockstep (independent loads in
+// flight).  Block 0 also publishes |E0| = eoff[n].
+constexpr int kRecBatch = 4;
+
 __global__ void k_records(uint32_t n, const uint64_t *__restrict__ eoff, const uint32_t *__restrict__ chunk_row,
                           const uint64_t *__restrict__ rp, const uint32_t *__restrict__ adj2,
-                          const uint2 *__restrict__ lv, const uint4 *__restrict__ vmeta, uint4 *__restrict__ erec) {
+                          const uint2 *__restrict__ lv, const uint4 *__restrict__ vmeta, uint4 *__restrict__ erec,
+                          Ctl *ctl) {
     const unsigned lane = lane_id();
     const uint64_t E = eoff[n];
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->e0 = E;
     const uint64_t chunks = (E + kRecChunk - 1) / kRecChunk;
     const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t c = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < chunks; c += warps) {
@@ -305,30 +382,53 @@ __global__ void k_records(uint32_t n, const uint64_t *__restrict__ eoff, const u
         uint32_t u = chunk_row[c];
         uint64_t u_lo = eoff[u], u_hi = eoff[u + 1], fb = rp[u];
         uint32_t ru = lv[u].x;
-        for (uint64_t e = e_lo + lane; e < e_hi; e += 32) {
-            while (e >= u_hi) {  // rows of no edge have u_lo == u_hi and are skipped
-                ++u;
-                u_lo = u_hi;
-                u_hi = eoff[u + 1];
-                fb = rp[u];
-                ru = lv[u].x;
-            }
-            const uint32_t v = adj2[fb + (e - u_lo)];
-            const uint4 m = vmeta[v];
-            const uint64_t as = ((uint64_t)m.y << 32) | m.x;
-            const uint32_t av = m.z, gv = m.w;
-            uint32_t p = av;
-            if (av <= kSortCap) {
-                const uint32_t *A = adj2 + as;
-                uint32_t lo = 0, hi = av;  // first position holding a rank below ru
-                while (lo < hi) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (A[mid] < ru) hi = mid; else lo = mid + 1;
+        for (uint64_t e0 = e_lo + lane; e0 < e_hi; e0 += 32 * kRecBatch) {
+            uint32_t r[kRecBatch], lo[kRecBatch], hi[kRecBatch], av[kRecBatch], gv[kRecBatch];
+            uint64_t as[kRecBatch];
+            bool ok[kRecBatch];
+#pragma unroll
+            for (int i = 0; i < kRecBatch; ++i) {
+                const uint64_t e = e0 + 32ull * i;
+                ok[i] = e < e_hi;
+                uint32_t v = 0;
+                if (ok[i]) {
+                    while (e >= u_hi) {  // rows of no edge have u_lo == u_hi and are skipped
+                        ++u;
+                        u_lo = u_hi;
+                        u_hi = eoff[u + 1];
+                        fb = rp[u];
+                        ru = lv[u].x;
+                    }
+                    v = adj2[fb + (e - u_lo)];
                 }
-                p = av - lo;
+                r[i] = ru;
+                const uint4 m = ok[i] ? vmeta[v] : make_uint4(0, 0, 0, 0);
+                as[i] = ((uint64_t)m.y << 32) | m.x;
+                av[i] = m.z;
+                gv[i] = m.w;
+                lo[i] = 0;
+                hi[i] = av[i] <= kSortCap ? av[i] : 0;  // unsorted A: no search, p = |A(v)|
             }
-            const uint64_t start = as + av - p;
-            erec[e] = make_uint4((uint32_t)start, (uint32_t)(start >> 32), gv + p, p);
+            // first position holding a rank below r, all searches in lockstep
+            for (int step = 0; step < 17; ++step) {
+                bool any = false;
+#pragma unroll
+                for (int i = 0; i < kRecBatch; ++i) {
+                    if (lo[i] < hi[i]) {
+                        const uint32_t mid = (lo[i] + hi[i]) >> 1;
+                        if (adj2[as[i] + mid] < r[i]) hi[i] = mid; else lo[i] = mid + 1;
+                        any = true;
+                    }
+                }
+                if (!any) break;
+            }
+#pragma unroll
+            for (int i = 0; i < kRecBatch; ++i) {
+                if (!ok[i]) continue;
+                const uint32_t p = av[i] <= kSortCap ? av[i] - lo[i] : av[i];
+                const uint64_t start = as[i] + av[i] - p;
+                erec[e0 + 32ull * i] = make_uint4((uint32_t)start, (uint32_t)(start >> 32), gv[i] + p, p);
+            }
         }
     }
 }
@@ -407,10 +507,19 @@ tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_de
     uint32_t launches = 1;
     if (b.lvp)
         k_row_fill<true><<<grid_for(n, kFillThreads, cap), kFillThreads, 0, s>>>(
-            n, b.rp, b.col, b.lv, b.lvp, b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big, ctx->d_ctl);
+            n, b.rp, b.col, b.lv, b.lvp, b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big, b.huge, ctx->d_ctl);
     else
         k_row_fill<false><<<grid_for(n, kFillThreads, cap), kFillThreads, 0, s>>>(
-            n, b.rp, b.col, b.lv, b.lvp, b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big, ctx->d_ctl);
+            n, b.rp, b.col, b.lv, b.lvp, b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big, b.huge, ctx->d_ctl);
+    if (max_deg > kHugeRow) {
+        if (b.lvp)
+            k_row_fill_huge<true><<<(unsigned)ctx->num_sms, 1024, 0, s>>>(b.huge, ctx->d_ctl, b.rp, b.col, b.lv, b.lvp,
+                                                                         b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big);
+        else
+            k_row_fill_huge<false><<<(unsigned)ctx->num_sms, 1024, 0, s>>>(b.huge, ctx->d_ctl, b.rp, b.col, b.lv, b.lvp,
+                                                                          b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big);
+        ++launches;
+    }
     if (max_deg > kWarpA) {
         const int smem = (int)(4 * kSortCap);
         TC_CUDA(ctx, cudaFuncSetAttribute(k_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -419,7 +528,7 @@ tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_de
     }
     launches += scan_u32_to_u64(b.fcnt, b.eoff, n, b.scan_tmp, s);
     k_chunk_rows<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.eoff, b.chunk_row);
-    k_records<<<cap, 256, 0, s>>>(n, b.eoff, b.chunk_row, b.rp, b.adj2, b.lv, b.vmeta, b.erec);
+    k_records<<<cap, 256, 0, s>>>(n, b.eoff, b.chunk_row, b.rp, b.adj2, b.lv, b.vmeta, b.erec, ctx->d_ctl);
     // fdeg and R are free after the levels: class of every vertex, 0/1 indicator
     k_class_flags<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.fcnt, b.deg, b.fdeg, ctx->d_ctl, tu.warp_cap, tu.block_cap,
                                                         tu.tiny_cap);

@@ -26,7 +26,7 @@ constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 struct Tuning {
     uint32_t warp_cap = 768;         // s(u) <= warp_cap: warp tasks, per-warp smem table
     uint32_t block_cap = 13107;      // s(u) <= block_cap: block tasks, smem table; larger: hub tasks
-    uint32_t task_work = 131072;     // target probes per block task (at least 2 s(u))
+    uint32_t task_work = 1048576;    // target probes per block task (at least 2 s(u))
     uint32_t warps_per_block = 8;    // warp-class kernel: warps per block
     uint32_t block_threads = 1024;   // block-class kernel threads
     uint32_t warp_task_work = 16384; // target probes per warp task
@@ -68,7 +68,8 @@ struct Ctl {
     unsigned int p_slot, p_queue, p_level;  // where the persistent BFS stopped
     unsigned int bar_count, bar_gen;        // grid barrier of the persistent BFS
     unsigned int n_big;              // rows whose A part the block sorter sorts
-    unsigned int pad[3];
+    unsigned int n_huge;             // rows of very high degree filled by a block each
+    unsigned int pad[2];
 };
 
 // ----------------------------------------------------------------------------- arena
