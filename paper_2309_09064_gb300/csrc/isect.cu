@@ -747,27 +747,46 @@ __device__ __forceinline__ void load_slice(const SliceSmem &S, const uint4 *__re
     }
 }
 
-// Warps take the slice's pieces one at a time (shared counter).
+// Warps take the slice's pieces in batches of up to 32 (shared counter): the
+// lanes of a warp locate the pieces of a batch in parallel (one binary search
+// each over seg), then the warp walks them one by one.  The batch shrinks for
+// small slices so that every warp of the block still gets work.
 template <class Set>
 __device__ __forceinline__ void probe_slice(const Set &set, const SliceSmem &S, uint32_t nv,
                                             const uint32_t *__restrict__ adj2, unsigned int *next, Acc &acc) {
     const unsigned lane = lane_id();
     const uint32_t total = S.seg[nv];
+    const uint32_t nwarps = blockDim.x >> 5;
+    uint32_t batch = total / (4 * nwarps);
+    batch = batch < 1 ? 1 : (batch > 32 ? 32 : batch);
     for (;;) {
-        uint32_t g = 0;
-        if (lane == 0) g = atomicAdd(next, 1u);
-        g = __shfl_sync(0xFFFFFFFFu, g, 0);
-        if (g >= total) break;
-        uint32_t a = 0, e = nv;  // range of piece g: largest t with seg[t] <= g
-        while (e - a > 1) {
-            const uint32_t m = (a + e) >> 1;
-            if (S.seg[m] <= g) a = m; else e = m;
+        uint32_t g0 = 0;
+        if (lane == 0) g0 = atomicAdd(next, batch);
+        g0 = __shfl_sync(0xFFFFFFFFu, g0, 0);
+        if (g0 >= total) break;
+        const uint32_t cnt = min(batch, total - g0);
+        unsigned long long b = 0;
+        uint32_t j_lo = 0, j_hi = 0, h = 0;
+        if (lane < cnt) {
+            const uint32_t g = g0 + lane;
+            uint32_t a = 0, e = nv;  // range of piece g: largest t with seg[t] <= g
+            while (e - a > 1) {
+                const uint32_t m = (a + e) >> 1;
+                if (S.seg[m] <= g) a = m; else e = m;
+            }
+            j_lo = (g - S.seg[a]) * kSeg;
+            j_hi = min(S.len[a], j_lo + kSeg);
+            b = S.b[a];
+            h = S.h[a];
+            acc.probes += j_hi - j_lo;
         }
-        const uint32_t len = S.len[a];
-        const uint32_t j_lo = (g - S.seg[a]) * kSeg;
-        const uint32_t j_hi = min(len, j_lo + kSeg);
-        if (lane == 0) acc.probes += j_hi - j_lo;
-        probe_row<Set::kUnroll>(set, adj2, S.b[a], j_lo, j_hi, S.h[a], acc);
+        for (uint32_t t = 0; t < cnt; ++t) {
+            const unsigned long long bt = __shfl_sync(0xFFFFFFFFu, b, t);
+            const uint32_t lo = __shfl_sync(0xFFFFFFFFu, j_lo, t);
+            const uint32_t hi = __shfl_sync(0xFFFFFFFFu, j_hi, t);
+            const uint32_t ht = __shfl_sync(0xFFFFFFFFu, h, t);
+            probe_row<Set::kUnroll>(set, adj2, bt, lo, hi, ht, acc);
+        }
     }
 }
 
