@@ -54,6 +54,7 @@ struct BucketTable {
     static constexpr int kUnroll = 8;  // ids in flight per lane
     static constexpr int kBatch = 4;   // lookups resolved together
     static constexpr uint32_t kPad = kEmpty;  // probe padding (lookups reject it)
+    static constexpr bool kFineTail = false;
     uint4 *bk;
     uint32_t shift, mask;  // home bucket = hash >> shift; mask = buckets - 1
     unsigned int *err;     // device error word: a walk longer than the table sets kGuardTable
@@ -143,6 +144,7 @@ struct CuckooTable {
     static constexpr int kUnroll = 8;
     static constexpr int kBatch = 8;
     static constexpr uint32_t kPad = kNone;
+    static constexpr bool kFineTail = false;
     uint32_t *t;            // 2m slots: T0 = t[0, m), T1 = t[m, 2m)
     const uint32_t *stash;  // shared, nstash entries
     uint32_t m, shift;      // m slots per table, shift = 32 - log2 m
@@ -166,6 +168,7 @@ struct HubSet {
     static constexpr int kUnroll = 8;  // ids in flight per lane
     static constexpr int kBatch = 8;   // prefilter tests, then all bitmap loads together
     static constexpr uint32_t kPad = kEmpty;  // probe padding (lookups reject it)
+    static constexpr bool kFineTail = true;   // bitmap lookups go to L2: skip padding work
     const uint32_t *filter;  // shared
     const uint32_t *bits;    // global, read-only while probing
     uint32_t fshift;
@@ -260,55 +263,77 @@ __device__ __forceinline__ void lookup_all(const Set &set, const uint32_t (&w)[U
 // Positions [j_lo, j_hi) of one probe range adj2[b ..] with one warp, lanes
 // striding over the positions with U loads in flight each; positions below
 // `split` are the A part.
+// Count the hits of one step of U x 32 positions starting at j0 into same /
+// cross: the split (end of the A part) is the same for the whole warp, and
+// most steps lie wholly on one side of it.
+template <int U>
+__device__ __forceinline__ void count_step(const bool (&hit)[U], uint32_t j0, uint32_t split, uint32_t lane,
+                                           uint32_t &same, uint32_t &cross) {
+    uint32_t c = 0;
+    if (j0 + 32u * U <= split) {
+#pragma unroll
+        for (int i = 0; i < U; ++i) c += hit[i];
+        same += c;
+    } else if (j0 >= split) {
+#pragma unroll
+        for (int i = 0; i < U; ++i) c += hit[i];
+        cross += c;
+    } else {
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            const bool in_a = j0 + (uint32_t)i * 32u + lane < split;
+            same += hit[i] && in_a;
+            cross += hit[i] && !in_a;
+        }
+    }
+}
+
 template <int U, class Set>
+__device__ __forceinline__ void lookup_step(const Set &set, const uint32_t (&w)[U], bool (&hit)[U]) {
+    constexpr int B = Set::kBatch < U ? Set::kBatch : U;
+#pragma unroll
+    for (int half = 0; half < U; half += B) {
+        uint32_t ww[B];
+        bool hh[B];
+#pragma unroll
+        for (int i = 0; i < B; ++i) ww[i] = w[half + i];
+        lookup_batch(set, ww, hh);
+#pragma unroll
+        for (int i = 0; i < B; ++i) hit[half + i] = hh[i];
+    }
+}
+
+// Positions [j_lo, j_hi) of one probe range adj2[b ..] with one warp: full
+// steps of U x 32 positions (U loads in flight per lane, no bounds checks),
+// then the ragged end in one bounds-checked step of U x 32 positions, or in
+// steps of 64 positions (kFineTail: pays where lookups are expensive);
+// positions below `split` are the A part.
+template <int U, bool kFineTail = false, class Set>
 __device__ __forceinline__ void probe_row(const Set &set, const uint32_t *__restrict__ adj2, unsigned long long b,
                                           uint32_t j_lo, uint32_t j_hi, uint32_t split, Acc &acc) {
     const unsigned lane = lane_id();
     const uint32_t *row = adj2 + b + lane;
     uint32_t same = 0, cross = 0;
-    for (uint32_t j0 = j_lo; j0 < j_hi; j0 += 32u * U) {
+    uint32_t j0 = j_lo;
+    for (; j0 + 32u * U <= j_hi; j0 += 32u * U) {
         uint32_t w[U];
-        if (j0 + 32u * U <= j_hi) {  // full step: no bounds checks
-#pragma unroll
-            for (int i = 0; i < U; ++i) w[i] = __ldg(row + j0 + (uint32_t)i * 32u);
-        } else {
-#pragma unroll
-            for (int i = 0; i < U; ++i) {
-                const uint32_t j = j0 + (uint32_t)i * 32u;
-                w[i] = j + lane < j_hi ? __ldg(row + j) : Set::kPad;
-            }
-        }
         bool hit[U];
-        constexpr int B = Set::kBatch;
 #pragma unroll
-        for (int half = 0; half < U; half += B) {
-            uint32_t ww[B];
-            bool hh[B];
+        for (int i = 0; i < U; ++i) w[i] = __ldg(row + j0 + (uint32_t)i * 32u);
+        lookup_step<U>(set, w, hit);
+        count_step<U>(hit, j0, split, lane, same, cross);
+    }
+    constexpr int T = kFineTail ? 2 : U;
+    for (; j0 < j_hi; j0 += 32u * T) {
+        uint32_t w[T];
+        bool hit[T];
 #pragma unroll
-            for (int i = 0; i < B; ++i) ww[i] = w[half + i];
-            lookup_batch(set, ww, hh);
-#pragma unroll
-            for (int i = 0; i < B; ++i) hit[half + i] = hh[i];
+        for (int i = 0; i < T; ++i) {
+            const uint32_t j = j0 + (uint32_t)i * 32u;
+            w[i] = j + lane < j_hi ? __ldg(row + j) : Set::kPad;
         }
-        // the split (end of the A part) is the same for the whole warp: most
-        // steps lie wholly on one side of it
-        uint32_t c = 0;
-        if (j0 + 32u * U <= split) {
-#pragma unroll
-            for (int i = 0; i < U; ++i) c += hit[i];
-            same += c;
-        } else if (j0 >= split) {
-#pragma unroll
-            for (int i = 0; i < U; ++i) c += hit[i];
-            cross += c;
-        } else {
-#pragma unroll
-            for (int i = 0; i < U; ++i) {
-                const bool in_a = j0 + (uint32_t)i * 32u + lane < split;
-                same += hit[i] && in_a;
-                cross += hit[i] && !in_a;
-            }
-        }
+        lookup_step<T>(set, w, hit);
+        count_step<T>(hit, j0, split, lane, same, cross);
     }
     acc.same += same;
     acc.cross += cross;
@@ -785,7 +810,7 @@ __device__ __forceinline__ void probe_slice(const Set &set, const SliceSmem &S, 
             const uint32_t lo = __shfl_sync(0xFFFFFFFFu, j_lo, t);
             const uint32_t hi = __shfl_sync(0xFFFFFFFFu, j_hi, t);
             const uint32_t ht = __shfl_sync(0xFFFFFFFFu, h, t);
-            probe_row<Set::kUnroll>(set, adj2, bt, lo, hi, ht, acc);
+            probe_row<Set::kUnroll, Set::kFineTail>(set, adj2, bt, lo, hi, ht, acc);
         }
     }
 }
