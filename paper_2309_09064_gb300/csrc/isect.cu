@@ -247,7 +247,8 @@ struct Hits {
 
 template <class Set, int U>
 __device__ __forceinline__ void lookup_all(const Set &set, const uint32_t (&w)[U], const bool (&in_a)[U], Hits &hits) {
-    constexpr int B = Set::kBatch;
+    constexpr int B = Set::kBatch < U ? Set::kBatch : U;
+    static_assert(U % B == 0, "the unroll must be a multiple of the lookup batch");
 #pragma unroll
     for (int half = 0; half < U; half += B) {
         uint32_t ww[B];
@@ -291,6 +292,7 @@ __device__ __forceinline__ void count_step(const bool (&hit)[U], uint32_t j0, ui
 template <int U, class Set>
 __device__ __forceinline__ void lookup_step(const Set &set, const uint32_t (&w)[U], bool (&hit)[U]) {
     constexpr int B = Set::kBatch < U ? Set::kBatch : U;
+    static_assert(U % B == 0, "the unroll must be a multiple of the lookup batch");
 #pragma unroll
     for (int half = 0; half < U; half += B) {
         uint32_t ww[B];
