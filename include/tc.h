@@ -219,6 +219,19 @@ tc_status tc_count_levels(tc_ctx *ctx, const tc_graph *g, uint32_t *d_levels, ui
                           tc_stats *stats);
 
 /*
+ * Count with levels the caller already has (the paper's case "when the
+ * results of a BFS are already available", Sec. III): d_levels is a device
+ * uint32_t[n], read only, e.g. the hop distances of any BFS forest.  The BFS
+ * of Algorithm 4 is skipped; everything else is as in tc_count.  The count is
+ * exact for any labelling in which the two ends of every edge differ by at
+ * most one level (then every triangle has one or three horizontal edges);
+ * the library checks that on the device and returns TC_ERR_INVALID if some
+ * edge breaks it.  t_same / t_cross and |E0| follow the given levels.
+ */
+tc_status tc_count_with_levels(tc_ctx *ctx, const tc_graph *g, const uint32_t *d_levels, uint64_t *triangles,
+                               tc_stats *stats);
+
+/*
  * One shard of a count split across nshards processes or devices (the
  * multi-GPU form of the method: BFS levels and rows are computed in full on
  * every shard, the intersection tasks -- contiguous slices of the oriented

@@ -53,7 +53,7 @@ size_t pipeline_bytes(const tc_ctx *ctx, uint32_t n, uint64_t slots, uint32_t ma
 }
 
 tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, const GroupSpec &groups,
-                         uint64_t *triangles, tc_stats *stats) {
+                         uint64_t *triangles, tc_stats *stats, const uint32_t *levels_in) {
     const uint32_t n = g.n;
     cudaStream_t s = ctx->stream;
     uint64_t hub_words = 0;
@@ -116,7 +116,7 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     k_ctl_reset<<<1, 128, 0, s>>>(ctx->d_ctl);
     note_launch(ctx);
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[0], s));
-    st = compute_levels(ctx, b, n, g.slots);
+    st = levels_in ? given_levels(ctx, b, n, levels_in) : compute_levels(ctx, b, n, g.slots);
     if (st != TC_OK) return st;
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[1], s));
     // the packed 4-byte {rank, level} word needs ranks below 2^24 and levels below 255

@@ -439,6 +439,58 @@ unsigned grid_for(uint64_t work, unsigned threads, unsigned cap) {
 constexpr uint32_t kPersistMaxF = 32768;          // frontier vertices (whole-grid mode)
 constexpr unsigned long long kPersistMaxE = 65536;  // frontier edges
 
+// Levels given by the caller: degrees, a copy of the levels, their maximum,
+// and the check that makes the count exact with them -- every edge joins
+// vertices whose levels differ by at most one (then a triangle's levels are
+// {l, l, l} or {l, l, l +- 1}: exactly three or exactly one horizontal edge).
+// Lanes own rows of degree <= 32, whole warps take the longer rows.
+__global__ void k_given_levels(uint32_t n, const uint64_t *__restrict__ rp, const uint32_t *__restrict__ col,
+                               const uint32_t *__restrict__ given, uint32_t *__restrict__ deg,
+                               uint32_t *__restrict__ L, Ctl *ctl) {
+    const unsigned lane = lane_id();
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t n_round = ((uint64_t)n + 31) & ~uint64_t(31);
+    unsigned bad = 0, top = 0;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_round; x += stride) {
+        const bool valid = x < n;
+        const uint64_t b = valid ? rp[x] : 0;
+        const uint32_t d = valid ? (uint32_t)(rp[x + 1] - b) : 0;
+        const uint32_t lx = valid ? given[x] : 0;
+        if (valid) {
+            deg[x] = d;
+            L[x] = lx;
+            top = lx > top ? lx : top;
+        }
+        if (valid && d <= 32)
+            for (uint32_t j = 0; j < d; ++j) {
+                const uint32_t ly = given[col[b + j]];
+                bad |= (ly > lx ? ly - lx : lx - ly) > 1u;
+            }
+        unsigned pending = __ballot_sync(0xFFFFFFFFu, valid && d > 32);
+        while (pending) {
+            const int src = __ffs(pending) - 1;
+            pending &= pending - 1;
+            const uint64_t bb = __shfl_sync(0xFFFFFFFFu, b, src);
+            const uint32_t bd = __shfl_sync(0xFFFFFFFFu, d, src);
+            const uint32_t bl = __shfl_sync(0xFFFFFFFFu, lx, src);
+            for (uint32_t j = lane; j < bd; j += 32) {
+                const uint32_t ly = given[col[bb + j]];
+                bad |= (ly > bl ? ly - bl : bl - ly) > 1u;
+            }
+        }
+    }
+    bad = __any_sync(0xFFFFFFFFu, bad);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned y = __shfl_xor_sync(0xFFFFFFFFu, top, o);
+        top = y > top ? y : top;
+    }
+    if (lane == 0) {
+        if (bad) atomicOr(&ctl->error, 0x200u);
+        if (top) atomicMax(&ctl->max_level, top);
+    }
+}
+
 }  // namespace
 
 // Pull the control block to the host (synchronises the stream).
@@ -539,6 +591,20 @@ tc_status selftest_barrier(tc_ctx *ctx, uint32_t timeout_ms) {
     if (st != TC_OK) return st;
     if (ctx->h_ctl->error == 4) return set_error(ctx, TC_ERR_TIMEOUT, "device wait timed out (self-test)");
     return set_error(ctx, TC_ERR_CUDA, "self-test barrier did not time out");
+}
+
+tc_status given_levels(tc_ctx *ctx, const PipeBufs &b, uint32_t n, const uint32_t *levels_in) {
+    cudaStream_t s = ctx->stream;
+    const unsigned cap = (unsigned)ctx->num_sms * 16u;
+    if (n == 0) return TC_OK;
+    k_given_levels<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.rp, b.col, levels_in, b.deg, b.L, ctx->d_ctl);
+    note_launch(ctx);
+    TC_CUDA(ctx, cudaGetLastError());
+    tc_status st = pull_ctl(ctx);
+    if (st != TC_OK) return st;
+    if (ctx->h_ctl->error & 0x200u)
+        return set_error(ctx, TC_ERR_INVALID, "given levels differ by more than one across an edge");
+    return TC_OK;
 }
 
 tc_status compute_levels(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t slots) {

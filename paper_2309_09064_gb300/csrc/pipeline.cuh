@@ -55,6 +55,9 @@ struct PipeBufs {
 };
 
 tc_status compute_levels(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t slots);
+// levels supplied by the caller (device uint32[n]): copied into b.L after the
+// check that they differ by at most one across every edge (TC_ERR_INVALID if not)
+tc_status given_levels(tc_ctx *ctx, const PipeBufs &b, uint32_t n, const uint32_t *levels_in);
 tc_status selftest_barrier(tc_ctx *ctx, uint32_t timeout_ms);
 // rank of every vertex in the working order, packed with its level (lv)
 tc_status compute_ranks(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_deg);
