@@ -219,6 +219,17 @@ tc_status tc_count_levels(tc_ctx *ctx, const tc_graph *g, uint32_t *d_levels, ui
                           tc_stats *stats);
 
 /*
+ * Triangles through every vertex: d_counts (device uint64_t[n], written by
+ * the library) gets t(x), the number of triangles containing x, and
+ * *triangles gets T (sum of t(x) = 3T).  The local clustering coefficient of
+ * x is 2 t(x) / (d(x) (d(x) - 1)).  Same method as tc_count; each triangle
+ * found adds one to its three vertices (one atomic per triangle for the
+ * third vertex, so this mode is slower than tc_count).
+ */
+tc_status tc_count_vertices(tc_ctx *ctx, const tc_graph *g, uint64_t *d_counts, uint64_t *triangles,
+                            tc_stats *stats);
+
+/*
  * Count with levels the caller already has (the paper's case "when the
  * results of a BFS are already available", Sec. III): d_levels is a device
  * uint32_t[n], read only, e.g. the hop distances of any BFS forest.  The BFS

@@ -20,7 +20,8 @@ __all__ = [
     "TcError", "TC_OK", "TC_NOT_READY", "TC_HOST", "TC_DEVICE", "TC_COPY", "TC_BORROW", "TC_VALIDATE",
     "TC_ORDER_DEGREE", "TC_ORDER_ID", "tc_create", "tc_destroy", "tc_last_error", "tc_set_stream",
     "tc_arena_bytes", "tc_build_csr", "tc_graph_from_csr", "tc_graph_info", "tc_graph_copy_out",
-    "tc_validate", "tc_graph_free", "tc_count", "tc_count_levels", "tc_count_with_levels", "tc_count_batch",
+    "tc_validate", "tc_graph_free", "tc_count", "tc_count_levels", "tc_count_with_levels", "tc_count_vertices",
+    "tc_count_batch",
     "tc_submit", "tc_poll",
     "tc_get_tuning", "tc_set_tuning", "tc_count_noalloc", "tc_poll_ex", "tc_count_shard", "tc_selftest_barrier",
     "library_path",
@@ -39,7 +40,8 @@ EXPORTED = ["tc_create", "tc_destroy", "tc_last_error", "tc_set_stream", "tc_get
             "tc_selftest_barrier",
             "tc_arena_bytes", "tc_build_csr",
             "tc_graph_from_csr", "tc_graph_info", "tc_graph_copy_out", "tc_validate", "tc_graph_free",
-            "tc_count", "tc_count_levels", "tc_count_with_levels", "tc_count_shard", "tc_count_batch", "tc_submit",
+            "tc_count", "tc_count_levels", "tc_count_with_levels", "tc_count_vertices", "tc_count_shard",
+            "tc_count_batch", "tc_submit",
             "tc_poll", "tc_poll_ex",
             "tc_count_noalloc"]
 
@@ -110,6 +112,7 @@ def _load():
         "tc_count": ([V, V, P(U64), P(tc_stats)], I),
         "tc_count_levels": ([V, V, V, P(U64), P(tc_stats)], I),
         "tc_count_with_levels": ([V, V, V, P(U64), P(tc_stats)], I),
+        "tc_count_vertices": ([V, V, V, P(U64), P(tc_stats)], I),
         "tc_count_shard": ([V, V, U32, U32, P(U64), P(tc_stats)], I),
         "tc_count_batch": ([V, U32, P(V), P(U64)], I),
         "tc_submit": ([V, V, P(U64)], I),
@@ -296,6 +299,17 @@ def tc_count_with_levels(ctx, g, levels):
     T = ctypes.c_uint64()
     st = tc_stats()
     _check(ctx, _lib.tc_count_with_levels(ctx, g, p, ctypes.byref(T), ctypes.byref(st)))
+    return T.value, st.to_dict()
+
+
+def tc_count_vertices(ctx, g, counts):
+    """Triangles through every vertex into `counts` (a CUDA tensor of n 8-byte ints, or a device address)."""
+    p, where = _ptr(counts)
+    if where != TC_DEVICE:
+        raise ValueError("counts must be a device buffer")
+    T = ctypes.c_uint64()
+    st = tc_stats()
+    _check(ctx, _lib.tc_count_vertices(ctx, g, p, ctypes.byref(T), ctypes.byref(st)))
     return T.value, st.to_dict()
 
 

@@ -8,6 +8,14 @@ namespace tc {
 
 namespace {
 
+// t(x) = hits credited to x by id + hits credited to x's rank.
+__global__ void k_vertex_finish(uint32_t n, const uint2 *__restrict__ lv, const unsigned long long *__restrict__ by_rank,
+                                unsigned long long *__restrict__ by_id) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride)
+        by_id[x] += by_rank[lv[x].x];
+}
+
 __global__ void k_ctl_reset(Ctl *ctl) {
     // zero everything, then the min-reduction identity for the root key
     unsigned int *w = reinterpret_cast<unsigned int *>(ctl);
@@ -53,12 +61,13 @@ size_t pipeline_bytes(const tc_ctx *ctx, uint32_t n, uint64_t slots, uint32_t ma
 }
 
 tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, const GroupSpec &groups,
-                         uint64_t *triangles, tc_stats *stats, const uint32_t *levels_in) {
+                         uint64_t *triangles, tc_stats *stats, const uint32_t *levels_in, uint64_t *vertex_counts) {
     const uint32_t n = g.n;
     cudaStream_t s = ctx->stream;
     uint64_t hub_words = 0;
     uint32_t hub_maps = 0;
-    const size_t need = pipeline_bytes(ctx, n, g.slots, g.max_deg, levels_out == nullptr, &hub_words, &hub_maps);
+    const size_t need = pipeline_bytes(ctx, n, g.slots, g.max_deg, levels_out == nullptr, &hub_words, &hub_maps) +
+                        (vertex_counts ? 8ull * ((size_t)n + 1) + 256 : 0);
     tc_status st = arena_reserve(ctx, need);
     if (st != TC_OK) return st;
     Arena &a = ctx->arena;
@@ -109,6 +118,15 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     b.hub_words = hub_words;
     if (hub_maps) b.hub_bits = a.take<uint32_t>(hub_words * hub_maps);
     b.groups = groups;
+    if (vertex_counts) {
+        b.vcount = reinterpret_cast<unsigned long long *>(vertex_counts);
+        b.vcount_rank = a.take<unsigned long long>((size_t)n + 1);
+        if (!b.vcount_rank) return set_error(ctx, TC_ERR_OOM, "arena carve failed");
+        if (n) {
+            TC_CUDA(ctx, cudaMemsetAsync(b.vcount, 0, 8ull * n, s));
+            TC_CUDA(ctx, cudaMemsetAsync(b.vcount_rank, 0, 8ull * n, s));
+        }
+    }
     ok = ok && b.fpref && b.eoff && b.lv && b.rkeys0 && b.rkeys1 && b.rcounts && b.roffs && b.adj2 && b.erec &&
          b.scan_tmp && b.task_pool && (!hub_maps || b.hub_bits);
     if (!ok) return set_error(ctx, TC_ERR_OOM, "arena carve failed");
@@ -136,6 +154,12 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
     st = intersect(ctx, b, n);
     if (st != TC_OK) return st;
+    if (vertex_counts && n) {  // the third vertices were counted by rank
+        k_vertex_finish<<<(unsigned)std::min<uint64_t>(((uint64_t)n + 255) / 256, (uint64_t)ctx->num_sms * 16), 256, 0,
+                          s>>>(n, b.lv, b.vcount_rank, b.vcount);
+        note_launch(ctx);
+        TC_CUDA(ctx, cudaGetLastError());
+    }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[3], s));
     st = pull(ctx);
     if (st != TC_OK) return st;

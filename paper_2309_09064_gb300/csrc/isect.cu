@@ -43,6 +43,22 @@ struct Acc {
     unsigned long long same = 0, cross = 0, probes = 0;
 };
 
+// Per-vertex triangle counts (tc_count_vertices): every triangle found adds
+// one to each of its three vertices -- the hashed vertex u and the probed
+// vertex v by id (tid), the third vertex w by rank (trank, the value found in
+// the probe range; mapped back to ids after the count).  Null otherwise.
+struct VertexOut {
+    unsigned long long *tid = nullptr;
+    unsigned long long *trank = nullptr;
+};
+
+template <int U>
+__device__ __forceinline__ void credit_third(const bool (&hit)[U], const uint32_t (&w)[U], const VertexOut &vo) {
+#pragma unroll
+    for (int i = 0; i < U; ++i)
+        if (hit[i]) atomicAdd(vo.trank + w[i], 1ull);
+}
+
 // ---------------------------------------------------------------------------- set representations
 
 // Bucketed open addressing: buckets of four 32-bit slots read with one 128-bit
@@ -230,40 +246,6 @@ __device__ __forceinline__ void lookup_batch(const HubSet &H, const uint32_t (&w
 
 // ---------------------------------------------------------------------------- probing
 
-// Hit counters of one probing call, 32-bit in registers, added to the 64-bit
-// accumulators once per call.  A hit in the A part of a probe range is a
-// triangle inside G0, a hit in the G1 part a cross-level triangle.
-struct Hits {
-    uint32_t all = 0, same = 0;
-    __device__ __forceinline__ void add(bool hit, bool in_a) {
-        all += hit;
-        same += hit && in_a;
-    }
-    __device__ __forceinline__ void flush(Acc &acc) const {
-        acc.same += same;
-        acc.cross += all - same;
-    }
-};
-
-template <class Set, int U>
-__device__ __forceinline__ void lookup_all(const Set &set, const uint32_t (&w)[U], const bool (&in_a)[U], Hits &hits) {
-    constexpr int B = Set::kBatch < U ? Set::kBatch : U;
-    static_assert(U % B == 0, "the unroll must be a multiple of the lookup batch");
-#pragma unroll
-    for (int half = 0; half < U; half += B) {
-        uint32_t ww[B];
-        bool hit[B];
-#pragma unroll
-        for (int i = 0; i < B; ++i) ww[i] = w[half + i];
-        lookup_batch(set, ww, hit);
-#pragma unroll
-        for (int i = 0; i < B; ++i) hits.add(hit[i], in_a[half + i]);
-    }
-}
-
-// Positions [j_lo, j_hi) of one probe range adj2[b ..] with one warp, lanes
-// striding over the positions with U loads in flight each; positions below
-// `split` are the A part.
 // Count the hits of one step of U x 32 positions starting at j0 into same /
 // cross: the split (end of the A part) is the same for the whole warp, and
 // most steps lie wholly on one side of it.
@@ -310,9 +292,10 @@ __device__ __forceinline__ void lookup_step(const Set &set, const uint32_t (&w)[
 // then the ragged end in one bounds-checked step of U x 32 positions, or in
 // steps of 64 positions (kFineTail: pays where lookups are expensive);
 // positions below `split` are the A part.
-template <int U, bool kFineTail = false, class Set>
-__device__ __forceinline__ void probe_row(const Set &set, const uint32_t *__restrict__ adj2, unsigned long long b,
-                                          uint32_t j_lo, uint32_t j_hi, uint32_t split, Acc &acc) {
+template <int U, bool kFineTail = false, bool kV = false, class Set>
+__device__ __forceinline__ uint32_t probe_row(const Set &set, const uint32_t *__restrict__ adj2, unsigned long long b,
+                                              uint32_t j_lo, uint32_t j_hi, uint32_t split, Acc &acc,
+                                              const VertexOut &vo = VertexOut{}) {
     const unsigned lane = lane_id();
     const uint32_t *row = adj2 + b + lane;
     uint32_t same = 0, cross = 0;
@@ -323,6 +306,7 @@ __device__ __forceinline__ void probe_row(const Set &set, const uint32_t *__rest
 #pragma unroll
         for (int i = 0; i < U; ++i) w[i] = __ldg(row + j0 + (uint32_t)i * 32u);
         lookup_step<U>(set, w, hit);
+        if constexpr (kV) credit_third<U>(hit, w, vo);
         count_step<U>(hit, j0, split, lane, same, cross);
     }
     constexpr int T = kFineTail ? 2 : U;
@@ -335,10 +319,12 @@ __device__ __forceinline__ void probe_row(const Set &set, const uint32_t *__rest
             w[i] = j + lane < j_hi ? __ldg(row + j) : Set::kPad;
         }
         lookup_step<T>(set, w, hit);
+        if constexpr (kV) credit_third<T>(hit, w, vo);
         count_step<T>(hit, j0, split, lane, same, cross);
     }
     acc.same += same;
     acc.cross += cross;
+    return same + cross;  // this lane's hits (the caller credits the probed vertex)
 }
 
 // Short probe ranges, concatenated: range r covers positions
@@ -347,11 +333,12 @@ __device__ __forceinline__ void probe_row(const Set &set, const uint32_t *__rest
 // One warp probes positions [q_lo, q_hi) (q_hi <= total) with every lane busy
 // however short the ranges are: each lane finds the range of its first
 // position by binary search and then walks forward.
-template <int U, class Set>
+template <int U, bool kV = false, class Set>
 __device__ __forceinline__ void probe_flat(const Set &set, const uint32_t *__restrict__ adj2,
                                            const unsigned long long *sb, const uint32_t *spre,
-                                           const uint32_t *ssplit, uint32_t nv, uint32_t q_lo, uint32_t q_hi,
-                                           Acc &acc, unsigned int *err) {
+                                           const uint32_t *ssplit, const uint32_t *sv, uint32_t nv, uint32_t q_lo,
+                                           uint32_t q_hi, Acc &acc, unsigned int *err,
+                                           const VertexOut &vo = VertexOut{}) {
     const unsigned lane = lane_id();
     const uint32_t q0 = min(q_lo + lane, q_hi - 1);
     uint32_t r = 0, e = nv;  // largest r < nv with pre[r] <= q0
@@ -362,10 +349,10 @@ __device__ __forceinline__ void probe_flat(const Set &set, const uint32_t *__res
     uint32_t lo = spre[r], hi = spre[r + 1];
     unsigned long long base = sb[r] - lo;
     uint32_t split = lo + ssplit[r];
-    Hits hits;
+    uint32_t same = 0, cross = 0;
     for (uint32_t j0 = q_lo; j0 < q_hi; j0 += 32u * U) {
-        uint32_t w[U];
-        bool in_a[U];
+        uint32_t w[U], vr[U];
+        bool in_a[U], hit[U];
 #pragma unroll
         for (int i = 0; i < U; ++i) {
             const uint32_t q = j0 + (uint32_t)i * 32u + lane;
@@ -386,10 +373,23 @@ __device__ __forceinline__ void probe_flat(const Set &set, const uint32_t *__res
             }
             w[i] = valid ? __ldg(adj2 + base + q) : Set::kPad;
             in_a[i] = q < split;
+            if constexpr (kV) vr[i] = sv[r];
         }
-        lookup_all(set, w, in_a, hits);
+        lookup_step<U>(set, w, hit);
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            same += hit[i] && in_a[i];
+            cross += hit[i] && !in_a[i];
+            if constexpr (kV) {
+                if (hit[i]) {
+                    atomicAdd(vo.trank + w[i], 1ull);
+                    atomicAdd(vo.tid + vr[i], 1ull);
+                }
+            }
+        }
     }
-    hits.flush(acc);
+    acc.same += same;
+    acc.cross += cross;
 }
 
 __device__ __forceinline__ uint32_t group_of(const GroupSpec &g, uint32_t u) {
@@ -513,6 +513,7 @@ struct WarpMeta {
     unsigned long long b[32];
     uint32_t pre[33];
     uint32_t split[32];
+    uint32_t v[32];  // probed vertex of each range (per-vertex counts only)
 };
 constexpr size_t kWarpMetaBytes = (sizeof(WarpMeta) + 15) & ~size_t(15);
 
@@ -522,7 +523,7 @@ __host__ __device__ constexpr size_t warp_set_bytes(bool cuckoo, uint32_t units)
     return cuckoo ? ((8ull * units + sizeof(CuckooShared) + 15) & ~15ull) : 16ull * units;
 }
 
-template <bool kCuckoo>
+template <bool kCuckoo, bool kV>
 __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__ tasks, const uint32_t *__restrict__ rows,
                                                      const uint32_t *__restrict__ ntask,
                                                      const uint64_t *__restrict__ rp,
@@ -531,7 +532,7 @@ __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__
                                                      const uint64_t *__restrict__ eoff,
                                                      const uint4 *__restrict__ erec, Ctl *ctl, uint32_t table_units,
                                                      uint32_t flat_cap, unsigned long long first,
-                                                     unsigned long long last, GroupSpec groups) {
+                                                     unsigned long long last, GroupSpec groups, VertexOut vo) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     const size_t set_bytes = warp_set_bytes(kCuckoo, table_units);
@@ -581,7 +582,11 @@ __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__
         for (uint32_t k0 = k_lo; k0 < k_hi; k0 += 32) {
             const uint32_t kk = k0 + lane;
             uint4 r = make_uint4(0, 0, 0, 0);
-            if (kk < k_hi) r = rec[kk];
+            uint32_t vid = 0;
+            if (kk < k_hi) {
+                r = rec[kk];
+                if constexpr (kV) vid = adj2[hb - fu + kk];
+            }
             acc.probes += r.z;
             const unsigned long long b = rec_start(r);
             // long ranges: the whole warp on each in turn
@@ -593,8 +598,14 @@ __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__
                 const unsigned long long bt = __shfl_sync(0xFFFFFFFFu, b, t);
                 const uint32_t lt = __shfl_sync(0xFFFFFFFFu, r.z, t);
                 const uint32_t ht = __shfl_sync(0xFFFFFFFFu, r.w, t);
-                if constexpr (kCuckoo) probe_row<CuckooTable::kUnroll>(C, adj2, bt, 0, lt, ht, acc);
-                else probe_row<BucketTable::kUnroll>(T, adj2, bt, 0, lt, ht, acc);
+                uint32_t got;
+                if constexpr (kCuckoo) got = probe_row<CuckooTable::kUnroll, false, kV>(C, adj2, bt, 0, lt, ht, acc, vo);
+                else got = probe_row<BucketTable::kUnroll, false, kV>(T, adj2, bt, 0, lt, ht, acc, vo);
+                if constexpr (kV) {
+                    got = warp_sum(got);
+                    const uint32_t vt = __shfl_sync(0xFFFFFFFFu, vid, t);
+                    if (lane == 0 && got) atomicAdd(vo.tid + vt, (unsigned long long)got);
+                }
             }
             // short ranges: concatenated
             const uint32_t sl = longr ? 0u : r.z;
@@ -609,20 +620,24 @@ __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__
                 meta->b[lane] = b;
                 meta->pre[lane] = incl - sl;
                 meta->split[lane] = r.w;
+                meta->v[lane] = vid;
                 if (lane == 31) meta->pre[32] = total;
                 __syncwarp();
                 if constexpr (kCuckoo)
-                    probe_flat<CuckooTable::kUnroll>(C, adj2, meta->b, meta->pre, meta->split, 32, 0, total, acc,
-                                                     &ctl->error);
+                    probe_flat<CuckooTable::kUnroll, kV>(C, adj2, meta->b, meta->pre, meta->split, meta->v, 32, 0,
+                                                         total, acc, &ctl->error, vo);
                 else
-                    probe_flat<BucketTable::kUnroll>(T, adj2, meta->b, meta->pre, meta->split, 32, 0, total, acc,
-                                                     &ctl->error);
+                    probe_flat<BucketTable::kUnroll, kV>(T, adj2, meta->b, meta->pre, meta->split, meta->v, 32, 0,
+                                                         total, acc, &ctl->error, vo);
                 __syncwarp();
             }
         }
-        if (groups.n_groups) {
+        if (groups.n_groups || kV) {
             const unsigned long long found = warp_sum(acc.same + acc.cross - before);
-            if (lane == 0 && found) atomicAdd(&groups.counts[group_of(groups, u)], found);
+            if (lane == 0 && found) {
+                if (groups.n_groups) atomicAdd(&groups.counts[group_of(groups, u)], found);
+                if constexpr (kV) atomicAdd(vo.tid + u, found);
+            }
         }
     }
     flush(acc, ctl, 0, lane == 0 ? build : 0, lane == 0 ? done : 0);
@@ -633,12 +648,16 @@ __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__
 
 // Size of the intersection of a[0..na) (shared, column `stride` apart) and
 // b[0..nb) (global), both descending: two-pointer merge.
+template <bool kV>
 __device__ __forceinline__ uint32_t merge_count_desc(const uint32_t *a, uint32_t stride, uint32_t na,
-                                                     const uint32_t *__restrict__ b, uint32_t nb) {
+                                                     const uint32_t *__restrict__ b, uint32_t nb,
+                                                     const VertexOut &vo) {
     uint32_t i = 0, j = 0, c = 0;
     while (i < na && j < nb) {
         const uint32_t x = a[i * stride], y = __ldg(b + j);
         c += x == y;
+        if constexpr (kV)
+            if (x == y) atomicAdd(vo.trank + y, 1ull);
         i += x >= y;
         j += y >= x;
     }
@@ -647,12 +666,17 @@ __device__ __forceinline__ uint32_t merge_count_desc(const uint32_t *a, uint32_t
 
 // Size of the intersection of a[0..na) (shared, column `stride` apart) and
 // b[0..nb) (global), in any order: every pair compared (na <= tiny_cap).
+template <bool kV>
 __device__ __forceinline__ uint32_t scan_count(const uint32_t *a, uint32_t stride, uint32_t na,
-                                               const uint32_t *__restrict__ b, uint32_t nb) {
+                                               const uint32_t *__restrict__ b, uint32_t nb, const VertexOut &vo) {
     uint32_t c = 0;
     for (uint32_t j = 0; j < nb; ++j) {
         const uint32_t y = __ldg(b + j);
-        for (uint32_t i = 0; i < na; ++i) c += a[i * stride] == y;
+        uint32_t cy = 0;
+        for (uint32_t i = 0; i < na; ++i) cy += a[i * stride] == y;
+        c += cy;
+        if constexpr (kV)
+            if (cy) atomicAdd(vo.trank + y, 1ull);
     }
     return c;
 }
@@ -663,12 +687,13 @@ __device__ __forceinline__ uint32_t scan_count(const uint32_t *a, uint32_t strid
 // for every v in F(u) the A parts (both descending) are merged -- only
 // elements ranked below u can match, since A(u) holds no other -- and the G1
 // parts compared pairwise.
+template <bool kV>
 __global__ void __launch_bounds__(256) k_isect_tiny(const uint32_t *__restrict__ rows, uint32_t lo, uint32_t hi,
                                                     const uint64_t *__restrict__ rp,
                                                     const uint32_t *__restrict__ adj2,
                                                     const uint32_t *__restrict__ fcnt,
                                                     const uint32_t *__restrict__ gcnt, Ctl *ctl, uint32_t tiny_cap,
-                                                    GroupSpec groups) {
+                                                    GroupSpec groups, VertexOut vo) {
     extern __shared__ uint32_t srow[];  // tiny_cap x blockDim, column per thread
     uint32_t *mine = srow + threadIdx.x;
     const uint32_t stride = blockDim.x;
@@ -688,8 +713,12 @@ __global__ void __launch_bounds__(256) k_isect_tiny(const uint32_t *__restrict__
             const uint64_t vb = rp[v], ve = rp[v + 1];
             const uint32_t fv = fcnt[v], gv = gcnt[v];
             const uint32_t av = (uint32_t)(ve - vb) - fv - gv;
-            same += merge_count_desc(mine, stride, au, adj2 + vb + fv, av);
-            cross += scan_count(mine + au * stride, stride, gu, adj2 + (ve - gv), gv);
+            const uint32_t sv = merge_count_desc<kV>(mine, stride, au, adj2 + vb + fv, av, vo);
+            const uint32_t cv = scan_count<kV>(mine + au * stride, stride, gu, adj2 + (ve - gv), gv, vo);
+            same += sv;
+            cross += cv;
+            if constexpr (kV)
+                if (sv + cv) atomicAdd(vo.tid + v, (unsigned long long)(sv + cv));
             probes += av + gv;
         }
         acc.same += same;
@@ -698,6 +727,8 @@ __global__ void __launch_bounds__(256) k_isect_tiny(const uint32_t *__restrict__
         build += su + fu;
         ++done;
         if (groups.n_groups && same + cross) atomicAdd(&groups.counts[group_of(groups, u)], (unsigned long long)(same + cross));
+        if constexpr (kV)
+            if (same + cross) atomicAdd(vo.tid + u, (unsigned long long)(same + cross));
     }
     const unsigned long long b = warp_sum(build), d = warp_sum(done);
     flush(acc, ctl, 3, lane_id() == 0 ? b : 0, lane_id() == 0 ? d : 0);
@@ -710,7 +741,7 @@ __global__ void __launch_bounds__(256) k_isect_tiny(const uint32_t *__restrict__
 // Warps take pieces one at a time, so no long range holds up the block.
 struct SliceSmem {
     unsigned long long *b;
-    uint32_t *len, *h, *seg;
+    uint32_t *len, *h, *seg, *v;  // v: probed vertex of each range (per-vertex counts only)
 };
 
 __device__ __forceinline__ SliceSmem carve_slice(unsigned char *p, uint32_t max_v) {
@@ -719,10 +750,11 @@ __device__ __forceinline__ SliceSmem carve_slice(unsigned char *p, uint32_t max_
     s.len = reinterpret_cast<uint32_t *>(p + 8ull * max_v);
     s.h = s.len + max_v;
     s.seg = s.h + max_v;
+    s.v = s.seg + max_v + 1;
     return s;
 }
 
-__host__ __device__ constexpr size_t slice_smem_bytes(uint32_t max_v) { return (20ull * max_v + 4 + 15) & ~15ull; }
+__host__ __device__ constexpr size_t slice_smem_bytes(uint32_t max_v) { return (24ull * max_v + 4 + 15) & ~15ull; }
 
 // Block-wide exclusive scan of the piece counts of ranges 0..nv-1 into
 // seg[0..nv]; all threads of the block call it; ends with a barrier.
@@ -763,14 +795,17 @@ __device__ __forceinline__ void scan_segments(const uint32_t *len, uint32_t *seg
     __syncthreads();
 }
 
-// Load the probe records of edges k in [k_lo, k_hi) of one row (no barrier).
+// Load the probe records of edges k in [k_lo, k_hi) of one row (no barrier),
+// and with per-vertex counts the probed vertices (F of the row, at frow).
+template <bool kV>
 __device__ __forceinline__ void load_slice(const SliceSmem &S, const uint4 *__restrict__ rec, uint32_t k_lo,
-                                           uint32_t k_hi) {
+                                           uint32_t k_hi, const uint32_t *__restrict__ frow) {
     for (uint32_t i = threadIdx.x; i < k_hi - k_lo; i += blockDim.x) {
         const uint4 r = rec[k_lo + i];
         S.b[i] = rec_start(r);
         S.len[i] = r.z;
         S.h[i] = r.w;
+        if constexpr (kV) S.v[i] = frow[k_lo + i];
     }
 }
 
@@ -778,9 +813,10 @@ __device__ __forceinline__ void load_slice(const SliceSmem &S, const uint4 *__re
 // lanes of a warp locate the pieces of a batch in parallel (one binary search
 // each over seg), then the warp walks them one by one.  The batch shrinks for
 // small slices so that every warp of the block still gets work.
-template <class Set>
+template <bool kV = false, class Set>
 __device__ __forceinline__ void probe_slice(const Set &set, const SliceSmem &S, uint32_t nv,
-                                            const uint32_t *__restrict__ adj2, unsigned int *next, Acc &acc) {
+                                            const uint32_t *__restrict__ adj2, unsigned int *next, Acc &acc,
+                                            const VertexOut &vo = VertexOut{}) {
     const unsigned lane = lane_id();
     const uint32_t total = S.seg[nv];
     const uint32_t nwarps = blockDim.x >> 5;
@@ -793,7 +829,7 @@ __device__ __forceinline__ void probe_slice(const Set &set, const SliceSmem &S, 
         if (g0 >= total) break;
         const uint32_t cnt = min(batch, total - g0);
         unsigned long long b = 0;
-        uint32_t j_lo = 0, j_hi = 0, h = 0;
+        uint32_t j_lo = 0, j_hi = 0, h = 0, vid = 0;
         if (lane < cnt) {
             const uint32_t g = g0 + lane;
             uint32_t a = 0, e = nv;  // range of piece g: largest t with seg[t] <= g
@@ -805,6 +841,7 @@ __device__ __forceinline__ void probe_slice(const Set &set, const SliceSmem &S, 
             j_hi = min(S.len[a], j_lo + kSeg);
             b = S.b[a];
             h = S.h[a];
+            if constexpr (kV) vid = S.v[a];
             acc.probes += j_hi - j_lo;
         }
         for (uint32_t t = 0; t < cnt; ++t) {
@@ -812,7 +849,12 @@ __device__ __forceinline__ void probe_slice(const Set &set, const SliceSmem &S, 
             const uint32_t lo = __shfl_sync(0xFFFFFFFFu, j_lo, t);
             const uint32_t hi = __shfl_sync(0xFFFFFFFFu, j_hi, t);
             const uint32_t ht = __shfl_sync(0xFFFFFFFFu, h, t);
-            probe_row<Set::kUnroll, Set::kFineTail>(set, adj2, bt, lo, hi, ht, acc);
+            uint32_t got = probe_row<Set::kUnroll, Set::kFineTail, kV>(set, adj2, bt, lo, hi, ht, acc, vo);
+            if constexpr (kV) {
+                got = warp_sum(got);
+                const uint32_t vt = __shfl_sync(0xFFFFFFFFu, vid, t);
+                if (lane == 0 && got) atomicAdd(vo.tid + vt, (unsigned long long)got);
+            }
         }
     }
 }
@@ -861,7 +903,7 @@ __device__ __forceinline__ void init_task_smem(TaskSmem *ts) {
 
 // Block class.  The hashed set lives in shared memory: a cuckoo table
 // (table_kind = 0) or the bucketed table (table_kind = 1).
-template <bool kCuckoo>
+template <bool kCuckoo, bool kV>
 __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict__ tasks, const uint32_t *__restrict__ rows,
                                                       const uint32_t *__restrict__ ntask,
                                                       const uint64_t *__restrict__ rp,
@@ -871,7 +913,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
                                                       const uint4 *__restrict__ erec, Ctl *ctl, uint32_t max_v,
                                                       uint32_t table_units, unsigned long long chunk,
                                                       unsigned long long first, unsigned long long last,
-                                                      GroupSpec groups) {
+                                                      GroupSpec groups, VertexOut vo) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TaskSmem ts;
     __shared__ CuckooShared cs;
@@ -895,7 +937,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
         const bool rebuild = task.x != cur_row;
         if constexpr (!kCuckoo)
             if (rebuild) T = clear_table(T.bk, su, table_units, threadIdx.x, blockDim.x, &ctl->error);
-        load_slice(S, erec + eoff[u], k_lo, k_hi);
+        load_slice<kV>(S, erec + eoff[u], k_lo, k_hi, adj2 + (hb - fu));
         __syncthreads();
         scan_segments(S.len, S.seg, k_hi - k_lo);
         if (rebuild) {
@@ -913,13 +955,16 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
             ++done;
         }
         const unsigned long long before = acc.same + acc.cross;
-        if constexpr (kCuckoo) probe_slice(C, S, k_hi - k_lo, adj2, &ts.next, acc);
-        else probe_slice(T, S, k_hi - k_lo, adj2, &ts.next, acc);
-        if (groups.n_groups) {
+        if constexpr (kCuckoo) probe_slice<kV>(C, S, k_hi - k_lo, adj2, &ts.next, acc, vo);
+        else probe_slice<kV>(T, S, k_hi - k_lo, adj2, &ts.next, acc, vo);
+        if (groups.n_groups || kV) {
             const unsigned long long found = warp_sum(acc.same + acc.cross - before);
             if (lane == 0 && found) atomicAdd(&ts.found, found);
             __syncthreads();
-            if (threadIdx.x == 0 && ts.found) atomicAdd(&groups.counts[group_of(groups, u)], ts.found);
+            if (threadIdx.x == 0 && ts.found) {
+                if (groups.n_groups) atomicAdd(&groups.counts[group_of(groups, u)], ts.found);
+                if constexpr (kV) atomicAdd(vo.tid + u, ts.found);
+            }
         }
     }
     flush(acc, ctl, 1, threadIdx.x == 0 ? build : 0, threadIdx.x == 0 ? done : 0);
@@ -945,6 +990,7 @@ __global__ void k_hub_set(const uint32_t *__restrict__ rows, uint32_t i0, uint32
 
 // Probe the tasks [first, last) of the hub rows with row index in
 // [i0, i0 + hub_group) against their bitmaps.
+template <bool kV>
 __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__ tasks, unsigned long long first,
                                                     unsigned long long last, const uint32_t *__restrict__ rows,
                                                     const uint32_t *__restrict__ ntask, uint32_t i0,
@@ -952,7 +998,8 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
                                                     const uint32_t *__restrict__ fcnt,
                                                     const uint64_t *__restrict__ eoff, const uint4 *__restrict__ erec,
                                                     Ctl *ctl, const uint32_t *bits, uint64_t words, uint32_t max_v,
-                                                    unsigned long long chunk, uint32_t filter_log2, GroupSpec groups) {
+                                                    unsigned long long chunk, uint32_t filter_log2, GroupSpec groups,
+                                                    VertexOut vo) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TaskSmem ts;
     const unsigned lane = lane_id();
@@ -975,7 +1022,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
         const bool rebuild = task.x != cur_row;
         if (rebuild)
             for (uint32_t j = threadIdx.x; j < filter_words; j += blockDim.x) filter[j] = 0u;
-        load_slice(S, erec + eoff[u], k_lo, k_hi);
+        load_slice<kV>(S, erec + eoff[u], k_lo, k_hi, adj2 + (hb - fu));
         __syncthreads();
         scan_segments(S.len, S.seg, k_hi - k_lo);
         if (rebuild) {
@@ -993,12 +1040,15 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
         }
         const HubSet H{filter, bits + (uint64_t)(task.x - i0) * words, fshift};
         const unsigned long long before = acc.same + acc.cross;
-        probe_slice(H, S, k_hi - k_lo, adj2, &ts.next, acc);
-        if (groups.n_groups) {
+        probe_slice<kV>(H, S, k_hi - k_lo, adj2, &ts.next, acc, vo);
+        if (groups.n_groups || kV) {
             const unsigned long long found = warp_sum(acc.same + acc.cross - before);
             if (lane == 0 && found) atomicAdd(&ts.found, found);
             __syncthreads();
-            if (threadIdx.x == 0 && ts.found) atomicAdd(&groups.counts[group_of(groups, u)], ts.found);
+            if (threadIdx.x == 0 && ts.found) {
+                if (groups.n_groups) atomicAdd(&groups.counts[group_of(groups, u)], ts.found);
+                if constexpr (kV) atomicAdd(vo.tid + u, ts.found);
+            }
         }
     }
     flush(acc, ctl, 2, threadIdx.x == 0 ? build : 0, threadIdx.x == 0 ? done : 0);
@@ -1035,6 +1085,8 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
     (void)n;
     cudaStream_t s = ctx->stream;
     const Tuning &tu = ctx->tune;
+    const VertexOut vo{b.vcount, b.vcount_rank};
+    const bool kv = b.vcount != nullptr;
     const Ctl &h = *ctx->h_ctl;  // pulled after planning
     // ev[4..7] bracket the warp, block and hub kernels
     // tiny rows: one thread each (this count's share of them)
@@ -1044,10 +1096,11 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
     const uint32_t hi3 = (uint32_t)((uint64_t)nt3 * (ctx->shard + 1) / ctx->nshards);
     if (hi3 > lo3) {
         const size_t smem = 4ull * tu.tiny_cap * 256;
-        TC_CUDA(ctx, cudaFuncSetAttribute(k_isect_tiny, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        auto tiny = kv ? k_isect_tiny<true> : k_isect_tiny<false>;
+        TC_CUDA(ctx, cudaFuncSetAttribute(tiny, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const uint32_t grid = std::min<uint32_t>((hi3 - lo3 + 255) / 256, (uint32_t)ctx->num_sms * 8u);
-        k_isect_tiny<<<grid, 256, smem, s>>>(b.rows[3], lo3, hi3, b.rp, b.adj2, b.fcnt, b.gcnt, ctx->d_ctl, tu.tiny_cap,
-                                             b.groups);
+        tiny<<<grid, 256, smem, s>>>(b.rows[3], lo3, hi3, b.rp, b.adj2, b.fcnt, b.gcnt, ctx->d_ctl, tu.tiny_cap,
+                                     b.groups, vo);
         note_launch(ctx);
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[9], s));
@@ -1063,7 +1116,8 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[4], s));
     if (hi0 > lo0) {
         const size_t smem = warp_kernel_smem(tu);
-        auto kern = tu.table_kind == 0 ? k_isect_warp<true> : k_isect_warp<false>;
+        auto kern = tu.table_kind == 0 ? (kv ? k_isect_warp<true, true> : k_isect_warp<true, false>)
+                                       : (kv ? k_isect_warp<false, true> : k_isect_warp<false, false>);
         TC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
         TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * tu.warps_per_block, smem));
@@ -1074,13 +1128,14 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         kern<<<(unsigned)grid, 32 * tu.warps_per_block, smem, s>>>(b.tasks[0], b.rows[0], b.ntask[0], b.rp, b.adj2,
                                                                    b.fcnt, b.eoff, b.erec, ctx->d_ctl,
                                                                    warp_table_units(tu), tu.flat_cap, lo0, hi0,
-                                                                   b.groups);
+                                                                   b.groups, vo);
         note_launch(ctx);
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[5], s));
     if (hi1 > lo1) {
         const size_t smem = block_kernel_smem(tu);
-        auto kern = tu.table_kind == 0 ? k_isect_block<true> : k_isect_block<false>;
+        auto kern = tu.table_kind == 0 ? (kv ? k_isect_block<true, true> : k_isect_block<true, false>)
+                                       : (kv ? k_isect_block<false, true> : k_isect_block<false, false>);
         TC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
         TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tu.block_threads, smem));
@@ -1090,7 +1145,7 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         const unsigned long long chunk = std::max<unsigned long long>(1, (hi1 - lo1) / (grid * 8));
         kern<<<(unsigned)grid, tu.block_threads, smem, s>>>(b.tasks[1], b.rows[1], b.ntask[1], b.rp, b.adj2, b.fcnt,
                                                             b.eoff, b.erec, ctx->d_ctl, tu.max_v, block_table_units(tu),
-                                                            chunk, lo1, hi1, b.groups);
+                                                            chunk, lo1, hi1, b.groups, vo);
         note_launch(ctx);
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[6], s));
@@ -1101,9 +1156,10 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         TC_CUDA(ctx, cudaMemcpyAsync(pref.data(), b.tpref[2], 8ull * (nh + 1), cudaMemcpyDeviceToHost, s));
         TC_CUDA(ctx, cudaStreamSynchronize(s));
         const size_t smem = hub_kernel_smem(tu);
-        TC_CUDA(ctx, cudaFuncSetAttribute(k_isect_hub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        auto hub = kv ? k_isect_hub<true> : k_isect_hub<false>;
+        TC_CUDA(ctx, cudaFuncSetAttribute(hub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
-        TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_isect_hub, tu.hub_threads, smem));
+        TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hub, tu.hub_threads, smem));
         if (per_sm < 1) per_sm = 1;
         for (uint32_t i0 = 0; i0 < nh; i0 += tu.hub_group) {
             const uint32_t g = std::min<uint32_t>(tu.hub_group, nh - i0);
@@ -1117,11 +1173,11 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
             uint64_t grid = (uint64_t)ctx->num_sms * per_sm;
             if (grid > last - first) grid = last - first;
             const unsigned long long chunk = std::max<unsigned long long>(1, (last - first) / (grid * 4));
-            k_isect_hub<<<(unsigned)grid, tu.hub_threads, smem, s>>>(b.tasks[2], first, last, b.rows[2], b.ntask[2], i0,
+            hub<<<(unsigned)grid, tu.hub_threads, smem, s>>>(b.tasks[2], first, last, b.rows[2], b.ntask[2], i0,
                                                                      b.rp, b.adj2, b.fcnt, b.eoff, b.erec, ctx->d_ctl,
                                                                      b.hub_bits,
                                                                      b.hub_words, tu.max_v, chunk, tu.hub_filter_log2,
-                                                                     b.groups);
+                                                                     b.groups, vo);
             note_launch(ctx, 2);
         }
     }

@@ -52,6 +52,10 @@ struct PipeBufs {
     uint64_t *scan_tmp = nullptr;
     // batched counting of a disjoint union
     GroupSpec groups;
+    // per-vertex triangle counts (tc_count_vertices): by id (the caller's
+    // array) and by rank (scratch); null otherwise
+    unsigned long long *vcount = nullptr;
+    unsigned long long *vcount_rank = nullptr;
 };
 
 tc_status compute_levels(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t slots);
