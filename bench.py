@@ -308,6 +308,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true", help="pick the intersection knobs by timing candidates first")
+    ap.add_argument("--vertex-counts", action="store_true",
+                    help="time tc_count_vertices (triangles through every vertex) instead of tc_count")
     ap.add_argument("--shard", action="store_true",
                     help="with N > 1: split one count across the ranks (strong scaling) instead of N replicas")
     args = ap.parse_args()
@@ -346,10 +348,14 @@ def main():
     if sharded:
         from paper_2309_09064_gb300 import shard as shard_mod
 
+    vcounts = torch.empty(max(n_, 1), dtype=torch.int64, device="cuda") if args.vertex_counts else None
+
     def one_count():
         if sharded:
             part, st = tc.tc_count_shard(ctx, g, rank, world)
             return shard_mod.sum_partials(part), st
+        if vcounts is not None:
+            return tc.tc_count_vertices(ctx, g, vcounts)
         return tc.tc_count(ctx, g)
 
     T0 = None
@@ -432,7 +438,9 @@ def main():
         "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": config_of(args.workload, w, n_, m, {"parallelism": (f"intersection tasks sharded x{world}"
                                                                       if sharded else f"replicas x{world}"),
-                                                      "tuning": tuned or tc.tc_get_tuning(ctx)}),
+                                                      "tuning": tuned or tc.tc_get_tuning(ctx),
+                                                      "output": ("per-vertex counts (tc_count_vertices)"
+                                                                 if args.vertex_counts else "T (tc_count)")}),
         "triangles": T0, "t_same": last["t_same"], "t_cross": last["t_cross"],
         "horizontal_edges": last["horizontal_edges"], "levels": last["levels"],
         "stage_ms": {"levels": mean("ms_levels"), "rows": mean("ms_mark"), "intersect": mean("ms_isect"),

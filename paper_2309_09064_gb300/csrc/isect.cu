@@ -50,13 +50,36 @@ struct Acc {
 struct VertexOut {
     unsigned long long *tid = nullptr;
     unsigned long long *trank = nullptr;
+    unsigned long long *priv = nullptr;  // shared: block-private counts of the ranks below kPrivRanks
 };
+
+// The highest-ranked vertices (the largest degrees) close the most
+// triangles; their counts are kept per block in shared memory and added to
+// trank once per block, so the global atomics on them do not serialise.
+constexpr uint32_t kPrivRanks = 1024;
+
+__device__ __forceinline__ void credit_rank(const VertexOut &vo, uint32_t w) {
+    if (w < kPrivRanks) atomicAdd(vo.priv + w, 1ull);
+    else atomicAdd(vo.trank + w, 1ull);
+}
 
 template <int U>
 __device__ __forceinline__ void credit_third(const bool (&hit)[U], const uint32_t (&w)[U], const VertexOut &vo) {
 #pragma unroll
     for (int i = 0; i < U; ++i)
-        if (hit[i]) atomicAdd(vo.trank + w[i], 1ull);
+        if (hit[i]) credit_rank(vo, w[i]);
+}
+
+// Zero the block-private counts (all threads; ends with a barrier) / add them
+// to the global ones (all threads; starts with a barrier).
+__device__ __forceinline__ void priv_begin(const VertexOut &vo) {
+    for (uint32_t i = threadIdx.x; i < kPrivRanks; i += blockDim.x) vo.priv[i] = 0;
+    __syncthreads();
+}
+__device__ __forceinline__ void priv_end(const VertexOut &vo) {
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < kPrivRanks; i += blockDim.x)
+        if (vo.priv[i]) atomicAdd(vo.trank + i, vo.priv[i]);
 }
 
 // ---------------------------------------------------------------------------- set representations
@@ -382,7 +405,7 @@ __device__ __forceinline__ void probe_flat(const Set &set, const uint32_t *__res
             cross += hit[i] && !in_a[i];
             if constexpr (kV) {
                 if (hit[i]) {
-                    atomicAdd(vo.trank + w[i], 1ull);
+                    credit_rank(vo, w[i]);
                     atomicAdd(vo.tid + vr[i], 1ull);
                 }
             }
@@ -544,6 +567,11 @@ __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__
     uint32_t cur_row = 0xFFFFFFFFu;
     BucketTable T{reinterpret_cast<uint4 *>(mine), 0, 0, &ctl->error};
     CuckooTable C{reinterpret_cast<uint32_t *>(mine), cs->stash, 64, 26, 0, 0, 0, 0, 0};
+    if constexpr (kV) {
+        vo.priv = reinterpret_cast<unsigned long long *>(smem_raw + (size_t)(blockDim.x >> 5) *
+                                                                         (set_bytes + kWarpMetaBytes));
+        priv_begin(vo);
+    }
     const long long t_start = clock64();
     for (;;) {
         unsigned long long k = 0;
@@ -642,6 +670,7 @@ __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__
     }
     flush(acc, ctl, 0, lane == 0 ? build : 0, lane == 0 ? done : 0);
     if (lane == 0 && inserts) atomicAdd(&ctl->cls_inserts[0], inserts);
+    if constexpr (kV) priv_end(vo);
 }
 
 // ---------------------------------------------------------------------------- tiny class
@@ -657,7 +686,7 @@ __device__ __forceinline__ uint32_t merge_count_desc(const uint32_t *a, uint32_t
         const uint32_t x = a[i * stride], y = __ldg(b + j);
         c += x == y;
         if constexpr (kV)
-            if (x == y) atomicAdd(vo.trank + y, 1ull);
+            if (x == y) credit_rank(vo, y);
         i += x >= y;
         j += y >= x;
     }
@@ -676,7 +705,7 @@ __device__ __forceinline__ uint32_t scan_count(const uint32_t *a, uint32_t strid
         for (uint32_t i = 0; i < na; ++i) cy += a[i * stride] == y;
         c += cy;
         if constexpr (kV)
-            if (cy) atomicAdd(vo.trank + y, 1ull);
+            if (cy) credit_rank(vo, y);
     }
     return c;
 }
@@ -697,6 +726,10 @@ __global__ void __launch_bounds__(256) k_isect_tiny(const uint32_t *__restrict__
     extern __shared__ uint32_t srow[];  // tiny_cap x blockDim, column per thread
     uint32_t *mine = srow + threadIdx.x;
     const uint32_t stride = blockDim.x;
+    if constexpr (kV) {
+        vo.priv = reinterpret_cast<unsigned long long *>(srow + (size_t)tiny_cap * blockDim.x);
+        priv_begin(vo);
+    }
     Acc acc;
     unsigned long long build = 0, done = 0;
     const uint32_t total = (uint32_t)((uint64_t)gridDim.x * blockDim.x);
@@ -732,6 +765,7 @@ __global__ void __launch_bounds__(256) k_isect_tiny(const uint32_t *__restrict__
     }
     const unsigned long long b = warp_sum(build), d = warp_sum(done);
     flush(acc, ctl, 3, lane_id() == 0 ? b : 0, lane_id() == 0 ? d : 0);
+    if constexpr (kV) priv_end(vo);
 }
 
 // ---------------------------------------------------------------------------- block and hub classes
@@ -925,6 +959,10 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
     uint32_t cur_row = 0xFFFFFFFFu;
     CuckooTable C{reinterpret_cast<uint32_t *>(tab), cs.stash, 64, 26, 0, 0, 0, 0, 0};
     BucketTable T{reinterpret_cast<uint4 *>(tab), 0, 0, &ctl->error};
+    if constexpr (kV) {
+        vo.priv = reinterpret_cast<unsigned long long *>(tab + (kCuckoo ? 8ull : 16ull) * table_units);
+        priv_begin(vo);
+    }
     init_task_smem(&ts);
     const long long t_start = clock64();
     while (next_task(ctl, 1, first, last, chunk, tasks, &ts, t_start)) {
@@ -969,6 +1007,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
     }
     flush(acc, ctl, 1, threadIdx.x == 0 ? build : 0, threadIdx.x == 0 ? done : 0);
     if (threadIdx.x == 0 && inserts) atomicAdd(&ctl->cls_inserts[1], inserts);
+    if constexpr (kV) priv_end(vo);
 }
 
 // Set the bits of the hashed sets of hub rows rows[i0 .. i0+g) into bitmaps
@@ -1007,6 +1046,10 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
     uint32_t *filter = reinterpret_cast<uint32_t *>(smem_raw + slice_smem_bytes(max_v));
     const uint32_t filter_words = 1u << (filter_log2 - 5);
     const uint32_t fshift = 32u - filter_log2;
+    if constexpr (kV) {
+        vo.priv = reinterpret_cast<unsigned long long *>(filter + filter_words);
+        priv_begin(vo);
+    }
     Acc acc;
     unsigned long long build = 0, done = 0, inserts = 0;
     uint32_t cur_row = 0xFFFFFFFFu;
@@ -1053,6 +1096,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
     }
     flush(acc, ctl, 2, threadIdx.x == 0 ? build : 0, threadIdx.x == 0 ? done : 0);
     if (threadIdx.x == 0 && inserts) atomicAdd(&ctl->cls_inserts[2], inserts);
+    if constexpr (kV) priv_end(vo);
 }
 
 uint32_t pow2_at_least(uint64_t x, uint32_t lo) {
@@ -1095,7 +1139,7 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
     const uint32_t lo3 = (uint32_t)((uint64_t)nt3 * ctx->shard / ctx->nshards);
     const uint32_t hi3 = (uint32_t)((uint64_t)nt3 * (ctx->shard + 1) / ctx->nshards);
     if (hi3 > lo3) {
-        const size_t smem = 4ull * tu.tiny_cap * 256;
+        const size_t smem = 4ull * tu.tiny_cap * 256 + (kv ? 8ull * kPrivRanks : 0);
         auto tiny = kv ? k_isect_tiny<true> : k_isect_tiny<false>;
         TC_CUDA(ctx, cudaFuncSetAttribute(tiny, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const uint32_t grid = std::min<uint32_t>((hi3 - lo3 + 255) / 256, (uint32_t)ctx->num_sms * 8u);
@@ -1115,7 +1159,7 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
     share(h.n_tasks[2], &lo2, &hi2);
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[4], s));
     if (hi0 > lo0) {
-        const size_t smem = warp_kernel_smem(tu);
+        const size_t smem = warp_kernel_smem(tu) + (kv ? 8ull * kPrivRanks : 0);
         auto kern = tu.table_kind == 0 ? (kv ? k_isect_warp<true, true> : k_isect_warp<true, false>)
                                        : (kv ? k_isect_warp<false, true> : k_isect_warp<false, false>);
         TC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1133,7 +1177,7 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[5], s));
     if (hi1 > lo1) {
-        const size_t smem = block_kernel_smem(tu);
+        const size_t smem = block_kernel_smem(tu) + (kv ? 8ull * kPrivRanks : 0);
         auto kern = tu.table_kind == 0 ? (kv ? k_isect_block<true, true> : k_isect_block<true, false>)
                                        : (kv ? k_isect_block<false, true> : k_isect_block<false, false>);
         TC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1155,7 +1199,7 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         std::vector<unsigned long long> pref(nh + 1);
         TC_CUDA(ctx, cudaMemcpyAsync(pref.data(), b.tpref[2], 8ull * (nh + 1), cudaMemcpyDeviceToHost, s));
         TC_CUDA(ctx, cudaStreamSynchronize(s));
-        const size_t smem = hub_kernel_smem(tu);
+        const size_t smem = hub_kernel_smem(tu) + (kv ? 8ull * kPrivRanks : 0);
         auto hub = kv ? k_isect_hub<true> : k_isect_hub<false>;
         TC_CUDA(ctx, cudaFuncSetAttribute(hub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
