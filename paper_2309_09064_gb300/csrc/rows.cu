@@ -366,7 +366,7 @@ __global__ void k_chunk_rows(uint32_t n, const uint64_t *__restrict__ eoff, uint
 // from the chunk's first row to the rows of its own edges, and runs the
 // binary searches of kRecBatch edges in lockstep (independent loads in
 // flight).  Block 0 also publishes |E0| = eoff[n].
-constexpr int kRecBatch = 4;
+constexpr int kRecBatch = 2;
 
 __global__ void k_records(uint32_t n, const uint64_t *__restrict__ eoff, const uint32_t *__restrict__ chunk_row,
                           const uint64_t *__restrict__ rp, const uint32_t *__restrict__ adj2,
