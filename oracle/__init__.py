@@ -66,6 +66,8 @@ def _load():
             lib.oracle_vertex_counts.restype = ctypes.c_uint64
             lib.oracle_alg4.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int, _u32p, _u64p]
             lib.oracle_alg4.restype = ctypes.c_int
+            lib.oracle_list_definition.argtypes = [ctypes.c_uint32, _u64p, _u32p, _u32p, ctypes.c_uint64]
+            lib.oracle_list_definition.restype = ctypes.c_uint64
             lib.oracle_alg3.argtypes = [ctypes.c_uint32, _u64p, _u32p, ctypes.c_int]
             lib.oracle_alg3.restype = ctypes.c_uint64
             _lib = lib
@@ -107,6 +109,16 @@ def vertex_counts(row_ptr, col):
     tv = np.zeros(max(n, 1), dtype=np.uint64)
     T = int(_load().oracle_vertex_counts(n, rp, c, tv))
     return T, tv[:n]
+
+
+def list_definition(row_ptr, col):
+    """Every triangle once: uint32 array (T, 3) of id triples a < b < c, rows in lexicographic order."""
+    n, rp, c = _csr_args(row_ptr, col)
+    lib = _load()
+    T = int(lib.oracle_list_definition(n, rp, c, np.zeros(3, np.uint32), 0))
+    out = np.zeros(3 * max(T, 1), dtype=np.uint32)
+    lib.oracle_list_definition(n, rp, c, out, T)
+    return out[:3 * T].reshape(T, 3)
 
 
 def alg4(row_ptr, col, degree_order: bool = True) -> dict:

@@ -25,16 +25,17 @@
  *   oracle_alg3             Algorithm 3 (cover-edge triangle counting) with
  *                           its level rule, as an independent cross-check.
  *   oracle_vertex_counts    per-vertex triangle counts from the definition.
+ *   oracle_list_definition  every triangle once, from the definition.
  *
  * Readings of points the paper leaves open (the same readings bind the CUDA
  * library):
- *   - "Relabel by decreasing degree": ties broken by ascending original id.
- *     "u < v" inside Algorithms 2-4 compares the new labels.
- *   - BFS roots: the loop "for all v, if v unvisited, BFS(G, v)" visits
+ *   - Relabelling by decreasing degree: ties broken by ascending original id.
+ *     The comparisons u < v inside Algorithms 2-4 compare the new labels.
+ *   - BFS roots: the outer loop, a BFS from every vertex still unvisited, visits
  *     vertices in label order, so each component's root is its first vertex
  *     in that order (highest degree, then lowest id, in the degree order).
  *   - The Hash[] array is indexed by vertex id, so it has n entries (the text
- *     says "size m", which cannot index vertices).
+ *     sizes it by m, which cannot index vertices).
  *   - Isolated vertices are their own BFS roots, at level 0.
  */
 #include <stdint.h>
@@ -215,10 +216,45 @@ uint64_t oracle_vertex_counts(uint32_t n, const uint64_t *rp, const uint32_t *co
     return T;
 }
 
+/*
+ * Every triangle once, from the definition: the triples a < b < c (vertex
+ * ids) of pairwise adjacent vertices, in lexicographic order -- for every a,
+ * every neighbour b > a, and every common neighbour c > b of a and b (sorted
+ * rows, one merge).  Writes the first min(T, cap) triples to out (3 ids
+ * each) and returns T.
+ */
+uint64_t oracle_list_definition(uint32_t n, const uint64_t *rp, const uint32_t *col, uint32_t *out, uint64_t cap)
+{
+    uint64_t T = 0;
+    for (uint32_t a = 0; a < n; ++a)
+        for (uint64_t j = rp[a]; j < rp[a + 1]; ++j) {
+            uint32_t b = col[j];
+            if (b <= a) continue;
+            uint64_t i1 = rp[a], e1 = rp[a + 1], i2 = rp[b], e2 = rp[b + 1];
+            while (i1 < e1 && i2 < e2) {
+                if (col[i1] < col[i2]) ++i1;
+                else if (col[i1] > col[i2]) ++i2;
+                else {
+                    uint32_t c = col[i1];
+                    if (c > b) {
+                        if (T < cap) {
+                            out[3 * T] = a;
+                            out[3 * T + 1] = b;
+                            out[3 * T + 2] = c;
+                        }
+                        ++T;
+                    }
+                    ++i1; ++i2;
+                }
+            }
+        }
+    return T;
+}
+
 /* ------------------------------------------------------------------- BFS levels */
 
 /*
- * "For all v in V: if v unvisited, BFS(G, v)" (Algorithms 3 and 4), with
+ * A BFS from every vertex still unvisited (Algorithms 3 and 4), with
  * vertices taken in label order 0..n-1 of the (relabelled) CSR.  L[p] = hop
  * distance from the root of p's component.  Returns the number of levels
  * (max L + 1), 0 for an empty graph.

@@ -122,6 +122,32 @@ def test_vertex_counts_match_brute_force():
     assert np.array_equal(got.astype(np.int64), tv)
 
 
+@pytest.mark.parametrize("seed,n,p", [(8, 25, 0.35), (9, 40, 0.2), (10, 12, 1.0), (11, 6, 0.0)])
+def test_triangle_list_matches_brute_force(seed, n, p):
+    """The listing is exactly the set of adjacent triples, each once, in lexicographic order."""
+    rp, col = csr_of(gg.gnp(n, p, seed))
+    A = dense(rp, col)
+    got = oracle.list_definition(rp, col)
+    assert got.shape == (len(brute_triangle_list(A)), 3)
+    assert [tuple(int(x) for x in r) for r in got] == brute_triangle_list(A)
+
+
+@pytest.mark.parametrize("n", [0, 3, 7, 12])
+def test_triangle_list_complete_graph(n):
+    rp, col = csr_of(gg.complete(n))
+    got = oracle.list_definition(rp, col)
+    assert [tuple(int(x) for x in r) for r in got] == list(itertools.combinations(range(n), 3))
+
+
+def test_triangle_list_agrees_with_the_counts_on_rmat():
+    rp, col = csr_of(gg.rmat(10, 16, seed=1))
+    got = oracle.list_definition(rp, col)
+    T, tv = oracle.vertex_counts(rp, col)
+    assert len(got) == T == oracle.count_definition(rp, col)
+    assert np.array_equal(np.bincount(got.ravel(), minlength=len(rp) - 1).astype(np.uint64), tv)
+    assert np.all((got[:, 0] < got[:, 1]) & (got[:, 1] < got[:, 2]))
+
+
 @pytest.mark.parametrize("graph", ["rmat10", "rmat9_ef32", "er2048"])
 def test_trace_a_cubed(graph):
     if graph == "rmat10":
