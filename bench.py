@@ -310,6 +310,8 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="pick the intersection knobs by timing candidates first")
     ap.add_argument("--vertex-counts", action="store_true",
                     help="time tc_count_vertices (triangles through every vertex) instead of tc_count")
+    ap.add_argument("--list-triangles", action="store_true",
+                    help="time tc_list_triangles (every triangle written out as three vertex ids) instead of tc_count")
     ap.add_argument("--shard", action="store_true",
                     help="with N > 1: split one count across the ranks (strong scaling) instead of N replicas")
     args = ap.parse_args()
@@ -349,6 +351,10 @@ def main():
         from paper_2309_09064_gb300 import shard as shard_mod
 
     vcounts = torch.empty(max(n_, 1), dtype=torch.int64, device="cuda") if args.vertex_counts else None
+    triples, list_cap = None, 0
+    if args.list_triangles:  # output sized by a count first: 12 bytes per triangle
+        list_cap, _ = tc.tc_count(ctx, g)
+        triples = torch.empty(3 * max(list_cap, 1), dtype=torch.int32, device="cuda")
 
     def one_count():
         if sharded:
@@ -356,6 +362,8 @@ def main():
             return shard_mod.sum_partials(part), st
         if vcounts is not None:
             return tc.tc_count_vertices(ctx, g, vcounts)
+        if triples is not None:
+            return tc.tc_list_triangles(ctx, g, triples, list_cap)
         return tc.tc_count(ctx, g)
 
     T0 = None
@@ -440,7 +448,11 @@ def main():
                                                                       if sharded else f"replicas x{world}"),
                                                       "tuning": tuned or tc.tc_get_tuning(ctx),
                                                       "output": ("per-vertex counts (tc_count_vertices)"
-                                                                 if args.vertex_counts else "T (tc_count)")}),
+                                                                 if args.vertex_counts else
+                                                                 "triangle list, 12 B per triangle "
+                                                                 "(tc_list_triangles; class times are the "
+                                                                 "listing pass)"
+                                                                 if args.list_triangles else "T (tc_count)")}),
         "triangles": T0, "t_same": last["t_same"], "t_cross": last["t_cross"],
         "horizontal_edges": last["horizontal_edges"], "levels": last["levels"],
         "stage_ms": {"levels": mean("ms_levels"), "rows": mean("ms_mark"), "intersect": mean("ms_isect"),

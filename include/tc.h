@@ -48,7 +48,8 @@ typedef enum tc_status {
     TC_ERR_CUDA = 3,      /* a CUDA runtime call failed */
     TC_ERR_TIMEOUT = 4,   /* a bounded device wait gave up */
     TC_ERR_BUSY = 5,      /* request queue full */
-    TC_NOT_READY = 6      /* tc_poll: result not ready yet */
+    TC_NOT_READY = 6,     /* tc_poll: result not ready yet */
+    TC_ERR_CAPACITY = 7   /* tc_list_triangles: more triangles than the output holds */
 } tc_status;
 
 typedef struct tc_ctx tc_ctx;
@@ -230,8 +231,8 @@ tc_status tc_count_vertices(tc_ctx *ctx, const tc_graph *g, uint64_t *d_counts, 
                             tc_stats *stats);
 
 /*
- * Count with levels the caller already has (the paper's case "when the
- * results of a BFS are already available", Sec. III): d_levels is a device
+ * Count with levels the caller already has (Sec. III: the method pays most
+ * where a BFS has been run anyway): d_levels is a device
  * uint32_t[n], read only, e.g. the hop distances of any BFS forest.  The BFS
  * of Algorithm 4 is skipped; everything else is as in tc_count.  The count is
  * exact for any labelling in which the two ends of every edge differ by at
@@ -241,6 +242,23 @@ tc_status tc_count_vertices(tc_ctx *ctx, const tc_graph *g, uint64_t *d_counts, 
  */
 tc_status tc_count_with_levels(tc_ctx *ctx, const tc_graph *g, const uint32_t *d_levels, uint64_t *triangles,
                                tc_stats *stats);
+
+/*
+ * List every triangle of g exactly once.  Algorithm 4 finds each triangle
+ * once (one or three horizontal edges; Sec. III), so its hits are the list:
+ * d_triples (device uint32_t[3 * capacity], nullable when capacity is 0)
+ * gets T rows {u, v, w} of vertex ids -- u the vertex whose set was hashed,
+ * v the probed one (u -> v a horizontal edge, u earlier in the working
+ * order), w the third vertex -- in no particular order; *triangles gets T.
+ * Two passes of the intersections: the first counts the triangles of every
+ * task, an exclusive scan turns those counts into output offsets, the second
+ * writes each task's triangles at its offset (rows d_triples[3T ..] are left
+ * untouched).  If T > capacity nothing is written and the call returns
+ * TC_ERR_CAPACITY with *triangles = T, so that the caller can size the
+ * output and call again.  stats as in tc_count (of the counting pass).
+ */
+tc_status tc_list_triangles(tc_ctx *ctx, const tc_graph *g, uint32_t *d_triples, uint64_t capacity,
+                            uint64_t *triangles, tc_stats *stats);
 
 /*
  * One shard of a count split across nshards processes or devices (the

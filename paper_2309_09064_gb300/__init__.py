@@ -21,26 +21,27 @@ __all__ = [
     "TC_ORDER_DEGREE", "TC_ORDER_ID", "tc_create", "tc_destroy", "tc_last_error", "tc_set_stream",
     "tc_arena_bytes", "tc_build_csr", "tc_graph_from_csr", "tc_graph_info", "tc_graph_copy_out",
     "tc_validate", "tc_graph_free", "tc_count", "tc_count_levels", "tc_count_with_levels", "tc_count_vertices",
-    "tc_count_batch",
+    "tc_list_triangles", "tc_count_batch",
     "tc_submit", "tc_poll",
     "tc_get_tuning", "tc_set_tuning", "tc_count_noalloc", "tc_poll_ex", "tc_count_shard", "tc_selftest_barrier",
     "library_path",
     "EXPORTED",
 ]
 
-TC_OK, TC_ERR_INVALID, TC_ERR_OOM, TC_ERR_CUDA, TC_ERR_TIMEOUT, TC_ERR_BUSY, TC_NOT_READY = range(7)
+TC_OK, TC_ERR_INVALID, TC_ERR_OOM, TC_ERR_CUDA, TC_ERR_TIMEOUT, TC_ERR_BUSY, TC_NOT_READY, TC_ERR_CAPACITY = range(8)
 TC_HOST, TC_DEVICE = 0, 1
 TC_COPY, TC_BORROW, TC_VALIDATE = 0, 1, 2
 TC_ORDER_DEGREE, TC_ORDER_ID = 0, 1
 _STATUS = {0: "TC_OK", 1: "TC_ERR_INVALID", 2: "TC_ERR_OOM", 3: "TC_ERR_CUDA", 4: "TC_ERR_TIMEOUT",
-           5: "TC_ERR_BUSY", 6: "TC_NOT_READY"}
+           5: "TC_ERR_BUSY", 6: "TC_NOT_READY", 7: "TC_ERR_CAPACITY"}
 
 # every entry point tc.h declares
 EXPORTED = ["tc_create", "tc_destroy", "tc_last_error", "tc_set_stream", "tc_get_tuning", "tc_set_tuning",
             "tc_selftest_barrier",
             "tc_arena_bytes", "tc_build_csr",
             "tc_graph_from_csr", "tc_graph_info", "tc_graph_copy_out", "tc_validate", "tc_graph_free",
-            "tc_count", "tc_count_levels", "tc_count_with_levels", "tc_count_vertices", "tc_count_shard",
+            "tc_count", "tc_count_levels", "tc_count_with_levels", "tc_count_vertices", "tc_list_triangles",
+            "tc_count_shard",
             "tc_count_batch", "tc_submit",
             "tc_poll", "tc_poll_ex",
             "tc_count_noalloc"]
@@ -113,6 +114,7 @@ def _load():
         "tc_count_levels": ([V, V, V, P(U64), P(tc_stats)], I),
         "tc_count_with_levels": ([V, V, V, P(U64), P(tc_stats)], I),
         "tc_count_vertices": ([V, V, V, P(U64), P(tc_stats)], I),
+        "tc_list_triangles": ([V, V, V, U64, P(U64), P(tc_stats)], I),
         "tc_count_shard": ([V, V, U32, U32, P(U64), P(tc_stats)], I),
         "tc_count_batch": ([V, U32, P(V), P(U64)], I),
         "tc_submit": ([V, V, P(U64)], I),
@@ -310,6 +312,26 @@ def tc_count_vertices(ctx, g, counts):
     T = ctypes.c_uint64()
     st = tc_stats()
     _check(ctx, _lib.tc_count_vertices(ctx, g, p, ctypes.byref(T), ctypes.byref(st)))
+    return T.value, st.to_dict()
+
+
+def tc_list_triangles(ctx, g, triples, capacity: int):
+    """Every triangle once into `triples` (a CUDA tensor of 3 * capacity 4-byte ints, or a device address;
+    None with capacity 0): returns (T, stats).  More than `capacity` triangles raise TcError with status
+    TC_ERR_CAPACITY and the count in its `triangles` attribute."""
+    p, where = _ptr(triples)
+    if p is not None and where != TC_DEVICE:
+        raise ValueError("triples must be a device buffer")
+    if hasattr(triples, "numel") and triples.numel() * triples.element_size() < 12 * capacity:
+        raise ValueError("triples holds fewer than 3 * capacity 4-byte ints")
+    T = ctypes.c_uint64()
+    st = tc_stats()
+    status = _lib.tc_list_triangles(ctx, g, p, capacity, ctypes.byref(T), ctypes.byref(st))
+    if status == TC_ERR_CAPACITY:
+        e = TcError(status, _lib.tc_last_error(ctx).decode())
+        e.triangles = T.value
+        raise e
+    _check(ctx, status)
     return T.value, st.to_dict()
 
 

@@ -384,6 +384,26 @@ tc_status tc_count_vertices(tc_ctx *ctx, const tc_graph *g, uint64_t *d_counts, 
     return count_pipeline(ctx, v, nullptr, none, triangles, stats, nullptr, d_counts);
 }
 
+tc_status tc_list_triangles(tc_ctx *ctx, const tc_graph *g, uint32_t *d_triples, uint64_t capacity,
+                            uint64_t *triangles, tc_stats *stats) {
+    if (!ctx || !g || (capacity && !d_triples) || capacity > (UINT64_MAX / 12))
+        return set_error(ctx, TC_ERR_INVALID, "bad argument");
+    if (g->ctx != ctx && g->ctx->device != ctx->device)
+        return set_error(ctx, TC_ERR_INVALID, "graph lives on another device");
+    DeviceGuard guard(ctx->device);
+    GraphView v;
+    v.n = g->n;
+    v.slots = g->slots;
+    v.rp = g->rp;
+    v.col = g->col;
+    v.max_deg = g->max_deg;
+    GroupSpec none;
+    ListSpec list;
+    list.out = d_triples;
+    list.capacity = capacity;
+    return count_pipeline(ctx, v, nullptr, none, triangles, stats, nullptr, nullptr, &list);
+}
+
 tc_status tc_count(tc_ctx *ctx, const tc_graph *g, uint64_t *triangles, tc_stats *stats) {
     return tc_count_levels(ctx, g, nullptr, triangles, stats);
 }

@@ -60,14 +60,24 @@ size_t pipeline_bytes(const tc_ctx *ctx, uint32_t n, uint64_t slots, uint32_t ma
     return bytes + 4096;
 }
 
+// Listing scratch: one hit record per task and per tiny row (tasks never
+// outnumber the oriented horizontal edges plus one, tiny rows the vertices)
+// and the scan's tile sums; rank -> id.
+uint64_t list_records(uint32_t n, uint64_t slots) { return slots / 2 + (uint64_t)n + 3; }
+size_t list_bytes(uint32_t n, uint64_t slots) {
+    const uint64_t H = list_records(n, slots);
+    return 8 * H + 8 * scan_tmp_elems(H) + 4ull * ((size_t)n + 1) + 3 * 256;
+}
+
 tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, const GroupSpec &groups,
-                         uint64_t *triangles, tc_stats *stats, const uint32_t *levels_in, uint64_t *vertex_counts) {
+                         uint64_t *triangles, tc_stats *stats, const uint32_t *levels_in, uint64_t *vertex_counts,
+                         const ListSpec *list) {
     const uint32_t n = g.n;
     cudaStream_t s = ctx->stream;
     uint64_t hub_words = 0;
     uint32_t hub_maps = 0;
     const size_t need = pipeline_bytes(ctx, n, g.slots, g.max_deg, levels_out == nullptr, &hub_words, &hub_maps) +
-                        (vertex_counts ? 8ull * ((size_t)n + 1) + 256 : 0);
+                        (vertex_counts ? 8ull * ((size_t)n + 1) + 256 : 0) + (list ? list_bytes(n, g.slots) : 0);
     tc_status st = arena_reserve(ctx, need);
     if (st != TC_OK) return st;
     Arena &a = ctx->arena;
@@ -127,6 +137,15 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
             TC_CUDA(ctx, cudaMemsetAsync(b.vcount_rank, 0, 8ull * n, s));
         }
     }
+    uint64_t *list_tmp = nullptr;
+    if (list) {
+        b.hits = a.take<unsigned long long>(list_records(n, g.slots));
+        list_tmp = a.take<uint64_t>(scan_tmp_elems(list_records(n, g.slots)));
+        if (ctx->opt.order == TC_ORDER_DEGREE && g.max_deg > 0) b.inv = a.take<uint32_t>(n1);
+        if (!b.hits || !list_tmp || (ctx->opt.order == TC_ORDER_DEGREE && g.max_deg > 0 && !b.inv))
+            return set_error(ctx, TC_ERR_OOM, "arena carve failed");
+        TC_CUDA(ctx, cudaMemsetAsync(b.hits, 0, 8 * list_records(n, g.slots), s));
+    }
     ok = ok && b.fpref && b.eoff && b.lv && b.rkeys0 && b.rkeys1 && b.rcounts && b.roffs && b.adj2 && b.erec &&
          b.scan_tmp && b.task_pool && (!hub_maps || b.hub_bits);
     if (!ok) return set_error(ctx, TC_ERR_OOM, "arena carve failed");
@@ -154,6 +173,36 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
     st = intersect(ctx, b, n);
     if (st != TC_OK) return st;
+    Ctl counted{};
+    if (list) {
+        // The counting pass recorded the triangles of every task; their
+        // exclusive prefix is where each task writes in the listing pass.
+        st = pull(ctx);
+        if (st != TC_OK) return st;
+        counted = *ctx->h_ctl;
+        const uint64_t T = counted.t_same + counted.t_cross;
+        if (triangles) *triangles = T;
+        if (counted.error) {
+            char msg[96];
+            std::snprintf(msg, sizeof msg, "device-side check failed during the count (code 0x%x)", counted.error);
+            return set_error(ctx, TC_ERR_INVALID, msg);
+        }
+        const uint64_t H = (uint64_t)counted.n_rows[3] + counted.n_tasks[0] + counted.n_tasks[1] + counted.n_tasks[2];
+        if (H + 1 > list_records(n, g.slots)) return set_error(ctx, TC_ERR_INVALID, "listing: more tasks than records");
+        note_launch(ctx, scan_u64(reinterpret_cast<uint64_t *>(b.hits), reinterpret_cast<uint64_t *>(b.hits), H,
+                                  list_tmp, s));
+        unsigned long long listed = 0;
+        TC_CUDA(ctx, cudaMemcpyAsync(&listed, b.hits + H, 8, cudaMemcpyDeviceToHost, s));
+        TC_CUDA(ctx, cudaStreamSynchronize(s));
+        if (listed != T) return set_error(ctx, TC_ERR_INVALID, "listing: task records disagree with the count");
+        if (T > list->capacity) return set_error(ctx, TC_ERR_CAPACITY, "listing: more triangles than capacity");
+        if (T) {
+            b.list_out = list->out;
+            TC_CUDA(ctx, cudaMemsetAsync(ctx->d_ctl->task_next, 0, sizeof(ctx->d_ctl->task_next), s));
+            st = intersect(ctx, b, n);
+            if (st != TC_OK) return st;
+        }
+    }
     if (vertex_counts && n) {  // the third vertices were counted by rank
         k_vertex_finish<<<(unsigned)std::min<uint64_t>(((uint64_t)n + 255) / 256, (uint64_t)ctx->num_sms * 16), 256, 0,
                           s>>>(n, b.lv, b.vcount_rank, b.vcount);
@@ -163,6 +212,16 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[3], s));
     st = pull(ctx);
     if (st != TC_OK) return st;
+    if (list) {
+        // the listing pass found every triangle again: its counters doubled
+        const Ctl &h2 = *ctx->h_ctl;
+        if (!h2.error && b.list_out &&
+            (h2.t_same != 2 * counted.t_same || h2.t_cross != 2 * counted.t_cross))
+            return set_error(ctx, TC_ERR_INVALID, "listing pass disagrees with the count");
+        const unsigned err = h2.error;
+        *ctx->h_ctl = counted;  // statistics of the counting pass
+        ctx->h_ctl->error = err;
+    }
     const Ctl &h = *ctx->h_ctl;
     if (h.error) {
         char msg[96];

@@ -43,15 +43,95 @@ struct Acc {
     unsigned long long same = 0, cross = 0, probes = 0;
 };
 
-// Per-vertex triangle counts (tc_count_vertices): every triangle found adds
-// one to each of its three vertices -- the hashed vertex u and the probed
-// vertex v by id (tid), the third vertex w by rank (trank, the value found in
-// the probe range; mapped back to ids after the count).  Null otherwise.
+// What the kernels do with the triangles they find, besides counting them
+// (template parameter kM of the kernels):
+//   kM = 1, per-vertex counts (tc_count_vertices): every triangle adds one to
+//     each of its three vertices -- the hashed vertex u and the probed vertex
+//     v by id (tid), the third vertex w by rank (trank, the value found in the
+//     probe range; mapped back to ids after the count);
+//   kM = 2, listing (tc_list_triangles, second pass): every triangle is
+//     written as (u, v, w) in vertex ids at the offset of its task (the
+//     counting pass recorded every task's hits in task_hits, a scan turned
+//     them into off), positions within a task handed out per warp step.
 struct VertexOut {
     unsigned long long *tid = nullptr;
     unsigned long long *trank = nullptr;
-    unsigned long long *priv = nullptr;  // shared: block-private counts of the ranks below kPrivRanks
+    unsigned long long *priv = nullptr;        // shared: block-private counts of the ranks below kPrivRanks
+    uint32_t *out = nullptr;                   // listing: triples
+    const uint32_t *inv = nullptr;             // listing: rank -> id (null: ranks are ids)
+    const unsigned long long *off = nullptr;   // listing: output offset of every task of the class
+    unsigned long long *task_hits = nullptr;   // counting pass of a listing: hits of every task of the class
 };
+
+constexpr unsigned kGuardList = 0x400u;  // a task found more triangles than the counting pass gave it room for
+
+// Listing position of one task: its output slots [base, end) (the counting
+// pass's hits of the task), the vertices of the current probe range, and the
+// cursor -- a warp-owned counter, or a shared one when several warps work on
+// the task.
+struct ListCtx {
+    unsigned long long base = 0, end = 0;
+    uint32_t u = 0, v = 0;
+    unsigned int local = 0;
+    unsigned int *shared = nullptr;
+    unsigned int *err = nullptr;
+};
+
+// One triangle (u, v, third vertex by rank w) at the thread's own cursor
+// (one thread per task: the tiny class).
+__device__ __forceinline__ void emit_one(const VertexOut &vo, ListCtx &lc, uint32_t w) {
+    const unsigned long long o = lc.base + lc.local++;
+    if (o >= lc.end) {
+        atomicOr(lc.err, kGuardList);
+        return;
+    }
+    uint32_t *t = vo.out + 3 * o;
+    t[0] = lc.u;
+    t[1] = lc.v;
+    t[2] = vo.inv ? vo.inv[w] : w;
+}
+
+// Write the hits of one warp step: a warp-wide prefix of the per-lane hit
+// counts gives every lane its first slot; vr[i] is the probed vertex of
+// element i (per element on the concatenated path).
+template <int U>
+__device__ __forceinline__ void emit_step(const bool (&hit)[U], const uint32_t (&w)[U], const uint32_t (&vr)[U],
+                                          const VertexOut &vo, ListCtx &lc) {
+    const unsigned lane = lane_id();
+    uint32_t c = 0;
+#pragma unroll
+    for (int i = 0; i < U; ++i) c += hit[i];
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= (unsigned)o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    if (total == 0) return;
+    uint32_t first = 0;
+    if (lc.shared) {
+        if (lane == 0) first = atomicAdd(lc.shared, total);
+        first = __shfl_sync(0xFFFFFFFFu, first, 0);
+    } else {
+        first = lc.local;
+        lc.local += total;
+    }
+    if (lc.base + first + total > lc.end) {  // never with a matching counting pass
+        if (lane == 0) atomicOr(lc.err, kGuardList);
+        return;
+    }
+    unsigned long long o = lc.base + first + (incl - c);
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+        if (hit[i]) {
+            uint32_t *t = vo.out + 3 * o++;
+            t[0] = lc.u;
+            t[1] = vr[i];
+            t[2] = vo.inv ? vo.inv[w[i]] : w[i];
+        }
+    }
+}
 
 // The highest-ranked vertices (the largest degrees) close the most
 // triangles; their counts are kept per block in shared memory and added to
@@ -315,10 +395,10 @@ __device__ __forceinline__ void lookup_step(const Set &set, const uint32_t (&w)[
 // then the ragged end in one bounds-checked step of U x 32 positions, or in
 // steps of 64 positions (kFineTail: pays where lookups are expensive);
 // positions below `split` are the A part.
-template <int U, bool kFineTail = false, bool kV = false, class Set>
+template <int U, bool kFineTail = false, int kM = 0, class Set>
 __device__ __forceinline__ uint32_t probe_row(const Set &set, const uint32_t *__restrict__ adj2, unsigned long long b,
                                               uint32_t j_lo, uint32_t j_hi, uint32_t split, Acc &acc,
-                                              const VertexOut &vo = VertexOut{}) {
+                                              const VertexOut &vo = VertexOut{}, ListCtx *lc = nullptr) {
     const unsigned lane = lane_id();
     const uint32_t *row = adj2 + b + lane;
     uint32_t same = 0, cross = 0;
@@ -329,7 +409,13 @@ __device__ __forceinline__ uint32_t probe_row(const Set &set, const uint32_t *__
 #pragma unroll
         for (int i = 0; i < U; ++i) w[i] = __ldg(row + j0 + (uint32_t)i * 32u);
         lookup_step<U>(set, w, hit);
-        if constexpr (kV) credit_third<U>(hit, w, vo);
+        if constexpr (kM == 1) credit_third<U>(hit, w, vo);
+        if constexpr (kM == 2) {
+            uint32_t vr[U];
+#pragma unroll
+            for (int i = 0; i < U; ++i) vr[i] = lc->v;
+            emit_step<U>(hit, w, vr, vo, *lc);
+        }
         count_step<U>(hit, j0, split, lane, same, cross);
     }
     constexpr int T = kFineTail ? 2 : U;
@@ -342,7 +428,13 @@ __device__ __forceinline__ uint32_t probe_row(const Set &set, const uint32_t *__
             w[i] = j + lane < j_hi ? __ldg(row + j) : Set::kPad;
         }
         lookup_step<T>(set, w, hit);
-        if constexpr (kV) credit_third<T>(hit, w, vo);
+        if constexpr (kM == 1) credit_third<T>(hit, w, vo);
+        if constexpr (kM == 2) {
+            uint32_t vr[T];
+#pragma unroll
+            for (int i = 0; i < T; ++i) vr[i] = lc->v;
+            emit_step<T>(hit, w, vr, vo, *lc);
+        }
         count_step<T>(hit, j0, split, lane, same, cross);
     }
     acc.same += same;
@@ -356,12 +448,12 @@ __device__ __forceinline__ uint32_t probe_row(const Set &set, const uint32_t *__
 // One warp probes positions [q_lo, q_hi) (q_hi <= total) with every lane busy
 // however short the ranges are: each lane finds the range of its first
 // position by binary search and then walks forward.
-template <int U, bool kV = false, class Set>
+template <int U, int kM = 0, class Set>
 __device__ __forceinline__ void probe_flat(const Set &set, const uint32_t *__restrict__ adj2,
                                            const unsigned long long *sb, const uint32_t *spre,
                                            const uint32_t *ssplit, const uint32_t *sv, uint32_t nv, uint32_t q_lo,
                                            uint32_t q_hi, Acc &acc, unsigned int *err,
-                                           const VertexOut &vo = VertexOut{}) {
+                                           const VertexOut &vo = VertexOut{}, ListCtx *lc = nullptr) {
     const unsigned lane = lane_id();
     const uint32_t q0 = min(q_lo + lane, q_hi - 1);
     uint32_t r = 0, e = nv;  // largest r < nv with pre[r] <= q0
@@ -396,14 +488,15 @@ __device__ __forceinline__ void probe_flat(const Set &set, const uint32_t *__res
             }
             w[i] = valid ? __ldg(adj2 + base + q) : Set::kPad;
             in_a[i] = q < split;
-            if constexpr (kV) vr[i] = sv[r];
+            if constexpr (kM != 0) vr[i] = sv[r];
         }
         lookup_step<U>(set, w, hit);
+        if constexpr (kM == 2) emit_step<U>(hit, w, vr, vo, *lc);
 #pragma unroll
         for (int i = 0; i < U; ++i) {
             same += hit[i] && in_a[i];
             cross += hit[i] && !in_a[i];
-            if constexpr (kV) {
+            if constexpr (kM == 1) {
                 if (hit[i]) {
                     credit_rank(vo, w[i]);
                     atomicAdd(vo.tid + vr[i], 1ull);
@@ -546,7 +639,7 @@ __host__ __device__ constexpr size_t warp_set_bytes(bool cuckoo, uint32_t units)
     return cuckoo ? ((8ull * units + sizeof(CuckooShared) + 15) & ~15ull) : 16ull * units;
 }
 
-template <bool kCuckoo, bool kV>
+template <bool kCuckoo, int kM>
 __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__ tasks, const uint32_t *__restrict__ rows,
                                                      const uint32_t *__restrict__ ntask,
                                                      const uint64_t *__restrict__ rp,
@@ -567,7 +660,7 @@ __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__
     uint32_t cur_row = 0xFFFFFFFFu;
     BucketTable T{reinterpret_cast<uint4 *>(mine), 0, 0, &ctl->error};
     CuckooTable C{reinterpret_cast<uint32_t *>(mine), cs->stash, 64, 26, 0, 0, 0, 0, 0};
-    if constexpr (kV) {
+    if constexpr (kM == 1) {
         vo.priv = reinterpret_cast<unsigned long long *>(smem_raw + (size_t)(blockDim.x >> 5) *
                                                                          (set_bytes + kWarpMetaBytes));
         priv_begin(vo);
@@ -591,6 +684,13 @@ __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__
         const uint32_t su = (uint32_t)(rp[u + 1] - hb);
         const uint4 *rec = erec + eoff[u];
         const uint32_t k_lo = (uint32_t)((uint64_t)task.y * fu / nt), k_hi = (uint32_t)((uint64_t)(task.y + 1) * fu / nt);
+        ListCtx lc;
+        if constexpr (kM == 2) {
+            lc.base = vo.off[k];
+            lc.end = vo.off[k + 1];
+            lc.u = u;
+            lc.err = &ctl->error;
+        }
         if (task.x != cur_row) {  // tasks of one row reuse its table
             __syncwarp();
             if constexpr (kCuckoo) {
@@ -613,7 +713,7 @@ __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__
             uint32_t vid = 0;
             if (kk < k_hi) {
                 r = rec[kk];
-                if constexpr (kV) vid = adj2[hb - fu + kk];
+                if constexpr (kM != 0) vid = adj2[hb - fu + kk];
             }
             acc.probes += r.z;
             const unsigned long long b = rec_start(r);
@@ -627,9 +727,12 @@ __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__
                 const uint32_t lt = __shfl_sync(0xFFFFFFFFu, r.z, t);
                 const uint32_t ht = __shfl_sync(0xFFFFFFFFu, r.w, t);
                 uint32_t got;
-                if constexpr (kCuckoo) got = probe_row<CuckooTable::kUnroll, false, kV>(C, adj2, bt, 0, lt, ht, acc, vo);
-                else got = probe_row<BucketTable::kUnroll, false, kV>(T, adj2, bt, 0, lt, ht, acc, vo);
-                if constexpr (kV) {
+                if constexpr (kM == 2) lc.v = __shfl_sync(0xFFFFFFFFu, vid, t);
+                if constexpr (kCuckoo)
+                    got = probe_row<CuckooTable::kUnroll, false, kM>(C, adj2, bt, 0, lt, ht, acc, vo, &lc);
+                else
+                    got = probe_row<BucketTable::kUnroll, false, kM>(T, adj2, bt, 0, lt, ht, acc, vo, &lc);
+                if constexpr (kM == 1) {
                     got = warp_sum(got);
                     const uint32_t vt = __shfl_sync(0xFFFFFFFFu, vid, t);
                     if (lane == 0 && got) atomicAdd(vo.tid + vt, (unsigned long long)got);
@@ -652,41 +755,47 @@ __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__
                 if (lane == 31) meta->pre[32] = total;
                 __syncwarp();
                 if constexpr (kCuckoo)
-                    probe_flat<CuckooTable::kUnroll, kV>(C, adj2, meta->b, meta->pre, meta->split, meta->v, 32, 0,
-                                                         total, acc, &ctl->error, vo);
+                    probe_flat<CuckooTable::kUnroll, kM>(C, adj2, meta->b, meta->pre, meta->split, meta->v, 32, 0,
+                                                         total, acc, &ctl->error, vo, &lc);
                 else
-                    probe_flat<BucketTable::kUnroll, kV>(T, adj2, meta->b, meta->pre, meta->split, meta->v, 32, 0,
-                                                         total, acc, &ctl->error, vo);
+                    probe_flat<BucketTable::kUnroll, kM>(T, adj2, meta->b, meta->pre, meta->split, meta->v, 32, 0,
+                                                         total, acc, &ctl->error, vo, &lc);
                 __syncwarp();
             }
         }
-        if (groups.n_groups || kV) {
+        if (groups.n_groups || kM == 1 || vo.task_hits) {
             const unsigned long long found = warp_sum(acc.same + acc.cross - before);
-            if (lane == 0 && found) {
-                if (groups.n_groups) atomicAdd(&groups.counts[group_of(groups, u)], found);
-                if constexpr (kV) atomicAdd(vo.tid + u, found);
+            if (lane == 0) {
+                if (vo.task_hits) vo.task_hits[k] = found;
+                if (groups.n_groups && found) atomicAdd(&groups.counts[group_of(groups, u)], found);
+                if constexpr (kM == 1)
+                    if (found) atomicAdd(vo.tid + u, found);
             }
         }
+        if constexpr (kM == 2)
+            if (lane == 0 && lc.base + lc.local != lc.end) atomicOr(&ctl->error, kGuardList);
     }
     flush(acc, ctl, 0, lane == 0 ? build : 0, lane == 0 ? done : 0);
     if (lane == 0 && inserts) atomicAdd(&ctl->cls_inserts[0], inserts);
-    if constexpr (kV) priv_end(vo);
+    if constexpr (kM == 1) priv_end(vo);
 }
 
 // ---------------------------------------------------------------------------- tiny class
 
 // Size of the intersection of a[0..na) (shared, column `stride` apart) and
 // b[0..nb) (global), both descending: two-pointer merge.
-template <bool kV>
+template <int kM>
 __device__ __forceinline__ uint32_t merge_count_desc(const uint32_t *a, uint32_t stride, uint32_t na,
                                                      const uint32_t *__restrict__ b, uint32_t nb,
-                                                     const VertexOut &vo) {
+                                                     const VertexOut &vo, ListCtx &lc) {
     uint32_t i = 0, j = 0, c = 0;
     while (i < na && j < nb) {
         const uint32_t x = a[i * stride], y = __ldg(b + j);
         c += x == y;
-        if constexpr (kV)
+        if constexpr (kM == 1)
             if (x == y) credit_rank(vo, y);
+        if constexpr (kM == 2)
+            if (x == y) emit_one(vo, lc, y);
         i += x >= y;
         j += y >= x;
     }
@@ -695,17 +804,20 @@ __device__ __forceinline__ uint32_t merge_count_desc(const uint32_t *a, uint32_t
 
 // Size of the intersection of a[0..na) (shared, column `stride` apart) and
 // b[0..nb) (global), in any order: every pair compared (na <= tiny_cap).
-template <bool kV>
+template <int kM>
 __device__ __forceinline__ uint32_t scan_count(const uint32_t *a, uint32_t stride, uint32_t na,
-                                               const uint32_t *__restrict__ b, uint32_t nb, const VertexOut &vo) {
+                                               const uint32_t *__restrict__ b, uint32_t nb, const VertexOut &vo,
+                                               ListCtx &lc) {
     uint32_t c = 0;
     for (uint32_t j = 0; j < nb; ++j) {
         const uint32_t y = __ldg(b + j);
         uint32_t cy = 0;
         for (uint32_t i = 0; i < na; ++i) cy += a[i * stride] == y;
         c += cy;
-        if constexpr (kV)
+        if constexpr (kM == 1)
             if (cy) credit_rank(vo, y);
+        if constexpr (kM == 2)
+            if (cy) emit_one(vo, lc, y);
     }
     return c;
 }
@@ -716,7 +828,7 @@ __device__ __forceinline__ uint32_t scan_count(const uint32_t *a, uint32_t strid
 // for every v in F(u) the A parts (both descending) are merged -- only
 // elements ranked below u can match, since A(u) holds no other -- and the G1
 // parts compared pairwise.
-template <bool kV>
+template <int kM>
 __global__ void __launch_bounds__(256) k_isect_tiny(const uint32_t *__restrict__ rows, uint32_t lo, uint32_t hi,
                                                     const uint64_t *__restrict__ rp,
                                                     const uint32_t *__restrict__ adj2,
@@ -726,7 +838,7 @@ __global__ void __launch_bounds__(256) k_isect_tiny(const uint32_t *__restrict__
     extern __shared__ uint32_t srow[];  // tiny_cap x blockDim, column per thread
     uint32_t *mine = srow + threadIdx.x;
     const uint32_t stride = blockDim.x;
-    if constexpr (kV) {
+    if constexpr (kM == 1) {
         vo.priv = reinterpret_cast<unsigned long long *>(srow + (size_t)tiny_cap * blockDim.x);
         priv_begin(vo);
     }
@@ -741,16 +853,24 @@ __global__ void __launch_bounds__(256) k_isect_tiny(const uint32_t *__restrict__
         for (uint32_t k = 0; k < su; ++k) mine[k * stride] = __ldg(adj2 + ub + fu + k);  // A(u) then G1(u)
         uint32_t same = 0, cross = 0;
         unsigned long long probes = 0;
+        ListCtx lc;
+        if constexpr (kM == 2) {
+            lc.base = vo.off[i];
+            lc.end = vo.off[i + 1];
+            lc.u = u;
+            lc.err = &ctl->error;
+        }
         for (uint32_t k = 0; k < fu; ++k) {
             const uint32_t v = __ldg(adj2 + ub + k);
+            lc.v = v;
             const uint64_t vb = rp[v], ve = rp[v + 1];
             const uint32_t fv = fcnt[v], gv = gcnt[v];
             const uint32_t av = (uint32_t)(ve - vb) - fv - gv;
-            const uint32_t sv = merge_count_desc<kV>(mine, stride, au, adj2 + vb + fv, av, vo);
-            const uint32_t cv = scan_count<kV>(mine + au * stride, stride, gu, adj2 + (ve - gv), gv, vo);
+            const uint32_t sv = merge_count_desc<kM>(mine, stride, au, adj2 + vb + fv, av, vo, lc);
+            const uint32_t cv = scan_count<kM>(mine + au * stride, stride, gu, adj2 + (ve - gv), gv, vo, lc);
             same += sv;
             cross += cv;
-            if constexpr (kV)
+            if constexpr (kM == 1)
                 if (sv + cv) atomicAdd(vo.tid + v, (unsigned long long)(sv + cv));
             probes += av + gv;
         }
@@ -760,12 +880,15 @@ __global__ void __launch_bounds__(256) k_isect_tiny(const uint32_t *__restrict__
         build += su + fu;
         ++done;
         if (groups.n_groups && same + cross) atomicAdd(&groups.counts[group_of(groups, u)], (unsigned long long)(same + cross));
-        if constexpr (kV)
+        if constexpr (kM == 1)
             if (same + cross) atomicAdd(vo.tid + u, (unsigned long long)(same + cross));
+        if (vo.task_hits) vo.task_hits[i] = same + cross;
+        if constexpr (kM == 2)
+            if (lc.base + lc.local != lc.end) atomicOr(&ctl->error, kGuardList);
     }
     const unsigned long long b = warp_sum(build), d = warp_sum(done);
     flush(acc, ctl, 3, lane_id() == 0 ? b : 0, lane_id() == 0 ? d : 0);
-    if constexpr (kV) priv_end(vo);
+    if constexpr (kM == 1) priv_end(vo);
 }
 
 // ---------------------------------------------------------------------------- block and hub classes
@@ -775,7 +898,7 @@ __global__ void __launch_bounds__(256) k_isect_tiny(const uint32_t *__restrict__
 // Warps take pieces one at a time, so no long range holds up the block.
 struct SliceSmem {
     unsigned long long *b;
-    uint32_t *len, *h, *seg, *v;  // v: probed vertex of each range (per-vertex counts only)
+    uint32_t *len, *h, *seg, *v;  // v: probed vertex of each range (per-vertex counts and listing only)
 };
 
 __device__ __forceinline__ SliceSmem carve_slice(unsigned char *p, uint32_t max_v) {
@@ -830,8 +953,9 @@ __device__ __forceinline__ void scan_segments(const uint32_t *len, uint32_t *seg
 }
 
 // Load the probe records of edges k in [k_lo, k_hi) of one row (no barrier),
-// and with per-vertex counts the probed vertices (F of the row, at frow).
-template <bool kV>
+// and with per-vertex counts or listing the probed vertices (F of the row, at
+// frow).
+template <int kM>
 __device__ __forceinline__ void load_slice(const SliceSmem &S, const uint4 *__restrict__ rec, uint32_t k_lo,
                                            uint32_t k_hi, const uint32_t *__restrict__ frow) {
     for (uint32_t i = threadIdx.x; i < k_hi - k_lo; i += blockDim.x) {
@@ -839,7 +963,7 @@ __device__ __forceinline__ void load_slice(const SliceSmem &S, const uint4 *__re
         S.b[i] = rec_start(r);
         S.len[i] = r.z;
         S.h[i] = r.w;
-        if constexpr (kV) S.v[i] = frow[k_lo + i];
+        if constexpr (kM != 0) S.v[i] = frow[k_lo + i];
     }
 }
 
@@ -847,10 +971,10 @@ __device__ __forceinline__ void load_slice(const SliceSmem &S, const uint4 *__re
 // lanes of a warp locate the pieces of a batch in parallel (one binary search
 // each over seg), then the warp walks them one by one.  The batch shrinks for
 // small slices so that every warp of the block still gets work.
-template <bool kV = false, class Set>
+template <int kM = 0, class Set>
 __device__ __forceinline__ void probe_slice(const Set &set, const SliceSmem &S, uint32_t nv,
                                             const uint32_t *__restrict__ adj2, unsigned int *next, Acc &acc,
-                                            const VertexOut &vo = VertexOut{}) {
+                                            const VertexOut &vo, ListCtx &lc) {
     const unsigned lane = lane_id();
     const uint32_t total = S.seg[nv];
     const uint32_t nwarps = blockDim.x >> 5;
@@ -875,7 +999,7 @@ __device__ __forceinline__ void probe_slice(const Set &set, const SliceSmem &S, 
             j_hi = min(S.len[a], j_lo + kSeg);
             b = S.b[a];
             h = S.h[a];
-            if constexpr (kV) vid = S.v[a];
+            if constexpr (kM != 0) vid = S.v[a];
             acc.probes += j_hi - j_lo;
         }
         for (uint32_t t = 0; t < cnt; ++t) {
@@ -883,8 +1007,9 @@ __device__ __forceinline__ void probe_slice(const Set &set, const SliceSmem &S, 
             const uint32_t lo = __shfl_sync(0xFFFFFFFFu, j_lo, t);
             const uint32_t hi = __shfl_sync(0xFFFFFFFFu, j_hi, t);
             const uint32_t ht = __shfl_sync(0xFFFFFFFFu, h, t);
-            uint32_t got = probe_row<Set::kUnroll, Set::kFineTail, kV>(set, adj2, bt, lo, hi, ht, acc, vo);
-            if constexpr (kV) {
+            if constexpr (kM == 2) lc.v = __shfl_sync(0xFFFFFFFFu, vid, t);
+            uint32_t got = probe_row<Set::kUnroll, Set::kFineTail, kM>(set, adj2, bt, lo, hi, ht, acc, vo, &lc);
+            if constexpr (kM == 1) {
                 got = warp_sum(got);
                 const uint32_t vt = __shfl_sync(0xFFFFFFFFu, vid, t);
                 if (lane == 0 && got) atomicAdd(vo.tid + vt, (unsigned long long)got);
@@ -896,8 +1021,9 @@ __device__ __forceinline__ void probe_slice(const Set &set, const SliceSmem &S, 
 struct TaskSmem {
     uint2 task;
     unsigned int next;
-    unsigned int pad;
+    unsigned int cursor;  // listing: triangles of the task written so far
     unsigned long long found;
+    unsigned long long k;                     // index of the task in its class's list
     unsigned long long chunk_pos, chunk_end;  // this block's current run of consecutive tasks
 };
 
@@ -920,12 +1046,52 @@ __device__ __forceinline__ bool next_task(Ctl *ctl, int c, unsigned long long fi
             }
             const unsigned long long k = ts->chunk_pos++;
             ts->task = k < ts->chunk_end ? tasks[k] : make_uint2(0xFFFFFFFFu, 0u);
+            ts->k = k;
         }
         ts->next = 0;
+        ts->cursor = 0;
         ts->found = 0;
     }
     __syncthreads();
     return ts->task.x != 0xFFFFFFFFu;
+}
+
+// Listing position of the current task of a block (cursor shared by its warps).
+template <int kM>
+__device__ __forceinline__ ListCtx list_ctx(const VertexOut &vo, TaskSmem &ts, uint32_t u, Ctl *ctl) {
+    ListCtx lc;
+    if constexpr (kM == 2) {
+        lc.base = vo.off[ts.k];
+        lc.end = vo.off[ts.k + 1];
+        lc.u = u;
+        lc.shared = &ts.cursor;
+        lc.err = &ctl->error;
+    }
+    return lc;
+}
+
+// End of a block's task: the triangles it found (this thread's share is
+// `mine`) go to the group counts, the hashed vertex's count, the task's hit
+// record; a listing task checks that it filled its slots exactly.
+template <int kM>
+__device__ __forceinline__ void finish_task(unsigned long long mine, const GroupSpec &groups, const VertexOut &vo,
+                                            TaskSmem &ts, uint32_t u, Ctl *ctl) {
+    if (groups.n_groups || kM == 1 || vo.task_hits) {
+        const unsigned long long found = warp_sum(mine);
+        if (lane_id() == 0 && found) atomicAdd(&ts.found, found);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (vo.task_hits) vo.task_hits[ts.k] = ts.found;
+            if (ts.found) {
+                if (groups.n_groups) atomicAdd(&groups.counts[group_of(groups, u)], ts.found);
+                if constexpr (kM == 1) atomicAdd(vo.tid + u, ts.found);
+            }
+        }
+    }
+    if constexpr (kM == 2) {
+        __syncthreads();
+        if (threadIdx.x == 0 && vo.off[ts.k] + ts.cursor != vo.off[ts.k + 1]) atomicOr(&ctl->error, kGuardList);
+    }
 }
 
 __device__ __forceinline__ void init_task_smem(TaskSmem *ts) {
@@ -937,7 +1103,7 @@ __device__ __forceinline__ void init_task_smem(TaskSmem *ts) {
 
 // Block class.  The hashed set lives in shared memory: a cuckoo table
 // (table_kind = 0) or the bucketed table (table_kind = 1).
-template <bool kCuckoo, bool kV>
+template <bool kCuckoo, int kM>
 __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict__ tasks, const uint32_t *__restrict__ rows,
                                                       const uint32_t *__restrict__ ntask,
                                                       const uint64_t *__restrict__ rp,
@@ -959,7 +1125,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
     uint32_t cur_row = 0xFFFFFFFFu;
     CuckooTable C{reinterpret_cast<uint32_t *>(tab), cs.stash, 64, 26, 0, 0, 0, 0, 0};
     BucketTable T{reinterpret_cast<uint4 *>(tab), 0, 0, &ctl->error};
-    if constexpr (kV) {
+    if constexpr (kM == 1) {
         vo.priv = reinterpret_cast<unsigned long long *>(tab + (kCuckoo ? 8ull : 16ull) * table_units);
         priv_begin(vo);
     }
@@ -975,7 +1141,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
         const bool rebuild = task.x != cur_row;
         if constexpr (!kCuckoo)
             if (rebuild) T = clear_table(T.bk, su, table_units, threadIdx.x, blockDim.x, &ctl->error);
-        load_slice<kV>(S, erec + eoff[u], k_lo, k_hi, adj2 + (hb - fu));
+        load_slice<kM>(S, erec + eoff[u], k_lo, k_hi, adj2 + (hb - fu));
         __syncthreads();
         scan_segments(S.len, S.seg, k_hi - k_lo);
         if (rebuild) {
@@ -993,21 +1159,14 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
             ++done;
         }
         const unsigned long long before = acc.same + acc.cross;
-        if constexpr (kCuckoo) probe_slice<kV>(C, S, k_hi - k_lo, adj2, &ts.next, acc, vo);
-        else probe_slice<kV>(T, S, k_hi - k_lo, adj2, &ts.next, acc, vo);
-        if (groups.n_groups || kV) {
-            const unsigned long long found = warp_sum(acc.same + acc.cross - before);
-            if (lane == 0 && found) atomicAdd(&ts.found, found);
-            __syncthreads();
-            if (threadIdx.x == 0 && ts.found) {
-                if (groups.n_groups) atomicAdd(&groups.counts[group_of(groups, u)], ts.found);
-                if constexpr (kV) atomicAdd(vo.tid + u, ts.found);
-            }
-        }
+        ListCtx lc = list_ctx<kM>(vo, ts, u, ctl);
+        if constexpr (kCuckoo) probe_slice<kM>(C, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);
+        else probe_slice<kM>(T, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);
+        finish_task<kM>(acc.same + acc.cross - before, groups, vo, ts, u, ctl);
     }
     flush(acc, ctl, 1, threadIdx.x == 0 ? build : 0, threadIdx.x == 0 ? done : 0);
     if (threadIdx.x == 0 && inserts) atomicAdd(&ctl->cls_inserts[1], inserts);
-    if constexpr (kV) priv_end(vo);
+    if constexpr (kM == 1) priv_end(vo);
 }
 
 // Set the bits of the hashed sets of hub rows rows[i0 .. i0+g) into bitmaps
@@ -1029,7 +1188,7 @@ __global__ void k_hub_set(const uint32_t *__restrict__ rows, uint32_t i0, uint32
 
 // Probe the tasks [first, last) of the hub rows with row index in
 // [i0, i0 + hub_group) against their bitmaps.
-template <bool kV>
+template <int kM>
 __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__ tasks, unsigned long long first,
                                                     unsigned long long last, const uint32_t *__restrict__ rows,
                                                     const uint32_t *__restrict__ ntask, uint32_t i0,
@@ -1046,7 +1205,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
     uint32_t *filter = reinterpret_cast<uint32_t *>(smem_raw + slice_smem_bytes(max_v));
     const uint32_t filter_words = 1u << (filter_log2 - 5);
     const uint32_t fshift = 32u - filter_log2;
-    if constexpr (kV) {
+    if constexpr (kM == 1) {
         vo.priv = reinterpret_cast<unsigned long long *>(filter + filter_words);
         priv_begin(vo);
     }
@@ -1065,7 +1224,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
         const bool rebuild = task.x != cur_row;
         if (rebuild)
             for (uint32_t j = threadIdx.x; j < filter_words; j += blockDim.x) filter[j] = 0u;
-        load_slice<kV>(S, erec + eoff[u], k_lo, k_hi, adj2 + (hb - fu));
+        load_slice<kM>(S, erec + eoff[u], k_lo, k_hi, adj2 + (hb - fu));
         __syncthreads();
         scan_segments(S.len, S.seg, k_hi - k_lo);
         if (rebuild) {
@@ -1083,20 +1242,13 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
         }
         const HubSet H{filter, bits + (uint64_t)(task.x - i0) * words, fshift};
         const unsigned long long before = acc.same + acc.cross;
-        probe_slice<kV>(H, S, k_hi - k_lo, adj2, &ts.next, acc, vo);
-        if (groups.n_groups || kV) {
-            const unsigned long long found = warp_sum(acc.same + acc.cross - before);
-            if (lane == 0 && found) atomicAdd(&ts.found, found);
-            __syncthreads();
-            if (threadIdx.x == 0 && ts.found) {
-                if (groups.n_groups) atomicAdd(&groups.counts[group_of(groups, u)], ts.found);
-                if constexpr (kV) atomicAdd(vo.tid + u, ts.found);
-            }
-        }
+        ListCtx lc = list_ctx<kM>(vo, ts, u, ctl);
+        probe_slice<kM>(H, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);
+        finish_task<kM>(acc.same + acc.cross - before, groups, vo, ts, u, ctl);
     }
     flush(acc, ctl, 2, threadIdx.x == 0 ? build : 0, threadIdx.x == 0 ? done : 0);
     if (threadIdx.x == 0 && inserts) atomicAdd(&ctl->cls_inserts[2], inserts);
-    if constexpr (kV) priv_end(vo);
+    if constexpr (kM == 1) priv_end(vo);
 }
 
 uint32_t pow2_at_least(uint64_t x, uint32_t lo) {
@@ -1129,9 +1281,25 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
     (void)n;
     cudaStream_t s = ctx->stream;
     const Tuning &tu = ctx->tune;
-    const VertexOut vo{b.vcount, b.vcount_rank};
-    const bool kv = b.vcount != nullptr;
+    // what the kernels do with the triangles: 0 count, 1 per-vertex counts,
+    // 2 listing (the counting pass of a listing is mode 0 with hit records)
+    const int mode = b.vcount ? 1 : (b.list_out ? 2 : 0);
+    VertexOut vo{b.vcount, b.vcount_rank};
+    vo.out = b.list_out;
+    vo.inv = b.inv;
     const Ctl &h = *ctx->h_ctl;  // pulled after planning
+    // hit records / output offsets: [tiny rows | warp tasks | block tasks | hub tasks]
+    const unsigned long long cbase[4] = {0, h.n_rows[3], h.n_rows[3] + h.n_tasks[0],
+                                         h.n_rows[3] + h.n_tasks[0] + h.n_tasks[1]};
+    auto vo_for = [&](int slot) {
+        VertexOut v = vo;
+        if (b.hits) {
+            if (mode == 2) v.off = b.hits + cbase[slot];
+            else v.task_hits = b.hits + cbase[slot];
+        }
+        return v;
+    };
+    const size_t priv = mode == 1 ? 8ull * kPrivRanks : 0;
     // ev[4..7] bracket the warp, block and hub kernels
     // tiny rows: one thread each (this count's share of them)
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[8], s));
@@ -1139,12 +1307,12 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
     const uint32_t lo3 = (uint32_t)((uint64_t)nt3 * ctx->shard / ctx->nshards);
     const uint32_t hi3 = (uint32_t)((uint64_t)nt3 * (ctx->shard + 1) / ctx->nshards);
     if (hi3 > lo3) {
-        const size_t smem = 4ull * tu.tiny_cap * 256 + (kv ? 8ull * kPrivRanks : 0);
-        auto tiny = kv ? k_isect_tiny<true> : k_isect_tiny<false>;
+        const size_t smem = 4ull * tu.tiny_cap * 256 + priv;
+        auto tiny = mode == 0 ? k_isect_tiny<0> : mode == 1 ? k_isect_tiny<1> : k_isect_tiny<2>;
         TC_CUDA(ctx, cudaFuncSetAttribute(tiny, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const uint32_t grid = std::min<uint32_t>((hi3 - lo3 + 255) / 256, (uint32_t)ctx->num_sms * 8u);
         tiny<<<grid, 256, smem, s>>>(b.rows[3], lo3, hi3, b.rp, b.adj2, b.fcnt, b.gcnt, ctx->d_ctl, tu.tiny_cap,
-                                     b.groups, vo);
+                                     b.groups, vo_for(0));
         note_launch(ctx);
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[9], s));
@@ -1159,9 +1327,11 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
     share(h.n_tasks[2], &lo2, &hi2);
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[4], s));
     if (hi0 > lo0) {
-        const size_t smem = warp_kernel_smem(tu) + (kv ? 8ull * kPrivRanks : 0);
-        auto kern = tu.table_kind == 0 ? (kv ? k_isect_warp<true, true> : k_isect_warp<true, false>)
-                                       : (kv ? k_isect_warp<false, true> : k_isect_warp<false, false>);
+        const size_t smem = warp_kernel_smem(tu) + priv;
+        auto kern = tu.table_kind == 0
+                        ? (mode == 0 ? k_isect_warp<true, 0> : mode == 1 ? k_isect_warp<true, 1> : k_isect_warp<true, 2>)
+                        : (mode == 0 ? k_isect_warp<false, 0>
+                                     : mode == 1 ? k_isect_warp<false, 1> : k_isect_warp<false, 2>);
         TC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
         TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * tu.warps_per_block, smem));
@@ -1172,14 +1342,18 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         kern<<<(unsigned)grid, 32 * tu.warps_per_block, smem, s>>>(b.tasks[0], b.rows[0], b.ntask[0], b.rp, b.adj2,
                                                                    b.fcnt, b.eoff, b.erec, ctx->d_ctl,
                                                                    warp_table_units(tu), tu.flat_cap, lo0, hi0,
-                                                                   b.groups, vo);
+                                                                   b.groups, vo_for(1));
         note_launch(ctx);
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[5], s));
     if (hi1 > lo1) {
-        const size_t smem = block_kernel_smem(tu) + (kv ? 8ull * kPrivRanks : 0);
-        auto kern = tu.table_kind == 0 ? (kv ? k_isect_block<true, true> : k_isect_block<true, false>)
-                                       : (kv ? k_isect_block<false, true> : k_isect_block<false, false>);
+        const size_t smem = block_kernel_smem(tu) + priv;
+        auto kern = tu.table_kind == 0 ? (mode == 0   ? k_isect_block<true, 0>
+                                          : mode == 1 ? k_isect_block<true, 1>
+                                                      : k_isect_block<true, 2>)
+                                       : (mode == 0   ? k_isect_block<false, 0>
+                                          : mode == 1 ? k_isect_block<false, 1>
+                                                      : k_isect_block<false, 2>);
         TC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
         TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tu.block_threads, smem));
@@ -1189,7 +1363,7 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         const unsigned long long chunk = std::max<unsigned long long>(1, (hi1 - lo1) / (grid * 8));
         kern<<<(unsigned)grid, tu.block_threads, smem, s>>>(b.tasks[1], b.rows[1], b.ntask[1], b.rp, b.adj2, b.fcnt,
                                                             b.eoff, b.erec, ctx->d_ctl, tu.max_v, block_table_units(tu),
-                                                            chunk, lo1, hi1, b.groups, vo);
+                                                            chunk, lo1, hi1, b.groups, vo_for(2));
         note_launch(ctx);
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[6], s));
@@ -1199,8 +1373,8 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         std::vector<unsigned long long> pref(nh + 1);
         TC_CUDA(ctx, cudaMemcpyAsync(pref.data(), b.tpref[2], 8ull * (nh + 1), cudaMemcpyDeviceToHost, s));
         TC_CUDA(ctx, cudaStreamSynchronize(s));
-        const size_t smem = hub_kernel_smem(tu) + (kv ? 8ull * kPrivRanks : 0);
-        auto hub = kv ? k_isect_hub<true> : k_isect_hub<false>;
+        const size_t smem = hub_kernel_smem(tu) + priv;
+        auto hub = mode == 0 ? k_isect_hub<0> : mode == 1 ? k_isect_hub<1> : k_isect_hub<2>;
         TC_CUDA(ctx, cudaFuncSetAttribute(hub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
         TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hub, tu.hub_threads, smem));
@@ -1221,7 +1395,7 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
                                                                      b.rp, b.adj2, b.fcnt, b.eoff, b.erec, ctx->d_ctl,
                                                                      b.hub_bits,
                                                                      b.hub_words, tu.max_v, chunk, tu.hub_filter_log2,
-                                                                     b.groups, vo);
+                                                                     b.groups, vo_for(3));
             note_launch(ctx, 2);
         }
     }

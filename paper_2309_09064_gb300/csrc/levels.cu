@@ -1,7 +1,7 @@
 // levels.cu -- degrees, canonical BFS roots and BFS levels (Algorithm 4, BFS loop).
 //
-// The paper's loop "for all v: if v unvisited, BFS(G, v)" takes vertices in the
-// working order, so every component's root is its first vertex in that order
+// Algorithm 4 starts a BFS from every vertex still unvisited, taking vertices in
+// the working order, so every component's root is its first vertex in that order
 // (degree order: highest degree, then lowest id).  On the GPU:
 //   1. k_init computes degrees, gives isolated vertices level 0 (each is its
 //      own root) and finds the globally first non-isolated vertex;

@@ -56,6 +56,11 @@ struct PipeBufs {
     // array) and by rank (scratch); null otherwise
     unsigned long long *vcount = nullptr;
     unsigned long long *vcount_rank = nullptr;
+    // listing: hit records of every task (counting pass), scanned in place
+    // into output offsets; the triples; rank -> id (null under the id order)
+    unsigned long long *hits = nullptr;
+    uint32_t *list_out = nullptr;
+    uint32_t *inv = nullptr;
 };
 
 tc_status compute_levels(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t slots);

@@ -24,10 +24,16 @@ __global__ void k_rank_keys(uint32_t n, const uint32_t *__restrict__ deg, uint32
         keys[x] = ((unsigned long long)(max_deg - deg[x]) << 32) | x;
 }
 
-__global__ void k_rank_scatter(uint32_t n, const unsigned long long *__restrict__ keys, uint32_t *__restrict__ rank) {
+// rank[x] = position of x's key; inv (nullable) gets the inverse, the id at
+// every position (the listing maps ranks found by the intersections back).
+__global__ void k_rank_scatter(uint32_t n, const unsigned long long *__restrict__ keys, uint32_t *__restrict__ rank,
+                               uint32_t *__restrict__ inv) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        rank[(uint32_t)(keys[i] & 0xFFFFFFFFull)] = (uint32_t)i;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t x = (uint32_t)(keys[i] & 0xFFFFFFFFull);
+        rank[x] = (uint32_t)i;
+        if (inv) inv[i] = x;
+    }
 }
 
 // lv[x] = {rank(x), L(x)}: one 8-byte read gives both for a neighbour; and,
@@ -64,7 +70,7 @@ tc_status compute_ranks(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max
         for (int sh = 0; sh < 32 && (max_deg >> sh) != 0; sh += 8) shifts[ns++] = 32 + sh;
         unsigned long long *cur = b.rkeys0, *alt = b.rkeys1;
         launches += 1 + radix_sort_u64(&cur, &alt, n, shifts, ns, b.rcounts, b.roffs, b.scan_tmp, s);
-        k_rank_scatter<<<grid_for(n, 256, cap), 256, 0, s>>>(n, cur, b.rank);
+        k_rank_scatter<<<grid_for(n, 256, cap), 256, 0, s>>>(n, cur, b.rank, b.inv);
         ++launches;
         rank = b.rank;
     }
