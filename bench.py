@@ -312,6 +312,8 @@ def main():
                     help="time tc_count_vertices (triangles through every vertex) instead of tc_count")
     ap.add_argument("--list-triangles", action="store_true",
                     help="time tc_list_triangles (every triangle written out as three vertex ids) instead of tc_count")
+    ap.add_argument("--alg3", action="store_true",
+                    help="time tc_count_alg3 (Algorithm 3, full neighbourhoods: the comparison kernel) instead of tc_count")
     ap.add_argument("--shard", action="store_true",
                     help="with N > 1: split one count across the ranks (strong scaling) instead of N replicas")
     args = ap.parse_args()
@@ -364,6 +366,8 @@ def main():
             return tc.tc_count_vertices(ctx, g, vcounts)
         if triples is not None:
             return tc.tc_list_triangles(ctx, g, triples, list_cap)
+        if args.alg3:
+            return tc.tc_count_alg3(ctx, g)
         return tc.tc_count(ctx, g)
 
     T0 = None
@@ -405,6 +409,8 @@ def main():
         "k_isect_hub": (mean("ms_class", 2), mean("class_bytes", 2)),
         "k_isect_tiny": (mean("ms_class", 3), mean("class_bytes", 3)),
     }
+    if args.alg3:  # one kernel: its time is the intersection stage's
+        kernels = {"k_alg3": (mean("ms_isect"), mean("class_bytes", 0))}
     dom = max(kernels, key=lambda k: kernels[k][0])
     dom_ms, dom_bytes = kernels[dom]
     peak, peak_kind = measured_peaks()
@@ -452,7 +458,9 @@ def main():
                                                                  "triangle list, 12 B per triangle "
                                                                  "(tc_list_triangles; class times are the "
                                                                  "listing pass)"
-                                                                 if args.list_triangles else "T (tc_count)")}),
+                                                                 if args.list_triangles else
+                                                                 "T by Algorithm 3 (tc_count_alg3, comparison kernel)"
+                                                                 if args.alg3 else "T (tc_count)")}),
         "triangles": T0, "t_same": last["t_same"], "t_cross": last["t_cross"],
         "horizontal_edges": last["horizontal_edges"], "levels": last["levels"],
         "stage_ms": {"levels": mean("ms_levels"), "rows": mean("ms_mark"), "intersect": mean("ms_isect"),

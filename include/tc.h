@@ -244,6 +244,17 @@ tc_status tc_count_with_levels(tc_ctx *ctx, const tc_graph *g, const uint32_t *d
                                tc_stats *stats);
 
 /*
+ * Algorithm 3 (cover-edge triangle counting, Sec. III) as a comparison
+ * kernel: the same BFS levels and working order as tc_count, then for every
+ * horizontal edge u -> v (u earlier) the full intersection of N(u) and N(v)
+ * on the CSR as given, a common neighbour w counting when it lies on another
+ * level or on the same level after v.  Same T and t_same / t_cross as
+ * tc_count with more work per edge (stats->probes = elements of both rows
+ * over all horizontal edges); ms_isect is this kernel's time.
+ */
+tc_status tc_count_alg3(tc_ctx *ctx, const tc_graph *g, uint64_t *triangles, tc_stats *stats);
+
+/*
  * List every triangle of g exactly once.  Algorithm 4 finds each triangle
  * once (one or three horizontal edges; Sec. III), so its hits are the list:
  * d_triples (device uint32_t[3 * capacity], nullable when capacity is 0)

@@ -21,7 +21,7 @@ __all__ = [
     "TC_ORDER_DEGREE", "TC_ORDER_ID", "tc_create", "tc_destroy", "tc_last_error", "tc_set_stream",
     "tc_arena_bytes", "tc_build_csr", "tc_graph_from_csr", "tc_graph_info", "tc_graph_copy_out",
     "tc_validate", "tc_graph_free", "tc_count", "tc_count_levels", "tc_count_with_levels", "tc_count_vertices",
-    "tc_list_triangles", "tc_count_batch",
+    "tc_list_triangles", "tc_count_alg3", "tc_count_batch",
     "tc_submit", "tc_poll",
     "tc_get_tuning", "tc_set_tuning", "tc_count_noalloc", "tc_poll_ex", "tc_count_shard", "tc_selftest_barrier",
     "library_path",
@@ -41,7 +41,7 @@ EXPORTED = ["tc_create", "tc_destroy", "tc_last_error", "tc_set_stream", "tc_get
             "tc_arena_bytes", "tc_build_csr",
             "tc_graph_from_csr", "tc_graph_info", "tc_graph_copy_out", "tc_validate", "tc_graph_free",
             "tc_count", "tc_count_levels", "tc_count_with_levels", "tc_count_vertices", "tc_list_triangles",
-            "tc_count_shard",
+            "tc_count_alg3", "tc_count_shard",
             "tc_count_batch", "tc_submit",
             "tc_poll", "tc_poll_ex",
             "tc_count_noalloc"]
@@ -89,10 +89,12 @@ class tc_stats(ctypes.Structure):
 def _load():
     try:
         path = _build.build()
-    except Exception as e:  # no nvcc / compile error: fail loudly, never fall back
-        if not os.path.exists(_build.LIB):
-            raise ImportError(f"libtc.so is not built and could not be built: {e}") from e
+    except FileNotFoundError as e:  # no nvcc here: a library built from these sources is still fine
+        if not os.path.exists(_build.LIB) or os.path.getmtime(_build.LIB) < _build._deps():
+            raise ImportError(f"libtc.so is missing or older than its sources, and nvcc is not available: {e}") from e
         path = _build.LIB
+    except Exception as e:  # compile error: fail loudly, never load a stale library
+        raise ImportError(f"libtc.so could not be built: {e}") from e
     lib = ctypes.CDLL(path)
     P, V, U32, U64, I = ctypes.POINTER, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
     sig = {
@@ -115,6 +117,7 @@ def _load():
         "tc_count_with_levels": ([V, V, V, P(U64), P(tc_stats)], I),
         "tc_count_vertices": ([V, V, V, P(U64), P(tc_stats)], I),
         "tc_list_triangles": ([V, V, V, U64, P(U64), P(tc_stats)], I),
+        "tc_count_alg3": ([V, V, P(U64), P(tc_stats)], I),
         "tc_count_shard": ([V, V, U32, U32, P(U64), P(tc_stats)], I),
         "tc_count_batch": ([V, U32, P(V), P(U64)], I),
         "tc_submit": ([V, V, P(U64)], I),
@@ -312,6 +315,14 @@ def tc_count_vertices(ctx, g, counts):
     T = ctypes.c_uint64()
     st = tc_stats()
     _check(ctx, _lib.tc_count_vertices(ctx, g, p, ctypes.byref(T), ctypes.byref(st)))
+    return T.value, st.to_dict()
+
+
+def tc_count_alg3(ctx, g):
+    """Algorithm 3 (full neighbourhoods with the level rule) as a comparison kernel: (T, stats)."""
+    T = ctypes.c_uint64()
+    st = tc_stats()
+    _check(ctx, _lib.tc_count_alg3(ctx, g, ctypes.byref(T), ctypes.byref(st)))
     return T.value, st.to_dict()
 
 

@@ -404,6 +404,21 @@ tc_status tc_list_triangles(tc_ctx *ctx, const tc_graph *g, uint32_t *d_triples,
     return count_pipeline(ctx, v, nullptr, none, triangles, stats, nullptr, nullptr, &list);
 }
 
+tc_status tc_count_alg3(tc_ctx *ctx, const tc_graph *g, uint64_t *triangles, tc_stats *stats) {
+    if (!ctx || !g) return set_error(ctx, TC_ERR_INVALID, "bad argument");
+    if (g->ctx != ctx && g->ctx->device != ctx->device)
+        return set_error(ctx, TC_ERR_INVALID, "graph lives on another device");
+    DeviceGuard guard(ctx->device);
+    GraphView v;
+    v.n = g->n;
+    v.slots = g->slots;
+    v.rp = g->rp;
+    v.col = g->col;
+    v.max_deg = g->max_deg;
+    GroupSpec none;
+    return count_pipeline(ctx, v, nullptr, none, triangles, stats, nullptr, nullptr, nullptr, true);
+}
+
 tc_status tc_count(tc_ctx *ctx, const tc_graph *g, uint64_t *triangles, tc_stats *stats) {
     return tc_count_levels(ctx, g, nullptr, triangles, stats);
 }

@@ -71,7 +71,7 @@ size_t list_bytes(uint32_t n, uint64_t slots) {
 
 tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, const GroupSpec &groups,
                          uint64_t *triangles, tc_stats *stats, const uint32_t *levels_in, uint64_t *vertex_counts,
-                         const ListSpec *list) {
+                         const ListSpec *list, bool alg3) {
     const uint32_t n = g.n;
     cudaStream_t s = ctx->stream;
     uint64_t hub_words = 0;
@@ -160,49 +160,58 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     b.lvp = (n <= (1u << 24) && ctx->h_ctl->max_level < 255) ? lvp : nullptr;
     st = compute_ranks(ctx, b, n, g.max_deg);
     if (st != TC_OK) return st;
-    st = build_rows(ctx, b, n, g.max_deg);
-    if (st != TC_OK) return st;
-    st = pull(ctx);  // row counts per class
-    if (st != TC_OK) return st;
-    st = plan_scans(ctx, b);
-    if (st != TC_OK) return st;
-    st = pull(ctx);  // task counts per class
-    if (st != TC_OK) return st;
-    st = emit_tasks(ctx, b);
-    if (st != TC_OK) return st;
-    TC_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
-    st = intersect(ctx, b, n);
-    if (st != TC_OK) return st;
-    Ctl counted{};
-    if (list) {
-        // The counting pass recorded the triangles of every task; their
-        // exclusive prefix is where each task writes in the listing pass.
-        st = pull(ctx);
+    Ctl counted{};  // listing: the counting pass's control block
+    if (alg3) {  // the comparison kernel: full neighbourhoods, no rows
+        TC_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
+        st = intersect_alg3(ctx, b, n, g.slots);
         if (st != TC_OK) return st;
-        counted = *ctx->h_ctl;
-        const uint64_t T = counted.t_same + counted.t_cross;
-        if (triangles) *triangles = T;
-        if (counted.error) {
-            char msg[96];
-            std::snprintf(msg, sizeof msg, "device-side check failed during the count (code 0x%x)", counted.error);
-            return set_error(ctx, TC_ERR_INVALID, msg);
-        }
-        const uint64_t H = (uint64_t)counted.n_rows[3] + counted.n_tasks[0] + counted.n_tasks[1] + counted.n_tasks[2];
-        if (H + 1 > list_records(n, g.slots)) return set_error(ctx, TC_ERR_INVALID, "listing: more tasks than records");
-        note_launch(ctx, scan_u64(reinterpret_cast<uint64_t *>(b.hits), reinterpret_cast<uint64_t *>(b.hits), H,
-                                  list_tmp, s));
-        unsigned long long listed = 0;
-        TC_CUDA(ctx, cudaMemcpyAsync(&listed, b.hits + H, 8, cudaMemcpyDeviceToHost, s));
-        TC_CUDA(ctx, cudaStreamSynchronize(s));
-        if (listed != T) return set_error(ctx, TC_ERR_INVALID, "listing: task records disagree with the count");
-        if (T > list->capacity) return set_error(ctx, TC_ERR_CAPACITY, "listing: more triangles than capacity");
-        if (T) {
-            b.list_out = list->out;
-            TC_CUDA(ctx, cudaMemsetAsync(ctx->d_ctl->task_next, 0, sizeof(ctx->d_ctl->task_next), s));
-            st = intersect(ctx, b, n);
+        ctx->isect_flags = 0;
+    } else {
+        st = build_rows(ctx, b, n, g.max_deg);
+        if (st != TC_OK) return st;
+        st = pull(ctx);  // row counts per class
+        if (st != TC_OK) return st;
+        st = plan_scans(ctx, b);
+        if (st != TC_OK) return st;
+        st = pull(ctx);  // task counts per class
+        if (st != TC_OK) return st;
+        st = emit_tasks(ctx, b);
+        if (st != TC_OK) return st;
+        TC_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
+        st = intersect(ctx, b, n);
+        if (st != TC_OK) return st;
+        if (list) {
+            // The counting pass recorded the triangles of every task; their
+            // exclusive prefix is where each task writes in the listing pass.
+            st = pull(ctx);
             if (st != TC_OK) return st;
+            counted = *ctx->h_ctl;
+            const uint64_t T = counted.t_same + counted.t_cross;
+            if (triangles) *triangles = T;
+            if (counted.error) {
+                char msg[96];
+                std::snprintf(msg, sizeof msg, "device-side check failed during the count (code 0x%x)", counted.error);
+                return set_error(ctx, TC_ERR_INVALID, msg);
+            }
+            const uint64_t H =
+                (uint64_t)counted.n_rows[3] + counted.n_tasks[0] + counted.n_tasks[1] + counted.n_tasks[2];
+            if (H + 1 > list_records(n, g.slots))
+                return set_error(ctx, TC_ERR_INVALID, "listing: more tasks than records");
+            note_launch(ctx, scan_u64(reinterpret_cast<uint64_t *>(b.hits), reinterpret_cast<uint64_t *>(b.hits), H,
+                                      list_tmp, s));
+            unsigned long long listed = 0;
+            TC_CUDA(ctx, cudaMemcpyAsync(&listed, b.hits + H, 8, cudaMemcpyDeviceToHost, s));
+            TC_CUDA(ctx, cudaStreamSynchronize(s));
+            if (listed != T) return set_error(ctx, TC_ERR_INVALID, "listing: task records disagree with the count");
+            if (T > list->capacity) return set_error(ctx, TC_ERR_CAPACITY, "listing: more triangles than capacity");
+            if (T) {
+                b.list_out = list->out;
+                TC_CUDA(ctx, cudaMemsetAsync(ctx->d_ctl->task_next, 0, sizeof(ctx->d_ctl->task_next), s));
+                st = intersect(ctx, b, n);
+                if (st != TC_OK) return st;
+            }
         }
-    }
+    }  // Algorithm 4
     if (vertex_counts && n) {  // the third vertices were counted by rank
         k_vertex_finish<<<(unsigned)std::min<uint64_t>(((uint64_t)n + 255) / 256, (uint64_t)ctx->num_sms * 16), 256, 0,
                           s>>>(n, b.lv, b.vcount_rank, b.vcount);
@@ -256,7 +265,7 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
         //   output: 8
         const uint64_t S = g.slots, N1 = (uint64_t)n + 1;
         const uint64_t lv = 8 * N1 + 4 * S + 4 * S + 4ull * n;
-        const uint64_t rw = 8 * N1 + 4 * S + 8 * S + 4 * S + 8ull * n;
+        const uint64_t rw = alg3 ? 0 : 8 * N1 + 4 * S + 8 * S + 4 * S + 8ull * n;
         uint64_t is = 0;
         for (int c = 0; c < 4; ++c) {
             stats->class_rows[c] = h.cls_rows[c];

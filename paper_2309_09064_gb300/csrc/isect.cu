@@ -91,23 +91,22 @@ __device__ __forceinline__ void emit_one(const VertexOut &vo, ListCtx &lc, uint3
     t[2] = vo.inv ? vo.inv[w] : w;
 }
 
-// Write the hits of one warp step: a warp-wide prefix of the per-lane hit
-// counts gives every lane its first slot; vr[i] is the probed vertex of
-// element i (per element on the concatenated path).
+// Write the hits of one warp step, element-major: the hits of element i of
+// all lanes are consecutive (one ballot per element gives every lane its
+// place), so the stores of one element go to one run of addresses.  vr[i] is
+// the probed vertex of element i (per element on the concatenated path).
 template <int U>
 __device__ __forceinline__ void emit_step(const bool (&hit)[U], const uint32_t (&w)[U], const uint32_t (&vr)[U],
                                           const VertexOut &vo, ListCtx &lc) {
     const unsigned lane = lane_id();
-    uint32_t c = 0;
+    const unsigned below = (1u << lane) - 1u;  // lanes before this one
+    unsigned m[U];
+    uint32_t total = 0;
 #pragma unroll
-    for (int i = 0; i < U; ++i) c += hit[i];
-    uint32_t incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= (unsigned)o) incl += y;
+    for (int i = 0; i < U; ++i) {
+        m[i] = __ballot_sync(0xFFFFFFFFu, hit[i]);
+        total += __popc(m[i]);
     }
-    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
     if (total == 0) return;
     uint32_t first = 0;
     if (lc.shared) {
@@ -121,15 +120,16 @@ __device__ __forceinline__ void emit_step(const bool (&hit)[U], const uint32_t (
         if (lane == 0) atomicOr(lc.err, kGuardList);
         return;
     }
-    unsigned long long o = lc.base + first + (incl - c);
+    unsigned long long o = lc.base + first;
 #pragma unroll
     for (int i = 0; i < U; ++i) {
         if (hit[i]) {
-            uint32_t *t = vo.out + 3 * o++;
+            uint32_t *t = vo.out + 3 * (o + __popc(m[i] & below));
             t[0] = lc.u;
             t[1] = vr[i];
             t[2] = vo.inv ? vo.inv[w[i]] : w[i];
         }
+        o += __popc(m[i]);
     }
 }
 

@@ -70,6 +70,8 @@ tc_status given_levels(tc_ctx *ctx, const PipeBufs &b, uint32_t n, const uint32_
 tc_status selftest_barrier(tc_ctx *ctx, uint32_t timeout_ms);
 // rank of every vertex in the working order, packed with its level (lv)
 tc_status compute_ranks(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_deg);
+// Algorithm 3 over the CSR as given, after the levels and ranks (alg3.cu).
+tc_status intersect_alg3(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t slots);
 // partition, orientation, compaction, classification and per-class task counts
 tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_deg);
 // scans of the per-class task counts (after the host has read the row counts)

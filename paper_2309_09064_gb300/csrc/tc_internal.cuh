@@ -181,7 +181,7 @@ struct ListSpec {
 };
 tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, const GroupSpec &groups,
                          uint64_t *triangles, tc_stats *stats, const uint32_t *levels_in = nullptr,
-                         uint64_t *vertex_counts = nullptr, const ListSpec *list = nullptr);
+                         uint64_t *vertex_counts = nullptr, const ListSpec *list = nullptr, bool alg3 = false);
 size_t pipeline_bytes(const tc_ctx *ctx, uint32_t n, uint64_t slots, uint32_t max_deg, bool own_levels,
                       uint64_t *hub_words, uint32_t *hub_maps);
 

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     text = open(os.path.join(ROOT, "include", "tc.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return set(re.findall(r"\b(tc_[a-z_]+)\s*\(", text))
+    return set(re.findall(r"\b(tc_[a-z0-9_]+)\s*\(", text))
 
 
 def test_header_declares_the_boundary_calls():
@@ -25,7 +25,7 @@ def test_library_exports_every_declared_symbol():
     import paper_2309_09064_gb300 as tc
     path = tc.library_path()
     out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
-    exported = set(re.findall(r" T (tc_[a-z_]+)$", out, flags=re.M))
+    exported = set(re.findall(r" T (tc_[a-z0-9_]+)$", out, flags=re.M))
     assert declared_functions() == exported
     assert set(tc.EXPORTED) == exported
     for name in exported:
