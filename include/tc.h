@@ -261,12 +261,15 @@ tc_status tc_count_alg3(tc_ctx *ctx, const tc_graph *g, uint64_t *triangles, tc_
  * gets T rows {u, v, w} of vertex ids -- u the vertex whose set was hashed,
  * v the probed one (u -> v a horizontal edge, u earlier in the working
  * order), w the third vertex -- in no particular order; *triangles gets T.
- * Two passes of the intersections: the first counts the triangles of every
- * task, an exclusive scan turns those counts into output offsets, the second
- * writes each task's triangles at its offset (rows d_triples[3T ..] are left
- * untouched).  If T > capacity nothing is written and the call returns
- * TC_ERR_CAPACITY with *triangles = T, so that the caller can size the
- * output and call again.  stats as in tc_count (of the counting pass).
+ * One pass of the intersections: every warp writes the triangles it finds
+ * into chunks of output rows it takes from a global cursor; a compaction
+ * then moves the rows written past T into the gaps the last, partly filled
+ * chunks left (rows past T are scratch: their contents are unspecified).
+ * The tiny rows (one thread each) are counted first and written at exact
+ * offsets after the others.  If T > capacity the call returns
+ * TC_ERR_CAPACITY with *triangles = T (the output rows are unspecified), so
+ * that the caller can size the output and call again.  stats as in tc_count
+ * (the class times are those of the listing kernels).
  */
 tc_status tc_list_triangles(tc_ctx *ctx, const tc_graph *g, uint32_t *d_triples, uint64_t capacity,
                             uint64_t *triangles, tc_stats *stats);

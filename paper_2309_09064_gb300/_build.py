@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libtc.so")
 
-SOURCES = ["api.cu", "count.cu", "levels.cu", "rank.cu", "rows.cu", "isect.cu", "scan.cu", "csr.cu", "batch.cu", "serve.cu", "alg3.cu",
+SOURCES = ["api.cu", "count.cu", "levels.cu", "rank.cu", "rows.cu", "isect.cu", "scan.cu", "csr.cu", "batch.cu", "serve.cu", "alg3.cu", "list.cu",
            "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

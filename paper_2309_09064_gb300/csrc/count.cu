@@ -60,13 +60,28 @@ size_t pipeline_bytes(const tc_ctx *ctx, uint32_t n, uint64_t slots, uint32_t ma
     return bytes + 4096;
 }
 
-// Listing scratch: one hit record per task and per tiny row (tasks never
-// outnumber the oriented horizontal edges plus one, tiny rows the vertices)
-// and the scan's tile sums; rank -> id.
-uint64_t list_records(uint32_t n, uint64_t slots) { return slots / 2 + (uint64_t)n + 3; }
-size_t list_bytes(uint32_t n, uint64_t slots) {
-    const uint64_t H = list_records(n, slots);
-    return 8 * H + 8 * scan_tmp_elems(H) + 4ull * ((size_t)n + 1) + 3 * 256;
+// Listing scratch (capacity `cap` triples in the caller's buffer): hit
+// records of the tiny rows (at most one per vertex), one open-chunk state
+// per warp that can be resident (64 per SM), an overflow area of one chunk
+// per state (the open chunks can reach past the caller's buffer), the fill
+// of every chunk, the compaction's two scans, rank -> id.
+struct ListSizes {
+    uint64_t tiny, states, ovf, nch, scratch, tmp;
+};
+ListSizes list_sizes(const tc_ctx *ctx, uint32_t n, uint64_t cap) {
+    ListSizes z;
+    z.tiny = (uint64_t)n + 2;
+    z.states = (uint64_t)ctx->num_sms * 64;
+    z.ovf = z.states * kListChunk;
+    z.nch = (cap + z.ovf) / kListChunk + 1;
+    z.scratch = list_compact_scratch(z.nch);
+    z.tmp = scan_tmp_elems(std::max<uint64_t>(z.tiny, z.nch + 1));
+    return z;
+}
+size_t list_bytes(const tc_ctx *ctx, uint32_t n, uint64_t cap) {
+    const ListSizes z = list_sizes(ctx, n, cap);
+    return 8 * z.tiny + 16 * z.states + 12 * z.ovf + 4 * z.nch + 8 * z.scratch + 8 * z.tmp +
+           4ull * ((size_t)n + 1) + 8 * 256;
 }
 
 tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, const GroupSpec &groups,
@@ -77,7 +92,7 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     uint64_t hub_words = 0;
     uint32_t hub_maps = 0;
     const size_t need = pipeline_bytes(ctx, n, g.slots, g.max_deg, levels_out == nullptr, &hub_words, &hub_maps) +
-                        (vertex_counts ? 8ull * ((size_t)n + 1) + 256 : 0) + (list ? list_bytes(n, g.slots) : 0);
+                        (vertex_counts ? 8ull * ((size_t)n + 1) + 256 : 0) + (list ? list_bytes(ctx, n, list->capacity) : 0);
     tc_status st = arena_reserve(ctx, need);
     if (st != TC_OK) return st;
     Arena &a = ctx->arena;
@@ -138,13 +153,26 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
         }
     }
     uint64_t *list_tmp = nullptr;
+    unsigned long long *list_scratch = nullptr;
     if (list) {
-        b.hits = a.take<unsigned long long>(list_records(n, g.slots));
-        list_tmp = a.take<uint64_t>(scan_tmp_elems(list_records(n, g.slots)));
+        const ListSizes z = list_sizes(ctx, n, list->capacity);
+        b.hits = a.take<unsigned long long>(z.tiny);
+        b.wstate = a.take<ulonglong2>(z.states);
+        b.wstate_len = z.states;
+        b.ovf = a.take<uint32_t>(3 * z.ovf);
+        b.ovf_cap = z.ovf;
+        b.fills = a.take<uint32_t>(z.nch);
+        b.nch = z.nch;
+        list_scratch = a.take<unsigned long long>(z.scratch);
+        list_tmp = a.take<uint64_t>(z.tmp);
+        b.list_out = list->out;
+        b.list_cap = list->capacity;
         if (ctx->opt.order == TC_ORDER_DEGREE && g.max_deg > 0) b.inv = a.take<uint32_t>(n1);
-        if (!b.hits || !list_tmp || (ctx->opt.order == TC_ORDER_DEGREE && g.max_deg > 0 && !b.inv))
+        if (!b.hits || !b.wstate || !b.ovf || !b.fills || !list_scratch || !list_tmp ||
+            (ctx->opt.order == TC_ORDER_DEGREE && g.max_deg > 0 && !b.inv))
             return set_error(ctx, TC_ERR_OOM, "arena carve failed");
-        TC_CUDA(ctx, cudaMemsetAsync(b.hits, 0, 8 * list_records(n, g.slots), s));
+        TC_CUDA(ctx, cudaMemsetAsync(b.hits, 0, 8 * z.tiny, s));
+        TC_CUDA(ctx, cudaMemsetAsync(b.wstate, 0, 16 * z.states, s));
     }
     ok = ok && b.fpref && b.eoff && b.lv && b.rkeys0 && b.rkeys1 && b.rcounts && b.roffs && b.adj2 && b.erec &&
          b.scan_tmp && b.task_pool && (!hub_maps || b.hub_bits);
@@ -160,7 +188,8 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     b.lvp = (n <= (1u << 24) && ctx->h_ctl->max_level < 255) ? lvp : nullptr;
     st = compute_ranks(ctx, b, n, g.max_deg);
     if (st != TC_OK) return st;
-    Ctl counted{};  // listing: the counting pass's control block
+    Ctl counted{};                   // listing: the control block after phase 1
+    unsigned long long list_tiny = 0;  // listing: triangles of the tiny rows
     if (alg3) {  // the comparison kernel: full neighbourhoods, no rows
         TC_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
         st = intersect_alg3(ctx, b, n, g.slots);
@@ -178,35 +207,36 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
         st = emit_tasks(ctx, b);
         if (st != TC_OK) return st;
         TC_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
+        b.list_phase = list ? 1 : 0;
         st = intersect(ctx, b, n);
         if (st != TC_OK) return st;
         if (list) {
-            // The counting pass recorded the triangles of every task; their
-            // exclusive prefix is where each task writes in the listing pass.
+            // Phase 1 wrote the triangles of the warp, block and hub classes
+            // into chunks and counted those of the tiny rows; compact the
+            // former into [0, T_big), then write the latter after them.
+            const uint32_t n3 = ctx->h_ctl->n_rows[3];
+            note_launch(ctx, scan_u64(reinterpret_cast<uint64_t *>(b.hits), reinterpret_cast<uint64_t *>(b.hits), n3,
+                                      list_tmp, s));
+            unsigned long long &t_tiny = list_tiny;
+            TC_CUDA(ctx, cudaMemcpyAsync(&t_tiny, b.hits + n3, 8, cudaMemcpyDeviceToHost, s));
             st = pull(ctx);
             if (st != TC_OK) return st;
             counted = *ctx->h_ctl;
             const uint64_t T = counted.t_same + counted.t_cross;
             if (triangles) *triangles = T;
-            if (counted.error) {
+            if (counted.error && !(T > list->capacity && counted.error == 0x400u)) {
                 char msg[96];
                 std::snprintf(msg, sizeof msg, "device-side check failed during the count (code 0x%x)", counted.error);
                 return set_error(ctx, TC_ERR_INVALID, msg);
             }
-            const uint64_t H =
-                (uint64_t)counted.n_rows[3] + counted.n_tasks[0] + counted.n_tasks[1] + counted.n_tasks[2];
-            if (H + 1 > list_records(n, g.slots))
-                return set_error(ctx, TC_ERR_INVALID, "listing: more tasks than records");
-            note_launch(ctx, scan_u64(reinterpret_cast<uint64_t *>(b.hits), reinterpret_cast<uint64_t *>(b.hits), H,
-                                      list_tmp, s));
-            unsigned long long listed = 0;
-            TC_CUDA(ctx, cudaMemcpyAsync(&listed, b.hits + H, 8, cudaMemcpyDeviceToHost, s));
-            TC_CUDA(ctx, cudaStreamSynchronize(s));
-            if (listed != T) return set_error(ctx, TC_ERR_INVALID, "listing: task records disagree with the count");
             if (T > list->capacity) return set_error(ctx, TC_ERR_CAPACITY, "listing: more triangles than capacity");
-            if (T) {
-                b.list_out = list->out;
-                TC_CUDA(ctx, cudaMemsetAsync(ctx->d_ctl->task_next, 0, sizeof(ctx->d_ctl->task_next), s));
+            if (t_tiny > T) return set_error(ctx, TC_ERR_INVALID, "listing: tiny-row records exceed the count");
+            st = list_compact(ctx, b, T - t_tiny, counted.list_cursor, list_scratch,
+                              reinterpret_cast<unsigned long long *>(list_tmp));
+            if (st != TC_OK) return st;
+            if (t_tiny) {
+                b.list_phase = 2;
+                b.tiny_base = T - t_tiny;
                 st = intersect(ctx, b, n);
                 if (st != TC_OK) return st;
             }
@@ -222,13 +252,12 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     st = pull(ctx);
     if (st != TC_OK) return st;
     if (list) {
-        // the listing pass found every triangle again: its counters doubled
+        // phase 2 found the tiny rows' triangles again
         const Ctl &h2 = *ctx->h_ctl;
-        if (!h2.error && b.list_out &&
-            (h2.t_same != 2 * counted.t_same || h2.t_cross != 2 * counted.t_cross))
-            return set_error(ctx, TC_ERR_INVALID, "listing pass disagrees with the count");
+        if (!h2.error && h2.t_same + h2.t_cross != counted.t_same + counted.t_cross + list_tiny)
+            return set_error(ctx, TC_ERR_INVALID, "listing pass of the tiny rows disagrees with the count");
         const unsigned err = h2.error;
-        *ctx->h_ctl = counted;  // statistics of the counting pass
+        *ctx->h_ctl = counted;  // statistics of the listing pass
         ctx->h_ctl->error = err;
     }
     const Ctl &h = *ctx->h_ctl;

@@ -49,55 +49,112 @@ struct Acc {
 //     each of its three vertices -- the hashed vertex u and the probed vertex
 //     v by id (tid), the third vertex w by rank (trank, the value found in the
 //     probe range; mapped back to ids after the count);
-//   kM = 2, listing (tc_list_triangles, second pass): every triangle is
-//     written as (u, v, w) in vertex ids at the offset of its task (the
-//     counting pass recorded every task's hits in task_hits, a scan turned
-//     them into off), positions within a task handed out per warp step.
+//   kM = 2, listing (tc_list_triangles): every triangle is written as
+//     (u, v, w) in vertex ids.  The warp, block and hub classes write in one
+//     pass into chunks of kListChunk slots that every warp takes from a global
+//     cursor as it fills them (a compaction after the pass closes the gaps
+//     the last, partly filled chunks leave); the tiny class writes at exact
+//     offsets (off: the scan of its rows' hits, recorded in task_hits by an
+//     earlier counting launch), after the others.
 struct VertexOut {
     unsigned long long *tid = nullptr;
     unsigned long long *trank = nullptr;
     unsigned long long *priv = nullptr;        // shared: block-private counts of the ranks below kPrivRanks
-    uint32_t *out = nullptr;                   // listing: triples
-    const uint32_t *inv = nullptr;             // listing: rank -> id (null: ranks are ids)
-    const unsigned long long *off = nullptr;   // listing: output offset of every task of the class
-    unsigned long long *task_hits = nullptr;   // counting pass of a listing: hits of every task of the class
-};
-
-constexpr unsigned kGuardList = 0x400u;  // a task found more triangles than the counting pass gave it room for
-
-// Listing position of one task: its output slots [base, end) (the counting
-// pass's hits of the task), the vertices of the current probe range, and the
-// cursor -- a warp-owned counter, or a shared one when several warps work on
-// the task.
-struct ListCtx {
-    unsigned long long base = 0, end = 0;
-    uint32_t u = 0, v = 0;
-    unsigned int local = 0;
-    unsigned int *shared = nullptr;
+    uint32_t *out = nullptr;                   // listing: triples, room for cap of them
+    unsigned long long cap = 0;
+    uint32_t *ovf = nullptr;                   // listing: overflow triples (positions cap .. cap + ovf_cap)
+    unsigned long long ovf_cap = 0;
+    unsigned long long *cursor = nullptr;      // listing: next free chunk position
+    uint32_t *fills = nullptr;                 // listing: filled slots of every full chunk (nch chunks)
+    unsigned long long nch = 0;
+    ulonglong2 *wstate = nullptr;              // listing: open chunk {next position, room} of every warp
+    unsigned long long wstate_len = 0;
     unsigned int *err = nullptr;
+    const uint32_t *inv = nullptr;             // listing: rank -> id (null: ranks are ids)
+    const unsigned long long *off = nullptr;   // listing, tiny class: output offset of every row
+    unsigned long long base = 0;               // listing, tiny class: where the tiny triangles start
+    unsigned long long *task_hits = nullptr;   // tiny counting launch of a listing: hits of every row
 };
 
-// One triangle (u, v, third vertex by rank w) at the thread's own cursor
-// (one thread per task: the tiny class).
-__device__ __forceinline__ void emit_one(const VertexOut &vo, ListCtx &lc, uint32_t w) {
-    const unsigned long long o = lc.base + lc.local++;
-    if (o >= lc.end) {
-        atomicOr(lc.err, kGuardList);
+constexpr unsigned kGuardList = 0x400u;  // a listing write fell outside its room
+
+// Where triple position p lives: the caller's buffer, then the overflow
+// area; null past both (the caller's capacity was too small).
+__device__ __forceinline__ uint32_t *triple_at(const VertexOut &vo, unsigned long long p) {
+    if (p < vo.cap) return vo.out + 3 * p;
+    p -= vo.cap;
+    return p < vo.ovf_cap ? vo.ovf + 3 * p : nullptr;
+}
+
+__device__ __forceinline__ void put_triple(const VertexOut &vo, unsigned long long p, uint32_t u, uint32_t v,
+                                           uint32_t w) {
+    uint32_t *t = triple_at(vo, p);
+    if (!t) {
+        atomicOr(vo.err, kGuardList);
         return;
     }
-    uint32_t *t = vo.out + 3 * o;
-    t[0] = lc.u;
-    t[1] = lc.v;
+    t[0] = u;
+    t[1] = v;
     t[2] = vo.inv ? vo.inv[w] : w;
 }
 
+// Listing state of one warp (all lanes hold the same values): its open
+// chunk -- next free position and the slots left in it (0: none) -- and the
+// vertices of the current range; or, for one thread of the tiny class, its
+// exact slots [base, end) and cursor.
+struct ListCtx {
+    unsigned long long pos = 0;
+    uint32_t room = 0;
+    uint32_t u = 0, v = 0;
+    uint32_t *stage = nullptr;  // the warp's shared staging area (kStageSlots ids, then as many vertices)
+    unsigned long long base = 0, end = 0;
+    uint32_t local = 0;
+};
+
+// Hits of one warp step staged in shared memory before they are written:
+// at most 32 lanes x 8 unrolled elements.
+constexpr uint32_t kStageSlots = 256;
+
+__device__ __forceinline__ void load_list_state(const VertexOut &vo, ListCtx &lc, unsigned long long gw) {
+    if (gw < vo.wstate_len) {
+        const ulonglong2 st = vo.wstate[gw];
+        lc.pos = st.x;
+        lc.room = (uint32_t)st.y;
+    } else {
+        atomicOr(vo.err, kGuardList);
+    }
+}
+
+__device__ __forceinline__ void store_list_state(const VertexOut &vo, const ListCtx &lc, unsigned long long gw) {
+    if (lane_id() == 0 && gw < vo.wstate_len) vo.wstate[gw] = make_ulonglong2(lc.pos, lc.room);
+}
+
+// One triangle (u, v, third vertex by rank w) at the thread's own cursor
+// (one thread per row: the tiny class).
+__device__ __forceinline__ void emit_one(const VertexOut &vo, ListCtx &lc, uint32_t w) {
+    const unsigned long long o = lc.base + lc.local++;
+    if (o >= lc.end) {
+        atomicOr(vo.err, kGuardList);
+        return;
+    }
+    put_triple(vo, o, lc.u, lc.v, w);
+}
+
 // Write the hits of one warp step, element-major: the hits of element i of
-// all lanes are consecutive (one ballot per element gives every lane its
-// place), so the stores of one element go to one run of addresses.  vr[i] is
-// the probed vertex of element i (per element on the concatenated path).
-template <int U>
+// all lanes are consecutive, one ballot per element placing them.  With a
+// stage (block and hub classes) the lanes first put them in shared memory,
+// then write them out with every lane busy, consecutive lanes writing
+// consecutive rows; without one (the warp class, whose steps come from
+// short ranges) each lane writes its own.  They go to the rest of the warp's
+// open chunk and, past its end, to a new chunk taken from the global cursor
+// (a step never fills a whole chunk); a chunk that fills up records its
+// fill.  With kPerElemV the probed vertex differs per element (vr[i], the
+// concatenated path); otherwise it is lc.v.
+template <int U, bool kPerElemV, bool kStage>
 __device__ __forceinline__ void emit_step(const bool (&hit)[U], const uint32_t (&w)[U], const uint32_t (&vr)[U],
                                           const VertexOut &vo, ListCtx &lc) {
+    static_assert(32 * U <= kStageSlots, "a warp step must fit in the stage");
+    static_assert(32 * U < kListChunk, "a warp step must fit in one fresh chunk");
     const unsigned lane = lane_id();
     const unsigned below = (1u << lane) - 1u;  // lanes before this one
     unsigned m[U];
@@ -108,28 +165,116 @@ __device__ __forceinline__ void emit_step(const bool (&hit)[U], const uint32_t (
         total += __popc(m[i]);
     }
     if (total == 0) return;
-    uint32_t first = 0;
-    if (lc.shared) {
-        if (lane == 0) first = atomicAdd(lc.shared, total);
-        first = __shfl_sync(0xFFFFFFFFu, first, 0);
-    } else {
-        first = lc.local;
-        lc.local += total;
-    }
-    if (lc.base + first + total > lc.end) {  // never with a matching counting pass
-        if (lane == 0) atomicOr(lc.err, kGuardList);
+    if (!kStage && total <= lc.room && lc.pos + lc.room <= vo.cap) {
+        // no stage (the warp class): each lane writes its own hits
+        uint32_t *dst = vo.out + 3 * lc.pos;
+        uint32_t k = 0;
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            if (hit[i]) {
+                uint32_t *t = dst + 3 * (k + __popc(m[i] & below));
+                t[0] = lc.u;
+                t[1] = kPerElemV ? vr[i] : lc.v;
+                t[2] = vo.inv ? vo.inv[w[i]] : w[i];
+            }
+            k += __popc(m[i]);
+        }
+        lc.pos += total;
+        lc.room -= total;
+        if (lc.room == 0) {
+            if (lane == 0) {
+                const unsigned long long id = lc.pos / kListChunk - 1;
+                if (id < vo.nch) vo.fills[id] = kListChunk;
+            }
+            lc.pos = 0;
+        }
         return;
     }
-    unsigned long long o = lc.base + first;
+    if (!kStage) {  // rare (a chunk boundary, the overflow area): one position at a time
+        unsigned long long fresh = 0;
+        if (total > lc.room) {
+            if (lane == 0) fresh = atomicAdd(vo.cursor, (unsigned long long)kListChunk);
+            fresh = __shfl_sync(0xFFFFFFFFu, fresh, 0);
+        }
+        uint32_t k = 0;
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            if (hit[i]) {
+                const uint32_t kk = k + __popc(m[i] & below);
+                put_triple(vo, kk < lc.room ? lc.pos + kk : fresh + (kk - lc.room), lc.u, kPerElemV ? vr[i] : lc.v,
+                           w[i]);
+            }
+            k += __popc(m[i]);
+        }
+        if (total < lc.room) {
+            lc.pos += total;
+            lc.room -= total;
+        } else {
+            if (lc.room && lane == 0) {
+                const unsigned long long id = (lc.pos + lc.room) / kListChunk - 1;
+                if (id < vo.nch) vo.fills[id] = kListChunk;
+            }
+            const uint32_t spill = total - lc.room;
+            lc.pos = spill ? fresh + spill : 0;
+            lc.room = spill ? kListChunk - spill : 0;
+        }
+        return;
+    }
+    uint32_t k = 0;
 #pragma unroll
     for (int i = 0; i < U; ++i) {
         if (hit[i]) {
-            uint32_t *t = vo.out + 3 * (o + __popc(m[i] & below));
-            t[0] = lc.u;
-            t[1] = vr[i];
-            t[2] = vo.inv ? vo.inv[w[i]] : w[i];
+            const uint32_t kk = k + __popc(m[i] & below);
+            lc.stage[kk] = w[i];
+            if constexpr (kPerElemV) lc.stage[kStageSlots + kk] = vr[i];
         }
-        o += __popc(m[i]);
+        k += __popc(m[i]);
+    }
+    __syncwarp();
+    if (total <= lc.room && lc.pos + lc.room <= vo.cap) {  // the open chunk takes it, in the caller's buffer
+        uint32_t *dst = vo.out + 3 * lc.pos;
+        for (uint32_t j = lane; j < total; j += 32) {
+            const uint32_t x = lc.stage[j];
+            uint32_t *t = dst + 3 * j;
+            t[0] = lc.u;
+            t[1] = kPerElemV ? lc.stage[kStageSlots + j] : lc.v;
+            t[2] = vo.inv ? vo.inv[x] : x;
+        }
+    } else {
+        unsigned long long fresh = 0;
+        if (total > lc.room) {
+            if (lane == 0) fresh = atomicAdd(vo.cursor, (unsigned long long)kListChunk);
+            fresh = __shfl_sync(0xFFFFFFFFu, fresh, 0);
+        }
+        for (uint32_t j = lane; j < total; j += 32)
+            put_triple(vo, j < lc.room ? lc.pos + j : fresh + (j - lc.room), lc.u,
+                       kPerElemV ? lc.stage[kStageSlots + j] : lc.v, lc.stage[j]);
+        if (total < lc.room) {
+            lc.pos += total;
+            lc.room -= total;
+        } else {
+            if (lc.room && lane == 0) {  // the open chunk is full
+                const unsigned long long id = (lc.pos + lc.room) / kListChunk - 1;
+                if (id < vo.nch) vo.fills[id] = kListChunk;
+            }
+            const uint32_t spill = total - lc.room;
+            lc.pos = spill ? fresh + spill : 0;
+            lc.room = spill ? kListChunk - spill : 0;
+        }
+        __syncwarp();
+        return;
+    }
+    __syncwarp();  // the stage is read before the next step refills it
+    if (total < lc.room) {
+        lc.pos += total;
+        lc.room -= total;
+    } else {  // total == room: the open chunk is full
+        if (lane == 0) {
+            const unsigned long long id = (lc.pos + lc.room) / kListChunk - 1;
+            if (id < vo.nch) vo.fills[id] = kListChunk;
+        }
+        lc.pos = 0;
+        lc.room = 0;
     }
 }
 
@@ -395,7 +540,7 @@ __device__ __forceinline__ void lookup_step(const Set &set, const uint32_t (&w)[
 // then the ragged end in one bounds-checked step of U x 32 positions, or in
 // steps of 64 positions (kFineTail: pays where lookups are expensive);
 // positions below `split` are the A part.
-template <int U, bool kFineTail = false, int kM = 0, class Set>
+template <int U, bool kFineTail = false, int kM = 0, bool kStage = false, class Set>
 __device__ __forceinline__ uint32_t probe_row(const Set &set, const uint32_t *__restrict__ adj2, unsigned long long b,
                                               uint32_t j_lo, uint32_t j_hi, uint32_t split, Acc &acc,
                                               const VertexOut &vo = VertexOut{}, ListCtx *lc = nullptr) {
@@ -410,12 +555,7 @@ __device__ __forceinline__ uint32_t probe_row(const Set &set, const uint32_t *__
         for (int i = 0; i < U; ++i) w[i] = __ldg(row + j0 + (uint32_t)i * 32u);
         lookup_step<U>(set, w, hit);
         if constexpr (kM == 1) credit_third<U>(hit, w, vo);
-        if constexpr (kM == 2) {
-            uint32_t vr[U];
-#pragma unroll
-            for (int i = 0; i < U; ++i) vr[i] = lc->v;
-            emit_step<U>(hit, w, vr, vo, *lc);
-        }
+        if constexpr (kM == 2) emit_step<U, false, kStage>(hit, w, w, vo, *lc);
         count_step<U>(hit, j0, split, lane, same, cross);
     }
     constexpr int T = kFineTail ? 2 : U;
@@ -429,12 +569,7 @@ __device__ __forceinline__ uint32_t probe_row(const Set &set, const uint32_t *__
         }
         lookup_step<T>(set, w, hit);
         if constexpr (kM == 1) credit_third<T>(hit, w, vo);
-        if constexpr (kM == 2) {
-            uint32_t vr[T];
-#pragma unroll
-            for (int i = 0; i < T; ++i) vr[i] = lc->v;
-            emit_step<T>(hit, w, vr, vo, *lc);
-        }
+        if constexpr (kM == 2) emit_step<T, false, kStage>(hit, w, w, vo, *lc);
         count_step<T>(hit, j0, split, lane, same, cross);
     }
     acc.same += same;
@@ -491,7 +626,7 @@ __device__ __forceinline__ void probe_flat(const Set &set, const uint32_t *__res
             if constexpr (kM != 0) vr[i] = sv[r];
         }
         lookup_step<U>(set, w, hit);
-        if constexpr (kM == 2) emit_step<U>(hit, w, vr, vo, *lc);
+        if constexpr (kM == 2) emit_step<U, true, false>(hit, w, vr, vo, *lc);
 #pragma unroll
         for (int i = 0; i < U; ++i) {
             same += hit[i] && in_a[i];
@@ -665,6 +800,9 @@ __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__
                                                                          (set_bytes + kWarpMetaBytes));
         priv_begin(vo);
     }
+    ListCtx lc;
+    const unsigned long long gw = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    if constexpr (kM == 2) load_list_state(vo, lc, gw);  // no stage: lanes write their own hits
     const long long t_start = clock64();
     for (;;) {
         unsigned long long k = 0;
@@ -684,13 +822,7 @@ __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__
         const uint32_t su = (uint32_t)(rp[u + 1] - hb);
         const uint4 *rec = erec + eoff[u];
         const uint32_t k_lo = (uint32_t)((uint64_t)task.y * fu / nt), k_hi = (uint32_t)((uint64_t)(task.y + 1) * fu / nt);
-        ListCtx lc;
-        if constexpr (kM == 2) {
-            lc.base = vo.off[k];
-            lc.end = vo.off[k + 1];
-            lc.u = u;
-            lc.err = &ctl->error;
-        }
+        lc.u = u;
         if (task.x != cur_row) {  // tasks of one row reuse its table
             __syncwarp();
             if constexpr (kCuckoo) {
@@ -763,21 +895,18 @@ __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__
                 __syncwarp();
             }
         }
-        if (groups.n_groups || kM == 1 || vo.task_hits) {
+        if (groups.n_groups || kM == 1) {
             const unsigned long long found = warp_sum(acc.same + acc.cross - before);
-            if (lane == 0) {
-                if (vo.task_hits) vo.task_hits[k] = found;
-                if (groups.n_groups && found) atomicAdd(&groups.counts[group_of(groups, u)], found);
-                if constexpr (kM == 1)
-                    if (found) atomicAdd(vo.tid + u, found);
+            if (lane == 0 && found) {
+                if (groups.n_groups) atomicAdd(&groups.counts[group_of(groups, u)], found);
+                if constexpr (kM == 1) atomicAdd(vo.tid + u, found);
             }
         }
-        if constexpr (kM == 2)
-            if (lane == 0 && lc.base + lc.local != lc.end) atomicOr(&ctl->error, kGuardList);
     }
     flush(acc, ctl, 0, lane == 0 ? build : 0, lane == 0 ? done : 0);
     if (lane == 0 && inserts) atomicAdd(&ctl->cls_inserts[0], inserts);
     if constexpr (kM == 1) priv_end(vo);
+    if constexpr (kM == 2) store_list_state(vo, lc, gw);
 }
 
 // ---------------------------------------------------------------------------- tiny class
@@ -855,10 +984,9 @@ __global__ void __launch_bounds__(256) k_isect_tiny(const uint32_t *__restrict__
         unsigned long long probes = 0;
         ListCtx lc;
         if constexpr (kM == 2) {
-            lc.base = vo.off[i];
-            lc.end = vo.off[i + 1];
+            lc.base = vo.base + vo.off[i];
+            lc.end = vo.base + vo.off[i + 1];
             lc.u = u;
-            lc.err = &ctl->error;
         }
         for (uint32_t k = 0; k < fu; ++k) {
             const uint32_t v = __ldg(adj2 + ub + k);
@@ -884,7 +1012,7 @@ __global__ void __launch_bounds__(256) k_isect_tiny(const uint32_t *__restrict__
             if (same + cross) atomicAdd(vo.tid + u, (unsigned long long)(same + cross));
         if (vo.task_hits) vo.task_hits[i] = same + cross;
         if constexpr (kM == 2)
-            if (lc.base + lc.local != lc.end) atomicOr(&ctl->error, kGuardList);
+            if (lc.base + lc.local != lc.end) atomicOr(vo.err, kGuardList);
     }
     const unsigned long long b = warp_sum(build), d = warp_sum(done);
     flush(acc, ctl, 3, lane_id() == 0 ? b : 0, lane_id() == 0 ? d : 0);
@@ -1008,7 +1136,7 @@ __device__ __forceinline__ void probe_slice(const Set &set, const SliceSmem &S, 
             const uint32_t hi = __shfl_sync(0xFFFFFFFFu, j_hi, t);
             const uint32_t ht = __shfl_sync(0xFFFFFFFFu, h, t);
             if constexpr (kM == 2) lc.v = __shfl_sync(0xFFFFFFFFu, vid, t);
-            uint32_t got = probe_row<Set::kUnroll, Set::kFineTail, kM>(set, adj2, bt, lo, hi, ht, acc, vo, &lc);
+            uint32_t got = probe_row<Set::kUnroll, Set::kFineTail, kM, true>(set, adj2, bt, lo, hi, ht, acc, vo, &lc);
             if constexpr (kM == 1) {
                 got = warp_sum(got);
                 const uint32_t vt = __shfl_sync(0xFFFFFFFFu, vid, t);
@@ -1021,7 +1149,7 @@ __device__ __forceinline__ void probe_slice(const Set &set, const SliceSmem &S, 
 struct TaskSmem {
     uint2 task;
     unsigned int next;
-    unsigned int cursor;  // listing: triangles of the task written so far
+    unsigned int pad;
     unsigned long long found;
     unsigned long long k;                     // index of the task in its class's list
     unsigned long long chunk_pos, chunk_end;  // this block's current run of consecutive tasks
@@ -1049,48 +1177,25 @@ __device__ __forceinline__ bool next_task(Ctl *ctl, int c, unsigned long long fi
             ts->k = k;
         }
         ts->next = 0;
-        ts->cursor = 0;
         ts->found = 0;
     }
     __syncthreads();
     return ts->task.x != 0xFFFFFFFFu;
 }
 
-// Listing position of the current task of a block (cursor shared by its warps).
-template <int kM>
-__device__ __forceinline__ ListCtx list_ctx(const VertexOut &vo, TaskSmem &ts, uint32_t u, Ctl *ctl) {
-    ListCtx lc;
-    if constexpr (kM == 2) {
-        lc.base = vo.off[ts.k];
-        lc.end = vo.off[ts.k + 1];
-        lc.u = u;
-        lc.shared = &ts.cursor;
-        lc.err = &ctl->error;
-    }
-    return lc;
-}
-
 // End of a block's task: the triangles it found (this thread's share is
-// `mine`) go to the group counts, the hashed vertex's count, the task's hit
-// record; a listing task checks that it filled its slots exactly.
+// `mine`) go to the group counts and to the hashed vertex's count.
 template <int kM>
 __device__ __forceinline__ void finish_task(unsigned long long mine, const GroupSpec &groups, const VertexOut &vo,
-                                            TaskSmem &ts, uint32_t u, Ctl *ctl) {
-    if (groups.n_groups || kM == 1 || vo.task_hits) {
+                                            TaskSmem &ts, uint32_t u) {
+    if (groups.n_groups || kM == 1) {
         const unsigned long long found = warp_sum(mine);
         if (lane_id() == 0 && found) atomicAdd(&ts.found, found);
         __syncthreads();
-        if (threadIdx.x == 0) {
-            if (vo.task_hits) vo.task_hits[ts.k] = ts.found;
-            if (ts.found) {
-                if (groups.n_groups) atomicAdd(&groups.counts[group_of(groups, u)], ts.found);
-                if constexpr (kM == 1) atomicAdd(vo.tid + u, ts.found);
-            }
+        if (threadIdx.x == 0 && ts.found) {
+            if (groups.n_groups) atomicAdd(&groups.counts[group_of(groups, u)], ts.found);
+            if constexpr (kM == 1) atomicAdd(vo.tid + u, ts.found);
         }
-    }
-    if constexpr (kM == 2) {
-        __syncthreads();
-        if (threadIdx.x == 0 && vo.off[ts.k] + ts.cursor != vo.off[ts.k + 1]) atomicOr(&ctl->error, kGuardList);
     }
 }
 
@@ -1130,6 +1235,13 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
         priv_begin(vo);
     }
     init_task_smem(&ts);
+    ListCtx lc;
+    const unsigned long long gw = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if constexpr (kM == 2) {
+        lc.stage = reinterpret_cast<uint32_t *>(tab + (kCuckoo ? 8ull : 16ull) * table_units) +
+                   (size_t)(threadIdx.x >> 5) * kStageSlots;
+        load_list_state(vo, lc, gw);
+    }
     const long long t_start = clock64();
     while (next_task(ctl, 1, first, last, chunk, tasks, &ts, t_start)) {
         const uint2 task = ts.task;
@@ -1159,14 +1271,15 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
             ++done;
         }
         const unsigned long long before = acc.same + acc.cross;
-        ListCtx lc = list_ctx<kM>(vo, ts, u, ctl);
+        lc.u = u;
         if constexpr (kCuckoo) probe_slice<kM>(C, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);
         else probe_slice<kM>(T, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);
-        finish_task<kM>(acc.same + acc.cross - before, groups, vo, ts, u, ctl);
+        finish_task<kM>(acc.same + acc.cross - before, groups, vo, ts, u);
     }
     flush(acc, ctl, 1, threadIdx.x == 0 ? build : 0, threadIdx.x == 0 ? done : 0);
     if (threadIdx.x == 0 && inserts) atomicAdd(&ctl->cls_inserts[1], inserts);
     if constexpr (kM == 1) priv_end(vo);
+    if constexpr (kM == 2) store_list_state(vo, lc, gw);
 }
 
 // Set the bits of the hashed sets of hub rows rows[i0 .. i0+g) into bitmaps
@@ -1213,6 +1326,12 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
     unsigned long long build = 0, done = 0, inserts = 0;
     uint32_t cur_row = 0xFFFFFFFFu;
     init_task_smem(&ts);
+    ListCtx lc;
+    const unsigned long long gw = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if constexpr (kM == 2) {
+        lc.stage = filter + filter_words + (size_t)(threadIdx.x >> 5) * kStageSlots;
+        load_list_state(vo, lc, gw);
+    }
     const long long t_start = clock64();
     while (next_task(ctl, 2, first, last, chunk, tasks, &ts, t_start)) {
         const uint2 task = ts.task;
@@ -1242,13 +1361,14 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
         }
         const HubSet H{filter, bits + (uint64_t)(task.x - i0) * words, fshift};
         const unsigned long long before = acc.same + acc.cross;
-        ListCtx lc = list_ctx<kM>(vo, ts, u, ctl);
+        lc.u = u;
         probe_slice<kM>(H, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);
-        finish_task<kM>(acc.same + acc.cross - before, groups, vo, ts, u, ctl);
+        finish_task<kM>(acc.same + acc.cross - before, groups, vo, ts, u);
     }
     flush(acc, ctl, 2, threadIdx.x == 0 ? build : 0, threadIdx.x == 0 ? done : 0);
     if (threadIdx.x == 0 && inserts) atomicAdd(&ctl->cls_inserts[2], inserts);
     if constexpr (kM == 1) priv_end(vo);
+    if constexpr (kM == 2) store_list_state(vo, lc, gw);
 }
 
 uint32_t pow2_at_least(uint64_t x, uint32_t lo) {
@@ -1277,29 +1397,36 @@ size_t block_kernel_smem(const Tuning &tu) {
 }
 size_t hub_kernel_smem(const Tuning &tu) { return slice_smem_bytes(tu.max_v) + (1ull << tu.hub_filter_log2) / 8; }
 
+// Shared memory one block may opt into on sm_103a.
+constexpr size_t kSmemLimit = 227 * 1024;
+
 tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
     (void)n;
     cudaStream_t s = ctx->stream;
     const Tuning &tu = ctx->tune;
     // what the kernels do with the triangles: 0 count, 1 per-vertex counts,
-    // 2 listing (the counting pass of a listing is mode 0 with hit records)
-    const int mode = b.vcount ? 1 : (b.list_out ? 2 : 0);
+    // 2 listing (phase 1: the tiny class counts and records, the others
+    // write; phase 2: the tiny class writes, the others do not run)
+    const int mode = b.vcount ? 1 : (b.list_phase ? 2 : 0);
     VertexOut vo{b.vcount, b.vcount_rank};
     vo.out = b.list_out;
+    vo.cap = b.list_cap;
+    vo.ovf = b.ovf;
+    vo.ovf_cap = b.ovf_cap;
+    vo.cursor = &ctx->d_ctl->list_cursor;
+    vo.fills = b.fills;
+    vo.nch = b.nch;
+    vo.wstate = b.wstate;
+    vo.wstate_len = b.wstate_len;
+    vo.err = &ctx->d_ctl->error;
     vo.inv = b.inv;
     const Ctl &h = *ctx->h_ctl;  // pulled after planning
-    // hit records / output offsets: [tiny rows | warp tasks | block tasks | hub tasks]
-    const unsigned long long cbase[4] = {0, h.n_rows[3], h.n_rows[3] + h.n_tasks[0],
-                                         h.n_rows[3] + h.n_tasks[0] + h.n_tasks[1]};
-    auto vo_for = [&](int slot) {
-        VertexOut v = vo;
-        if (b.hits) {
-            if (mode == 2) v.off = b.hits + cbase[slot];
-            else v.task_hits = b.hits + cbase[slot];
-        }
-        return v;
-    };
     const size_t priv = mode == 1 ? 8ull * kPrivRanks : 0;
+    // warps of a listing launch: at most one open chunk state each
+    auto list_grid = [&](uint64_t grid, uint32_t warps_per_block) {
+        if (mode == 2 && grid * warps_per_block > b.wstate_len) grid = b.wstate_len / warps_per_block;
+        return grid;
+    };
     // ev[4..7] bracket the warp, block and hub kernels
     // tiny rows: one thread each (this count's share of them)
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[8], s));
@@ -1307,15 +1434,27 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
     const uint32_t lo3 = (uint32_t)((uint64_t)nt3 * ctx->shard / ctx->nshards);
     const uint32_t hi3 = (uint32_t)((uint64_t)nt3 * (ctx->shard + 1) / ctx->nshards);
     if (hi3 > lo3) {
+        const int tmode = b.list_phase == 1 ? 0 : mode;
         const size_t smem = 4ull * tu.tiny_cap * 256 + priv;
-        auto tiny = mode == 0 ? k_isect_tiny<0> : mode == 1 ? k_isect_tiny<1> : k_isect_tiny<2>;
+        auto tiny = tmode == 0 ? k_isect_tiny<0> : tmode == 1 ? k_isect_tiny<1> : k_isect_tiny<2>;
         TC_CUDA(ctx, cudaFuncSetAttribute(tiny, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const uint32_t grid = std::min<uint32_t>((hi3 - lo3 + 255) / 256, (uint32_t)ctx->num_sms * 8u);
+        VertexOut vt = vo;
+        if (b.list_phase == 1) vt.task_hits = b.hits;
+        if (b.list_phase == 2) {
+            vt.off = b.hits;
+            vt.base = b.tiny_base;
+        }
         tiny<<<grid, 256, smem, s>>>(b.rows[3], lo3, hi3, b.rp, b.adj2, b.fcnt, b.gcnt, ctx->d_ctl, tu.tiny_cap,
-                                     b.groups, vo_for(0));
+                                     b.groups, vt);
         note_launch(ctx);
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[9], s));
+    if (b.list_phase == 2) {  // the other classes wrote in phase 1
+        ctx->isect_flags |= hi3 > lo3 ? 8u : 0u;
+        TC_CUDA(ctx, cudaGetLastError());
+        return TC_OK;
+    }
     // this count's share of every class's task list (all of it unless sharded)
     auto share = [&](unsigned long long total, unsigned long long *lo, unsigned long long *hi) {
         *lo = total * ctx->shard / ctx->nshards;
@@ -1328,6 +1467,7 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[4], s));
     if (hi0 > lo0) {
         const size_t smem = warp_kernel_smem(tu) + priv;
+        if (smem > kSmemLimit) return set_error(ctx, TC_ERR_INVALID, "tuning leaves no shared memory for this mode");
         auto kern = tu.table_kind == 0
                         ? (mode == 0 ? k_isect_warp<true, 0> : mode == 1 ? k_isect_warp<true, 1> : k_isect_warp<true, 2>)
                         : (mode == 0 ? k_isect_warp<false, 0>
@@ -1339,15 +1479,17 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         uint64_t grid = (uint64_t)ctx->num_sms * per_sm;
         const uint64_t need = (hi0 - lo0 + tu.warps_per_block - 1) / tu.warps_per_block;
         if (grid > need) grid = need;
+        grid = list_grid(grid, tu.warps_per_block);
         kern<<<(unsigned)grid, 32 * tu.warps_per_block, smem, s>>>(b.tasks[0], b.rows[0], b.ntask[0], b.rp, b.adj2,
                                                                    b.fcnt, b.eoff, b.erec, ctx->d_ctl,
                                                                    warp_table_units(tu), tu.flat_cap, lo0, hi0,
-                                                                   b.groups, vo_for(1));
+                                                                   b.groups, vo);
         note_launch(ctx);
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[5], s));
     if (hi1 > lo1) {
-        const size_t smem = block_kernel_smem(tu) + priv;
+        const size_t smem = block_kernel_smem(tu) + priv + (mode == 2 ? 4ull * kStageSlots * (tu.block_threads / 32) : 0);
+        if (smem > kSmemLimit) return set_error(ctx, TC_ERR_INVALID, "tuning leaves no shared memory for this mode");
         auto kern = tu.table_kind == 0 ? (mode == 0   ? k_isect_block<true, 0>
                                           : mode == 1 ? k_isect_block<true, 1>
                                                       : k_isect_block<true, 2>)
@@ -1360,10 +1502,11 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         if (per_sm < 1) per_sm = 1;
         uint64_t grid = (uint64_t)ctx->num_sms * per_sm;
         if (grid > hi1 - lo1) grid = hi1 - lo1;
+        grid = list_grid(grid, tu.block_threads / 32);
         const unsigned long long chunk = std::max<unsigned long long>(1, (hi1 - lo1) / (grid * 8));
         kern<<<(unsigned)grid, tu.block_threads, smem, s>>>(b.tasks[1], b.rows[1], b.ntask[1], b.rp, b.adj2, b.fcnt,
                                                             b.eoff, b.erec, ctx->d_ctl, tu.max_v, block_table_units(tu),
-                                                            chunk, lo1, hi1, b.groups, vo_for(2));
+                                                            chunk, lo1, hi1, b.groups, vo);
         note_launch(ctx);
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[6], s));
@@ -1373,7 +1516,8 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         std::vector<unsigned long long> pref(nh + 1);
         TC_CUDA(ctx, cudaMemcpyAsync(pref.data(), b.tpref[2], 8ull * (nh + 1), cudaMemcpyDeviceToHost, s));
         TC_CUDA(ctx, cudaStreamSynchronize(s));
-        const size_t smem = hub_kernel_smem(tu) + priv;
+        const size_t smem = hub_kernel_smem(tu) + priv + (mode == 2 ? 4ull * kStageSlots * (tu.hub_threads / 32) : 0);
+        if (smem > kSmemLimit) return set_error(ctx, TC_ERR_INVALID, "tuning leaves no shared memory for this mode");
         auto hub = mode == 0 ? k_isect_hub<0> : mode == 1 ? k_isect_hub<1> : k_isect_hub<2>;
         TC_CUDA(ctx, cudaFuncSetAttribute(hub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
@@ -1390,12 +1534,13 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
                                                                  b.hub_words);
             uint64_t grid = (uint64_t)ctx->num_sms * per_sm;
             if (grid > last - first) grid = last - first;
+            grid = list_grid(grid, tu.hub_threads / 32);
             const unsigned long long chunk = std::max<unsigned long long>(1, (last - first) / (grid * 4));
             hub<<<(unsigned)grid, tu.hub_threads, smem, s>>>(b.tasks[2], first, last, b.rows[2], b.ntask[2], i0,
                                                                      b.rp, b.adj2, b.fcnt, b.eoff, b.erec, ctx->d_ctl,
                                                                      b.hub_bits,
                                                                      b.hub_words, tu.max_v, chunk, tu.hub_filter_log2,
-                                                                     b.groups, vo_for(3));
+                                                                     b.groups, vo);
             note_launch(ctx, 2);
         }
     }

@@ -5,6 +5,9 @@
 
 namespace tc {
 
+// Listing: output slots a warp takes at a time (see isect.cu).
+constexpr uint32_t kListChunk = 2048;
+
 // All scratch of one count, carved from the context arena.  Sizes: n vertices,
 // S = row_ptr[n] CSR slots.
 struct PipeBufs {
@@ -56,11 +59,23 @@ struct PipeBufs {
     // array) and by rank (scratch); null otherwise
     unsigned long long *vcount = nullptr;
     unsigned long long *vcount_rank = nullptr;
-    // listing: hit records of every task (counting pass), scanned in place
-    // into output offsets; the triples; rank -> id (null under the id order)
-    unsigned long long *hits = nullptr;
+    // listing (tc_list_triangles).  Phase 1: the tiny class counts and
+    // records its rows' hits (hits), the other classes write their triangles
+    // into chunks; phase 2: the tiny class writes at tiny_base + its scanned
+    // offsets.  Triple positions run through list_out (list_cap triples),
+    // then the overflow area (ovf_cap triples).
+    int list_phase = 0;
+    unsigned long long *hits = nullptr;       // [rows of the tiny class + 1]
     uint32_t *list_out = nullptr;
-    uint32_t *inv = nullptr;
+    unsigned long long list_cap = 0;
+    uint32_t *ovf = nullptr;
+    unsigned long long ovf_cap = 0;
+    uint32_t *fills = nullptr;                // [nch] filled slots per chunk
+    unsigned long long nch = 0;
+    ulonglong2 *wstate = nullptr;             // [wstate_len] open chunk of every warp
+    unsigned long long wstate_len = 0;
+    unsigned long long tiny_base = 0;
+    uint32_t *inv = nullptr;                  // [n] rank -> id (null under the id order)
 };
 
 tc_status compute_levels(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t slots);
@@ -70,6 +85,12 @@ tc_status given_levels(tc_ctx *ctx, const PipeBufs &b, uint32_t n, const uint32_
 tc_status selftest_barrier(tc_ctx *ctx, uint32_t timeout_ms);
 // rank of every vertex in the working order, packed with its level (lv)
 tc_status compute_ranks(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_deg);
+// Listing: close the open chunks, then move the triangles written past the
+// first t_big positions into the gaps below it (list.cu).  g_end = the chunk
+// cursor after the listing pass.
+tc_status list_compact(tc_ctx *ctx, const PipeBufs &b, unsigned long long t_big, unsigned long long g_end,
+                       unsigned long long *scratch, unsigned long long *scan_tmp);
+size_t list_compact_scratch(unsigned long long nch);
 // Algorithm 3 over the CSR as given, after the levels and ranks (alg3.cu).
 tc_status intersect_alg3(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t slots);
 // partition, orientation, compaction, classification and per-class task counts

@@ -70,6 +70,7 @@ struct Ctl {
     unsigned int n_big;              // rows whose A part the block sorter sorts
     unsigned int n_huge;             // rows of very high degree filled by a block each
     unsigned int pad[2];
+    unsigned long long list_cursor;  // listing: next free chunk position
 };
 
 // ----------------------------------------------------------------------------- arena
