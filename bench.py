@@ -45,6 +45,10 @@ WORKLOADS = {
     "grid4096": dict(kind="grid", rows=4096, cols=4096, p=0.3, seed=4),
 }
 CPU_SAMPLE = dict(kind="rmat", scale=18, edge_factor=16, seed=1)
+# DRAM bytes (read + write) of one launch of the dominant kernel, from a one-pass
+# ncu capture of this exact command (profiles/k_isect_block_rmat24_dram.md);
+# valid only for the kernel as captured: plain count, default tuning.
+MEASURED_TRAFFIC = {("rmat24", "k_isect_block"): 353.63e9}
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -417,7 +421,10 @@ def main():
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
     whole_gbs = mean("alg_bytes") / (ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": (MEASURED_TRAFFIC.get((args.workload, dom))
+                            if not (args.list_triangles or args.vertex_counts or args.alg3 or args.autotune)
+                            else None),
                 "bytes_per_launch": dom_bytes, "ms_per_launch": dom_ms,
                 "whole_count": {"alg_bytes": mean("alg_bytes"), "achieved": whole_gbs, "frac": whole_gbs / peak}}
 
