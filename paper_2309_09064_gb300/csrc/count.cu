@@ -89,6 +89,7 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
                          const ListSpec *list, bool alg3) {
     const uint32_t n = g.n;
     cudaStream_t s = ctx->stream;
+    const uint32_t launches0 = ctx->launches;  // the context's running total before this call
     uint64_t hub_words = 0;
     uint32_t hub_maps = 0;
     const size_t need = pipeline_bytes(ctx, n, g.slots, g.max_deg, levels_out == nullptr, &hub_words, &hub_maps) +
@@ -309,7 +310,7 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
                 else cudaEventElapsedTime(&stats->ms_class[3], ctx->ev[8], ctx->ev[9]);
             }
         }
-        stats->launches = ctx->launches;
+        stats->launches = ctx->launches - launches0;
         stats->reserved = 0;
         stats->isect_bytes = is;
         stats->alg_bytes = lv + rw + is + 8;

@@ -115,7 +115,7 @@ struct tc_ctx {
     tc::Ctl *d_ctl = nullptr;
     tc::Ctl *h_ctl = nullptr;   // pinned
     cudaEvent_t ev[10] = {};
-    uint32_t launches = 0;    // kernels launched by the current call
+    uint32_t launches = 0;    // kernels launched on this context so far (a call reports its own difference)
     uint32_t isect_flags = 0; // which intersection kernels the last count launched (1 warp, 2 block, 4 hub)
     uint32_t shard = 0, nshards = 1;  // intersection tasks of this count: share `shard` of `nshards`
     uint64_t alloc_calls = 0;         // device allocations made by this context

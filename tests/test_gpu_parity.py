@@ -214,9 +214,12 @@ def test_torch_stream(tc):
 def test_repeated_counts_are_identical(tc, ctx):
     n, s, d = gg.rmat(13, 16, seed=2)
     g = tc.tc_build_csr(ctx, n, s, d)
-    res = {tc.tc_count(ctx, g)[0] for _ in range(5)}
+    runs = [tc.tc_count(ctx, g) for _ in range(5)]
     tc.tc_graph_free(g)
-    assert len(res) == 1
+    assert len({T for T, _ in runs}) == 1
+    # stats.launches counts the kernels of one call: the same for every repeat
+    launches = {st["launches"] for _, st in runs}
+    assert len(launches) == 1 and 0 < launches.pop() < 1000
 
 
 # ------------------------------------------------------------------------- batched and served forms
