@@ -26,11 +26,11 @@ CANDIDATES = [
     {"block_cap": 8192, "max_v": 1024},
     {"block_cap": 8192, "max_v": 1024, "hub_filter_log2": 19},
     {"hub_filter_log2": 19, "max_v": 1024},
-    {"block_cap": 8192, "max_v": 1024, "hub_filter_log2": 19, "hub_group": 16},
+    {"block_cap": 8192, "max_v": 1024, "hub_filter_log2": 19, "hub_group": 8},
     {"block_cap": 8192, "max_v": 1024, "hub_filter_log2": 19, "hub_group": 4},
     {"warp_cap": 512},
     {"warp_cap": 2048, "warps_per_block": 4},
-    {"task_work": 262144, "hub_task_work": 524288},
+    {"task_work": 1048576, "hub_task_work": 262144, "hub_group": 8},
     {"task_work": 65536, "hub_task_work": 131072},
     {"task_work": 524288, "hub_task_work": 1048576},
     {"block_threads": 512, "hub_threads": 512, "block_cap": 8192, "max_v": 1024, "hub_filter_log2": 19},
