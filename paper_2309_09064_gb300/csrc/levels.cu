@@ -331,16 +331,20 @@ __device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned nblocks, long lo
 
 // Persistent top-down BFS for small frontiers (high-diameter graphs): one
 // launch runs level after level, one grid barrier per level, until the
-// frontier is empty or leaves [min_f, max_f] x [0, max_e]; then the host
-// takes over again.  A thread expands a frontier vertex of degree <= 32 on its
-// own; larger rows are expanded by the whole warp, one at a time.  Counter slots rotate mod 3 (level L reads slot s,
-// writes s+1, and s+2 is cleared for level L+1); queues alternate.
+// frontier is empty or leaves [min_f, max_f] x [0, max_e], or its mean
+// degree passes max_avg (a high-degree vertex would hold up the one warp
+// that expands it; the edge-balanced kernel spreads it over the GPU); then
+// the host takes over again.  A frontier vertex of degree <= 32 is expanded
+// by a group of G lanes (G = the threads the grid has per frontier vertex,
+// a power of two up to 32; one thread when the frontier is large); larger
+// rows by the whole warp, one at a time.  Counter slots rotate mod 3 (level L reads
+// slot s, writes s+1, and s+2 is cleared for level L+1); queues alternate.
 __global__ void __launch_bounds__(512) k_bfs_persist(uint32_t *__restrict__ q0, uint32_t *__restrict__ q1,
                                                      const uint64_t *__restrict__ rp,
                                                      const uint32_t *__restrict__ col,
                                                      const uint32_t *__restrict__ deg, uint32_t *L, Ctl *ctl,
                                                      uint32_t slot, uint32_t queue, uint32_t level, uint32_t max_f,
-                                                     unsigned long long max_e, uint32_t min_f) {
+                                                     unsigned long long max_e, uint32_t min_f, uint32_t max_avg) {
     const unsigned lane = lane_id();
     const unsigned gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -353,7 +357,9 @@ __global__ void __launch_bounds__(512) k_bfs_persist(uint32_t *__restrict__ q0, 
     for (;;) {
         const uint32_t fcount = vcount[slot];
         const unsigned long long fedges = vedges[slot];
-        if (fcount == 0 || fcount > max_f || fedges > max_e || fcount < min_f) break;
+        if (fcount == 0 || fcount > max_f || fedges > max_e || fcount < min_f ||
+            fedges > (unsigned long long)fcount * max_avg)
+            break;
         const uint32_t s1 = slot == 2 ? 0 : slot + 1, s2 = s1 == 2 ? 0 : s1 + 1;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             ctl->fr_count[s2] = 0;
@@ -363,22 +369,47 @@ __global__ void __launch_bounds__(512) k_bfs_persist(uint32_t *__restrict__ q0, 
         uint32_t *qn = queue ? q0 : q1;
         unsigned long long edges = 0;
         const uint32_t nthreads = nwarps * 32u, gtid = gwarp * 32u + lane;
-        const uint32_t f_round = (fcount + 31u) & ~31u;
-        for (uint32_t i = gtid; i < f_round; i += nthreads) {
+        // Lanes per frontier vertex: as many as the grid has to spare (a power
+        // of two up to 32), so that the neighbours of a small frontier are
+        // visited in parallel rather than one after another by one thread.
+        uint32_t G = 1;
+        while (G < 32 && (unsigned long long)fcount * (G * 2) <= nthreads) G <<= 1;
+        const uint32_t sub = lane & (G - 1), ngroups = nthreads / G, vt = gtid / G;
+        for (uint32_t r0 = 0; r0 < fcount; r0 += ngroups) {
+            const uint32_t i = r0 + vt;
             const bool valid = i < fcount;
             const uint32_t v = valid ? q[i] : 0u;
             const uint64_t b = valid ? rp[v] : 0, e = valid ? rp[v + 1] : 0;
             const bool small = e - b <= 32;
-            if (small) {
-                for (uint64_t j = b; j < e; ++j) {
-                    const uint32_t w = col[j];
-                    if (L[w] == kUnvisited && atomicCAS(&L[w], kUnvisited, level + 1) == kUnvisited) {
-                        qn[atomicAdd(&ctl->fr_count[s1], 1u)] = w;
+            if (G == 1) {
+                if (small) {
+                    for (uint64_t j = b; j < e; ++j) {
+                        const uint32_t w = col[j];
+                        if (L[w] == kUnvisited && atomicCAS(&L[w], kUnvisited, level + 1) == kUnvisited) {
+                            qn[atomicAdd(&ctl->fr_count[s1], 1u)] = w;
+                            edges += deg[w];
+                        }
+                    }
+                }
+            } else {  // the G lanes of a group take their vertex's neighbours in turn
+                const uint32_t d = valid && small ? (uint32_t)(e - b) : 0u;
+                const uint32_t kmax = __reduce_max_sync(0xFFFFFFFFu, (d + G - 1) / G);
+                for (uint32_t k = 0; k < kmax; ++k) {
+                    const uint32_t j = k * G + sub;
+                    bool claim = false;
+                    uint32_t w = 0;
+                    if (j < d) {
+                        w = col[b + j];
+                        claim = L[w] == kUnvisited && atomicCAS(&L[w], kUnvisited, level + 1) == kUnvisited;
+                    }
+                    const uint32_t pos = warp_append(claim, &ctl->fr_count[s1]);
+                    if (claim) {
+                        qn[pos] = w;
                         edges += deg[w];
                     }
                 }
             }
-            unsigned big = __ballot_sync(0xFFFFFFFFu, !small);
+            unsigned big = __ballot_sync(0xFFFFFFFFu, valid && !small && sub == 0);
             while (big) {
                 const int src = __ffs(big) - 1;
                 big &= big - 1;
@@ -438,6 +469,7 @@ unsigned grid_for(uint64_t work, unsigned threads, unsigned cap) {
 
 constexpr uint32_t kPersistMaxF = 32768;          // frontier vertices (whole-grid mode)
 constexpr unsigned long long kPersistMaxE = 65536;  // frontier edges
+constexpr uint32_t kPersistMaxAvg = 256;            // mean frontier degree
 
 // Levels given by the caller: degrees, a copy of the levels, their maximum,
 // and the check that makes the count exact with them -- every edge joins
@@ -521,11 +553,15 @@ static tc_status bfs_loop(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t s
         if (!bottom_up && fedges > unexplored / 14 && fcount > 64) bottom_up = true;
         else if (bottom_up && fcount < n / 24 && fcount < prev_count) bottom_up = false;
         const uint32_t nxt = slot == 2 ? 0 : slot + 1;
-        if (!bottom_up && fcount <= kPersistMaxF && fedges <= kPersistMaxE) {
+        if (!bottom_up && fcount <= kPersistMaxF && fedges <= kPersistMaxE &&
+            fedges <= (unsigned long long)fcount * kPersistMaxAvg) {
             if (persist_blocks < 0) {
                 int per_sm = 0;
                 TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs_persist, 512, 0));
-                persist_blocks = std::max(1, std::min(per_sm, 1)) * ctx->num_sms;
+                // enough threads for the largest frontier it takes, no more: fewer
+                // blocks make the per-level grid barrier cheaper
+                persist_blocks = std::min<int>(std::max(1, std::min(per_sm, 1)) * ctx->num_sms,
+                                               (int)((kPersistMaxF + 511) / 512));
             }
             k_reset_next<<<1, 1, 0, s>>>(ctx->d_ctl, (int)nxt);
             uint32_t *q0 = b.q0, *q1 = b.q1;
@@ -534,10 +570,10 @@ static tc_status bfs_loop(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t s
             uint32_t *L = b.L;
             Ctl *ctl = ctx->d_ctl;
             uint32_t a_slot = slot, a_queue = queue, a_level = level;
-            uint32_t a_max_f = kPersistMaxF, a_min_f = 0;
+            uint32_t a_max_f = kPersistMaxF, a_min_f = 0, a_max_avg = kPersistMaxAvg;
             unsigned long long a_max_e = kPersistMaxE;
             void *args[] = {&q0, &q1, &rp, &col, &deg, &L, &ctl, &a_slot, &a_queue, &a_level, &a_max_f, &a_max_e,
-                            &a_min_f};
+                            &a_min_f, &a_max_avg};
             TC_CUDA(ctx, cudaLaunchCooperativeKernel((const void *)k_bfs_persist, dim3(persist_blocks), dim3(512),
                                                      args, 0, s));
             note_launch(ctx, 2);
