@@ -397,15 +397,16 @@ __global__ void __launch_bounds__(512) k_bfs_persist(uint32_t *__restrict__ q0, 
                 for (uint32_t k = 0; k < kmax; ++k) {
                     const uint32_t j = k * G + sub;
                     bool claim = false;
-                    uint32_t w = 0;
+                    uint32_t w = 0, dw = 0;
                     if (j < d) {
                         w = col[b + j];
+                        dw = deg[w];  // read beside L[w], not after the claim
                         claim = L[w] == kUnvisited && atomicCAS(&L[w], kUnvisited, level + 1) == kUnvisited;
                     }
                     const uint32_t pos = warp_append(claim, &ctl->fr_count[s1]);
                     if (claim) {
                         qn[pos] = w;
-                        edges += deg[w];
+                        edges += dw;
                     }
                 }
             }
