@@ -23,6 +23,7 @@ constexpr uint32_t kWarpA = 1024;     // A parts up to this size: sorted by the 
 constexpr uint32_t kSortCap = 32768;  // A parts up to this size: sorted (larger: k_sort_big); beyond: unsorted
 constexpr uint32_t kHugeRow = 8192;   // rows of higher degree: one block each (k_row_fill_huge)
 constexpr int kFillThreads = 256;
+constexpr uint32_t kFillAhead = 8;   // neighbours of a lane-owned row read ahead together
 
 // Sort buf[0..P) ascending (P a power of two) with one warp: bitonic network.
 __device__ __forceinline__ void warp_bitonic(uint32_t *buf, uint32_t P) {
@@ -90,20 +91,31 @@ __global__ void __launch_bounds__(kFillThreads) k_row_fill(uint32_t n, const uin
         const uint2 me = valid ? rank_level<kPacked>(lv, lvp, (uint32_t)x) : make_uint2(0, 0);
         if (valid && dx <= kSmallRow) {
             uint32_t fp = 0, gp = 0, ap = 0;
-            for (uint32_t j = 0; j < dx; ++j) {
-                const uint32_t y = col[b + j];
-                const uint2 q = rank_level<kPacked>(lv, lvp, y);
-                if (q.y != me.y) {
-                    adj2[b + dx - 1 - gp++] = q.x;
-                } else if (me.x < q.x) {
-                    adj2[b + fp++] = y;
-                } else {  // insert into the lane's column, descending
-                    uint32_t i = ap++;
-                    while (i > 0 && buf[(i - 1) * 32 + lane] < q.x) {
-                        buf[i * 32 + lane] = buf[(i - 1) * 32 + lane];
-                        --i;
+            for (uint32_t j0 = 0; j0 < dx; j0 += kFillAhead) {
+                // the ids and their rank/level words of kFillAhead neighbours in
+                // flight together, then the neighbours in order
+                uint32_t y[kFillAhead];
+                uint2 q[kFillAhead];
+#pragma unroll
+                for (uint32_t t = 0; t < kFillAhead; ++t) y[t] = j0 + t < dx ? col[b + j0 + t] : 0u;
+#pragma unroll
+                for (uint32_t t = 0; t < kFillAhead; ++t)
+                    q[t] = j0 + t < dx ? rank_level<kPacked>(lv, lvp, y[t]) : make_uint2(0, 0);
+#pragma unroll
+                for (uint32_t t = 0; t < kFillAhead; ++t) {
+                    if (j0 + t >= dx) break;
+                    if (q[t].y != me.y) {
+                        adj2[b + dx - 1 - gp++] = q[t].x;
+                    } else if (me.x < q[t].x) {
+                        adj2[b + fp++] = y[t];
+                    } else {  // insert into the lane's column, descending
+                        uint32_t i = ap++;
+                        while (i > 0 && buf[(i - 1) * 32 + lane] < q[t].x) {
+                            buf[i * 32 + lane] = buf[(i - 1) * 32 + lane];
+                            --i;
+                        }
+                        buf[i * 32 + lane] = q[t].x;
                     }
-                    buf[i * 32 + lane] = q.x;
                 }
             }
             for (uint32_t i = 0; i < ap; ++i) adj2[b + fp + i] = buf[i * 32 + lane];
