@@ -1151,7 +1151,6 @@ struct TaskSmem {
     unsigned int next;
     unsigned int pad;
     unsigned long long found;
-    unsigned long long k;                     // index of the task in its class's list
     unsigned long long chunk_pos, chunk_end;  // this block's current run of consecutive tasks
 };
 
@@ -1174,7 +1173,6 @@ __device__ __forceinline__ bool next_task(Ctl *ctl, int c, unsigned long long fi
             }
             const unsigned long long k = ts->chunk_pos++;
             ts->task = k < ts->chunk_end ? tasks[k] : make_uint2(0xFFFFFFFFu, 0u);
-            ts->k = k;
         }
         ts->next = 0;
         ts->found = 0;
