@@ -174,11 +174,17 @@ def run_reference(args):
     dt = (time.perf_counter() - t0) / max(args.steps, 1)
     value = m / dt
     w = WORKLOADS[args.workload]
+    # the workload's own n and m (as our arm reports them), from the oracle-built sizes stored with the tests
+    wn = wm = 0
+    gold_path = os.path.join(ROOT, "tests", "golden", "configs.json")
+    if os.path.exists(gold_path):
+        gold = json.load(open(gold_path)).get(args.workload, {})
+        wn, wm = gold.get("n", 0), gold.get("m", 0)
     line = {"metric": "edges/sec counted (exact)", "value": value, "unit": "edges/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "impl": "reference",
-            "config": config_of(args.workload, w, 0, 0, {"reference_sample": "R-MAT scale 18, seed 1"}),
+            "config": config_of(args.workload, w, wn, wm, {"reference_sample": "R-MAT scale 18, seed 1"}),
             "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
                              "sample": f"each step: oracle Algorithm 4 (serial C) on R-MAT scale 18 "
                                        f"(m={m}) of the same generator"},
