@@ -287,6 +287,7 @@ __global__ void k_count_roots(Ctl *ctl, int cur) {
 __global__ void k_reset_next(Ctl *ctl, int nxt) {
     ctl->fr_count[nxt] = 0;
     ctl->fr_edges[nxt] = 0;
+    ctl->bar_count = 0;  // a persistent launch may follow: its barriers count from zero
 }
 
 __global__ void k_after_level(Ctl *ctl, int nxt, uint32_t level) {
@@ -296,31 +297,29 @@ __global__ void k_after_level(Ctl *ctl, int nxt, uint32_t level) {
 }
 
 // Grid-wide barrier for the persistent BFS (all blocks are co-resident: the
-// kernel is launched cooperatively).  Sense by generation counter; a wait
-// gives up after `timeout_cycles` of clock time, raises the error flag and
-// returns false, so the kernel ends and the host reads TC_ERR_TIMEOUT.
-__device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned nblocks, long long timeout_cycles) {
+// kernel is launched cooperatively).  The arrival counter only grows within
+// a launch (the host zeroes it before each launch): barrier k of the launch
+// is passed once the counter reaches (k + 1) x nblocks, so an arriving block
+// adds one and waits for that count, with no generation word to reset.  A
+// wait gives up after `timeout_cycles` of clock time, raises the error flag
+// and returns false, so the kernel ends and the host reads TC_ERR_TIMEOUT.
+__device__ __forceinline__ bool grid_barrier(Ctl *ctl, unsigned nblocks, unsigned k, long long timeout_cycles) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *gen = &ctl->bar_gen;
-        const unsigned g = *gen;
-        __threadfence();
+        volatile unsigned *count = &ctl->bar_count;
+        const unsigned target = (k + 1) * nblocks;
+        __threadfence();  // this block's frontier writes before its arrival
+        atomicAdd(&ctl->bar_count, 1u);
         int ok = 1;
-        if (atomicAdd(&ctl->bar_count, 1u) == nblocks - 1) {
-            ctl->bar_count = 0;
-            __threadfence();
-            atomicAdd(&ctl->bar_gen, 1u);
-        } else {
-            const long long t0 = clock64();
-            while (*gen == g) {
-                if (clock64() - t0 > timeout_cycles) {
-                    ctl->error = 4;
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
+        const long long t0 = clock64();
+        while (*count < target) {
+            if (clock64() - t0 > timeout_cycles) {
+                ctl->error = 4;
+                ok = 0;
+                break;
             }
+            __nanosleep(32);
         }
         __threadfence();
         s_ok = ok;
@@ -354,6 +353,7 @@ __global__ void __launch_bounds__(512) k_bfs_persist(uint32_t *__restrict__ q0, 
     unsigned int add_visited = 0;
     unsigned long long add_edges = 0;
     uint32_t start_level = level;
+    unsigned bar_k = 0;  // barriers passed in this launch
     for (;;) {
         const uint32_t fcount = vcount[slot];
         const unsigned long long fedges = vedges[slot];
@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(512) k_bfs_persist(uint32_t *__restrict__ q0, 
         }
         edges = warp_sum(edges);
         if (lane == 0 && edges) atomicAdd(&ctl->fr_edges[s1], edges);
-        if (!grid_barrier(ctl, gridDim.x, 4000000000ll)) return;  // ~2 s at 2 GHz
+        if (!grid_barrier(ctl, gridDim.x, bar_k++, 4000000000ll)) return;  // ~2 s at 2 GHz
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             add_visited += vcount[s1];
             add_edges += vedges[s1];
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(512) k_bfs_persist(uint32_t *__restrict__ q0, 
 // Self-test of the bounded wait: the barrier expects one more block than the
 // grid has, so no generation change ever comes and every block times out.
 __global__ void k_barrier_selftest(Ctl *ctl, long long timeout_cycles) {
-    grid_barrier(ctl, gridDim.x + 1, timeout_cycles);
+    grid_barrier(ctl, gridDim.x + 1, 0, timeout_cycles);
 }
 
 unsigned grid_for(uint64_t work, unsigned threads, unsigned cap) {

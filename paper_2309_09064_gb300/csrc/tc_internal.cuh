@@ -66,7 +66,7 @@ struct Ctl {
     unsigned int error;              // nonzero: a device-side check failed
     unsigned int max_s2;             // largest hashed row among block-class rows / max degree
     unsigned int p_slot, p_queue, p_level;  // where the persistent BFS stopped
-    unsigned int bar_count, bar_gen;        // grid barrier of the persistent BFS
+    unsigned int bar_count, bar_spare;      // arrivals at the persistent BFS's grid barriers (this launch)
     unsigned int n_big;              // rows whose A part the block sorter sorts
     unsigned int n_huge;             // rows of very high degree filled by a block each
     unsigned int pad[2];
