@@ -362,6 +362,7 @@ __global__ void k_class_scatter(uint32_t n, const uint32_t *__restrict__ cls, ui
 // numbered e = eoff[u] + k (v = F(u)[k]) and cut into chunks of kRecChunk;
 // chunk_row[c] is the row holding edge c * kRecChunk.
 constexpr uint32_t kRecChunk = 256;
+constexpr uint32_t kRecLinear = 16;  // A parts up to this size are counted, not searched
 
 __global__ void k_chunk_rows(uint32_t n, const uint64_t *__restrict__ eoff, uint32_t *__restrict__ chunk_row) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -420,6 +421,12 @@ __global__ void k_records(uint32_t n, const uint64_t *__restrict__ eoff, const u
                 gv[i] = m.w;
                 lo[i] = 0;
                 hi[i] = av[i] <= kSortCap ? av[i] : 0;  // unsorted A: no search, p = |A(v)|
+                if (av[i] <= kRecLinear) {  // short A: count the ranks >= r, all loads at once
+                    uint32_t c = 0;
+#pragma unroll
+                    for (uint32_t j = 0; j < kRecLinear; ++j) c += j < av[i] && adj2[as[i] + j] >= r[i];
+                    lo[i] = hi[i] = c;
+                }
             }
             // first position holding a rank below r, all searches in lockstep
             for (int step = 0; step < 17; ++step) {
