@@ -126,9 +126,9 @@ typedef struct tc_tuning {
     uint32_t hub_group;        /* hub rows probed per launch, one n-bit bitmap each (1..64) */
     uint32_t hub_filter_log2;  /* hub prefilter size: 2^k bits of shared memory (10..20) */
     uint32_t hub_threads;      /* hub kernel threads (64..1024, multiple of 32) */
-    uint32_t tiny_cap;         /* s(u) <= tiny_cap (and degree <= 4 tiny_cap): one thread per row, sorted
-                                  merges instead of a table; takes precedence over the classes above
-                                  (0..64; 0 turns it off) */
+    uint32_t tiny_cap;         /* s(u) <= tiny_cap (and degree <= 4 tiny_cap, |G1(u)| <= 8): one thread per
+                                  row, sorted merges instead of a table; takes precedence over the classes
+                                  above (0..64; 0 turns it off) */
     uint32_t table_kind;        /* shared-memory sets of the warp and block classes: 0 two-choice cuckoo
                                    tables (two 32-bit loads per lookup; block_cap up to 13107), 1 bucketed
                                    tables (block_cap up to 16384) */

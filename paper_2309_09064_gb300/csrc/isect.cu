@@ -27,7 +27,7 @@
 //                                  runs); a block keeps a shared-memory
 //                                  prefilter of its set so that only
 //                                  prefilter-positive probes read the bitmap;
-//   tiny class  s(u) <= tiny_cap : one thread per row, sorted merges / scans.
+//   tiny class  s(u) <= tiny_cap (|G1(u)| <= 8) : one thread per row, sorted merges / scans.
 // Within a task, warps take probe ranges dynamically and walk each range
 // with every lane holding several independent loads.  A block keeps its table
 // (or prefilter) when its next task belongs to the same row.
@@ -953,7 +953,7 @@ __device__ __forceinline__ uint32_t scan_count(const uint32_t *a, uint32_t strid
 
 // Tiny class: one thread per row u (s(u) <= tiny_cap, deg(u) <= 4 tiny_cap,
 // so every v in F(u), which comes later in the working order, has at most
-// 4 tiny_cap neighbours too).  A(u) and G1(u) are copied to a shared column;
+// 4 tiny_cap neighbours too; and |G1(u)| <= 8, see k_class_flags).  A(u) and G1(u) are copied to a shared column;
 // for every v in F(u) the A parts (both descending) are merged -- only
 // elements ranked below u can match, since A(u) holds no other -- and the G1
 // parts compared pairwise.

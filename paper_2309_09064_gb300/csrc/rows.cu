@@ -320,9 +320,13 @@ __global__ void __launch_bounds__(1024) k_sort_big(const uint32_t *__restrict__ 
 // s <= warp_cap, class 1 (block) s <= block_cap, class 2 (hub).
 // The lists are built by a stable scan, so they (and the task lists made from
 // them) are in vertex order on every run: shards of a count agree on them.
-__global__ void k_class_flags(uint32_t n, const uint32_t *__restrict__ fcnt, const uint32_t *__restrict__ deg,
-                              uint32_t *__restrict__ cls, Ctl *ctl, uint32_t warp_cap, uint32_t block_cap,
-                              uint32_t tiny_cap) {
+// The tiny class compares the level-spanning parts pairwise (|G1(u)| x
+// |G1(v)| per edge), so it takes only rows whose G1 part is short.
+constexpr uint32_t kTinyG = 8;
+
+__global__ void k_class_flags(uint32_t n, const uint32_t *__restrict__ fcnt, const uint32_t *__restrict__ gcnt,
+                              const uint32_t *__restrict__ deg, uint32_t *__restrict__ cls, Ctl *ctl,
+                              uint32_t warp_cap, uint32_t block_cap, uint32_t tiny_cap) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     unsigned my_max = 0;
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
@@ -331,7 +335,7 @@ __global__ void k_class_flags(uint32_t n, const uint32_t *__restrict__ fcnt, con
         if (f > 0) {
             const uint32_t s = deg[x] - f;
             c = s <= warp_cap ? 0u : (s <= block_cap ? 1u : 2u);
-            if (s <= tiny_cap && deg[x] <= 4 * tiny_cap) c = 3;
+            if (s <= tiny_cap && deg[x] <= 4 * tiny_cap && gcnt[x] <= kTinyG) c = 3;
             if (c == 1 || c == 2) my_max = s > my_max ? s : my_max;
         }
         cls[x] = c;
@@ -549,8 +553,8 @@ tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_de
     k_chunk_rows<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.eoff, b.chunk_row);
     k_records<<<cap, 256, 0, s>>>(n, b.eoff, b.chunk_row, b.rp, b.adj2, b.lv, b.vmeta, b.erec, ctx->d_ctl);
     // fdeg and R are free after the levels: class of every vertex, 0/1 indicator
-    k_class_flags<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.fcnt, b.deg, b.fdeg, ctx->d_ctl, tu.warp_cap, tu.block_cap,
-                                                        tu.tiny_cap);
+    k_class_flags<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.fcnt, b.gcnt, b.deg, b.fdeg, ctx->d_ctl, tu.warp_cap,
+                                                        tu.block_cap, tu.tiny_cap);
     launches += 3;
     for (uint32_t c = 0; c < 4; ++c) {
         k_class_indicator<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.fdeg, c, b.R);
