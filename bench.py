@@ -138,21 +138,43 @@ def dist_setup():
     return world, rank, local
 
 
+def host_info():
+    """Host cores and CPU model, for the baseline's record."""
+    import platform
+    model = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu part") and not model:
+                model = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return {"cpus": os.cpu_count(), "machine": platform.machine(), "model": model}
+
+
 def cpu_baseline_run(repeats=5):
     """The CPU oracle (serial C, Algorithm 4 under the degree order) on R-MAT
-    scale 18 of the same generator: edges/s = m / mean oracle time."""
+    scale 18 of the same generator, pinned to one host core: edges/s = m /
+    mean oracle time."""
     import oracle
     n, s, d = make_tuples(CPU_SAMPLE)
     rp, col = oracle.build_csr(n, s, d)
     m = len(col) // 2
     times = []
     T = None
-    for _ in range(repeats):
-        t0 = time.perf_counter()
-        T = oracle.alg4(rp, col, True)["T"]
-        times.append(time.perf_counter() - t0)
+    old_aff = os.sched_getaffinity(0) if hasattr(os, "sched_getaffinity") else None
+    if old_aff:
+        os.sched_setaffinity(0, {min(old_aff)})
+    try:
+        for _ in range(repeats):
+            t0 = time.perf_counter()
+            T = oracle.alg4(rp, col, True)["T"]
+            times.append(time.perf_counter() - t0)
+    finally:
+        if old_aff:
+            os.sched_setaffinity(0, old_aff)
     mean = sum(times) / len(times)
-    return {"value": m / mean, "unit": "edges/s", "cores": 1, "kind": "oracle",
+    return {"value": m / mean, "unit": "edges/s", "cores": 1, "kind": "oracle", "host": host_info(),
             "sample": f"R-MAT scale 18 (n=262144, m={m}, seed 1, same generator and A-D), "
                       f"oracle Algorithm 4 (serial C, 1 thread), mean of {repeats} runs, "
                       f"{mean:.2f} s each, T={T}"}
@@ -166,12 +188,17 @@ def run_reference(args):
     n, s, d = make_tuples(CPU_SAMPLE)
     rp, col = oracle.build_csr(n, s, d)
     m = len(col) // 2
+    old_aff = os.sched_getaffinity(0) if hasattr(os, "sched_getaffinity") else None
+    if old_aff:
+        os.sched_setaffinity(0, {min(old_aff)})  # the serial oracle on one host core
     for _ in range(args.warmup):
         oracle.alg4(rp, col, True)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         oracle.alg4(rp, col, True)
     dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    if old_aff:
+        os.sched_setaffinity(0, old_aff)
     value = m / dt
     w = WORKLOADS[args.workload]
     # the workload's own n and m (as our arm reports them), from the oracle-built sizes stored with the tests
@@ -185,7 +212,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "impl": "reference",
             "config": config_of(args.workload, w, wn, wm, {"reference_sample": "R-MAT scale 18, seed 1"}),
-            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle", "host": host_info(),
                              "sample": f"each step: oracle Algorithm 4 (serial C) on R-MAT scale 18 "
                                        f"(m={m}) of the same generator"},
             "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
