@@ -147,8 +147,11 @@ tc_status tc_destroy(tc_ctx *ctx);
 const char *tc_last_error(const tc_ctx *ctx);
 /* Run subsequent work on `stream` (a cudaStream_t; NULL: the context's own). */
 tc_status tc_set_stream(tc_ctx *ctx, void *stream);
-/* Read / replace the context's tuning (TC_ERR_INVALID if out of range). */
+/* Copy the context's tuning (the launch-shape knobs above) to *out (host). */
 tc_status tc_get_tuning(const tc_ctx *ctx, tc_tuning *out);
+/* Replace the context's tuning with a copy of *t (host), used from the next
+ * count on; TC_ERR_INVALID (tuning unchanged) if a field is out of its range
+ * or the kernels' shared memory would not fit. */
 tc_status tc_set_tuning(tc_ctx *ctx, const tc_tuning *t);
 /* Bytes of device memory currently held by the context's arena. */
 tc_status tc_arena_bytes(const tc_ctx *ctx, uint64_t *bytes);

@@ -82,3 +82,12 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(cls), name
         for field, _ in cls._fields_:
             assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+def test_every_declaration_is_documented():
+    """Each entry point of include/tc.h is preceded by its own comment (arguments, layout, ownership, errors)."""
+    text = open(os.path.join(ROOT, "include", "tc.h")).read()
+    decls = list(re.finditer(r"^(?:tc_status|const char \*|void|int)\s*\*?\s*(tc_[a-z0-9_]+)\s*\(", text, flags=re.M))
+    assert len(decls) >= 20
+    undocumented = [m.group(1) for m in decls if not text[:m.start()].rstrip().endswith("*/")]
+    assert undocumented == []
