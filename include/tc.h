@@ -139,24 +139,41 @@ typedef struct tc_tuning {
 
 /* ------------------------------------------------------------------ context */
 
-/* Create a context on CUDA device `device`.  opt may be NULL (defaults). */
+/*
+ * Create a context on CUDA device `device`; opt (host, nullable: defaults) is
+ * copied.  No counterpart in the paper, whose counters are single serial
+ * functions: the context holds what Sec. III charges to every count -- the
+ * scratch memory (one grow-only device arena, reused by later counts on the
+ * context and freed by tc_destroy), the stream and the tuning.  *out gets the
+ * context; TC_ERR_CUDA if the device cannot be used, TC_ERR_OOM if host
+ * memory runs out.
+ */
 tc_status tc_create(tc_ctx **out, int device, const tc_options *opt);
-/* Destroy a context: waits for its work, frees its arena and request slots. */
+/* Destroy a context: waits for its work, frees its arena and request slots
+ * (Sec. III: all auxiliary memory is freed; nothing leaks).  Graphs made on
+ * the context must be freed first. */
 tc_status tc_destroy(tc_ctx *ctx);
-/* One-line description of the last error on this context ("" if none). */
+/* One-line description of the last error on this context ("" if none; the
+ * string is owned by the context).  No counterpart in the paper. */
 const char *tc_last_error(const tc_ctx *ctx);
-/* Run subsequent work on `stream` (a cudaStream_t; NULL: the context's own). */
+/* Run subsequent work on `stream` (a cudaStream_t owned by the caller, which
+ * must outlive its use; NULL: the context's own).  No counterpart in the
+ * paper. */
 tc_status tc_set_stream(tc_ctx *ctx, void *stream);
-/* Copy the context's tuning (the launch-shape knobs above) to *out (host). */
+/* Copy the context's tuning (the launch-shape knobs of Algorithm 4's hashed
+ * loops, above) to *out (host). */
 tc_status tc_get_tuning(const tc_ctx *ctx, tc_tuning *out);
 /* Replace the context's tuning with a copy of *t (host), used from the next
  * count on; TC_ERR_INVALID (tuning unchanged) if a field is out of its range
- * or the kernels' shared memory would not fit. */
+ * or the kernels' shared memory would not fit.  Any valid tuning gives the
+ * same exact counts (it only reshapes the hashed loops of Algorithm 4). */
 tc_status tc_set_tuning(tc_ctx *ctx, const tc_tuning *t);
-/* Bytes of device memory currently held by the context's arena. */
+/* Bytes of device memory currently held by the context's arena (*bytes,
+ * host): the auxiliary memory that Sec. III charges to the count. */
 tc_status tc_arena_bytes(const tc_ctx *ctx, uint64_t *bytes);
 
 /*
+ * No counterpart in the paper (failure handling of this library).
  * Self-test of the bounded device-wide wait used by the persistent BFS: one
  * launch waits at a grid barrier that can never complete (one arrival is
  * missing), gives up after timeout_ms (1..10000) and reports it.  Returns
@@ -171,38 +188,49 @@ tc_status tc_selftest_barrier(tc_ctx *ctx, uint32_t timeout_ms);
 
 /*
  * Build the CSR of the simple undirected graph spanned by n_tuples tuples
- * (src[i], dst[i]): both directions are added, self-loops dropped, repeats
- * removed and rows sorted (device radix sort).  src/dst are host or device
- * arrays (`where`).  Ids >= n give TC_ERR_INVALID.  The graph owns its
- * device arrays.
+ * (src[i], dst[i]): the input form of the method (Sec. I: an undirected
+ * graph G = (V, E) stored in CSR; the paper takes that CSR as given, so the
+ * build itself has no counterpart there).  Both directions are added,
+ * self-loops dropped, repeats removed and rows sorted (device radix sort).
+ * src/dst are host or device arrays (`where`), uint32_t[n_tuples] each,
+ * read only.  Ids >= n give TC_ERR_INVALID; TC_ERR_OOM if device memory runs
+ * out.  *out gets a graph that owns its device arrays (tc_graph_free).
  */
 tc_status tc_build_csr(tc_ctx *ctx, uint32_t n, uint64_t n_tuples, const uint32_t *src,
                        const uint32_t *dst, int where, tc_graph **out);
 
 /*
  * Wrap an existing CSR (row_ptr[n+1], col[row_ptr[n]]), host or device
- * (`where`).  TC_COPY copies into library memory (host input is always
- * copied); TC_BORROW keeps device pointers (caller keeps them alive and
- * unchanged).  TC_VALIDATE runs the well-formedness check and returns
- * TC_ERR_INVALID on the first violation.
+ * (`where`): the paper's input, one undirected graph in CSR (Sec. I), treated
+ * as read only (Sec. III).  TC_COPY copies into library memory (host input
+ * is always copied); TC_BORROW keeps device pointers (caller keeps them
+ * alive and unchanged).  TC_VALIDATE runs the well-formedness check
+ * (symmetric, rows ascending, no loops, no repeats, ids < n) and returns
+ * TC_ERR_INVALID on the first violation; without it a malformed CSR gives
+ * unspecified counts.  *out gets the graph (tc_graph_free).
  */
 tc_status tc_graph_from_csr(tc_ctx *ctx, uint32_t n, const uint64_t *row_ptr, const uint32_t *col,
                             int where, int flags, tc_graph **out);
 
-/* Device pointers and sizes of a graph (valid until tc_graph_free). */
+/* Device pointers and sizes of a graph (valid until tc_graph_free); any
+ * output pointer may be NULL.  No counterpart in the paper. */
 tc_status tc_graph_info(const tc_graph *g, uint32_t *n, uint64_t *slots, const uint64_t **d_row_ptr,
                         const uint32_t **d_col);
 
 /*
  * Copy a graph's CSR out: row_ptr gets n+1 offsets, col gets row_ptr[n] ids,
- * into host or device buffers (`where`) the caller owns.
+ * into host or device buffers (`where`) the caller owns.  Blocks until the
+ * copy is done.  No counterpart in the paper.
  */
 tc_status tc_graph_copy_out(tc_ctx *ctx, const tc_graph *g, uint64_t *row_ptr, uint32_t *col, int where);
 
-/* Check a graph's CSR (symmetric, ascending rows, no loops, no repeats); *ok = 1 if well formed. */
+/* Check a graph's CSR against the input the method assumes (Sec. I: a simple
+ * undirected graph -- symmetric, ascending rows, no loops, no repeats);
+ * *ok (host) = 1 if well formed, 0 otherwise. */
 tc_status tc_validate(tc_ctx *ctx, const tc_graph *g, int *ok);
 
-/* Release a graph (and its device arrays unless borrowed). */
+/* Release a graph (and its device arrays unless borrowed): the library
+ * frees what it allocated (Sec. III).  NULL is accepted. */
 tc_status tc_graph_free(tc_graph *g);
 
 /* ----------------------------------------------------------------- counting */
@@ -223,7 +251,8 @@ tc_status tc_count_levels(tc_ctx *ctx, const tc_graph *g, uint32_t *d_levels, ui
                           tc_stats *stats);
 
 /*
- * Triangles through every vertex: d_counts (device uint64_t[n], written by
+ * Triangles through every vertex (Sec. I names clustering coefficients as a
+ * use of triangle counts): d_counts (device uint64_t[n], written by
  * the library) gets t(x), the number of triangles containing x, and
  * *triangles gets T (sum of t(x) = 3T).  The local clustering coefficient of
  * x is 2 t(x) / (d(x) (d(x) - 1)).  Same method as tc_count; each triangle
@@ -279,7 +308,7 @@ tc_status tc_list_triangles(tc_ctx *ctx, const tc_graph *g, uint32_t *d_triples,
 
 /*
  * One shard of a count split across nshards processes or devices (the
- * multi-GPU form of the method: BFS levels and rows are computed in full on
+ * multi-GPU form of the method, Sec. V: BFS levels and rows are computed in full on
  * every shard, the intersection tasks -- contiguous slices of the oriented
  * horizontal edges, of about equal probe work -- are divided, and the exact
  * total is the sum of the nshards partial counts, one 8-byte exchange).
@@ -289,8 +318,14 @@ tc_status tc_count_shard(tc_ctx *ctx, const tc_graph *g, uint32_t shard, uint32_
                          tc_stats *stats);
 
 /*
- * Count G independent graphs in one batched launch sequence; counts is a host
- * uint64_t[G].  Every count equals tc_count on the same graph.
+ * Count G independent graphs in one batched launch sequence.  No counterpart
+ * in the paper (it counts one graph per call): each graph's count is
+ * Algorithm 4 exactly as in tc_count, the G graphs run as one disjoint union
+ * (Sec. V names parallelising the BFS, the partition and the intersections;
+ * here they run over all graphs at once).  graphs: host array of G graph
+ * handles (read only, any mix of sizes); counts: host uint64_t[G], written
+ * on success.  Every count equals tc_count on the same graph.  TC_ERR_OOM if
+ * the union does not fit in device memory.
  */
 tc_status tc_count_batch(tc_ctx *ctx, uint32_t G, const tc_graph *const *graphs, uint64_t *counts);
 
@@ -300,20 +335,26 @@ tc_status tc_count_batch(tc_ctx *ctx, uint32_t G, const tc_graph *const *graphs,
  * they count, e.g. code running inside another allocator or a process whose
  * memory pool already owns the whole device).  Same method and same results
  * as tc_count, run by one thread block with all scratch in a fixed array of
- * device memory declared in the library (about 5.8 MB, held by every GPU
- * that loads the library until exit).
+ * device memory declared in the library (about 5.8 MB).
  *   d_row_ptr, d_col: device CSR (well formed, as for TC_BORROW), n <= 65536
  *     vertices, slots = row_ptr[n] <= 1048576 (TC_ERR_INVALID beyond that);
  *   order: TC_ORDER_DEGREE or TC_ORDER_ID;
  *   d_out: device uint64_t[4], written when the stream reaches the kernel:
  *     [0] = T, [1] = triangles inside G0, [2] = cross-level triangles,
- *     [3] = 0 (1 if the device saw row_ptr[n] beyond the limit; nothing else
- *     is then written);
+ *     [3] = 0 on success, 1 if the device saw row_ptr[n] beyond the limit
+ *     (then [0..2] = 0);
  *   stream: cudaStream_t (NULL: the legacy default stream).
- * Asynchronous: returns after the launch.  Every call shares the one array, so
- * calls that overlap on the GPU (other streams or threads) race; serialise
- * them.  The first call on a device looks up the array's device address; make
- * it before any stream capture.
+ * Asynchronous: returns after the launch; TC_ERR_CUDA if the launch itself
+ * failed (an earlier, unrelated CUDA error of the process is neither reported
+ * nor cleared).  Every call shares the one array, so calls that overlap on
+ * the GPU (other streams or threads) race; serialise them.
+ * Set-up: the CUDA driver loads a library's device code lazily by default,
+ * so the array is allocated on a device by the first call on that device
+ * (which looks up its address); only later calls allocate nothing.  Make a
+ * first call on every device at start-up, before memory is handed out (n = 0
+ * with a one-element row_ptr holding 0 is enough), and outside any stream
+ * capture.  The array then stays until the process exits.  Cost: O(n + m)
+ * for the levels (all components at once) plus the hashed intersections.
  */
 tc_status tc_count_noalloc(const uint64_t *d_row_ptr, const uint32_t *d_col, uint32_t n, uint64_t slots,
                            uint32_t order, uint64_t *d_out, void *stream);
@@ -322,23 +363,28 @@ tc_status tc_count_noalloc(const uint64_t *d_row_ptr, const uint32_t *d_col, uin
 
 /*
  * Queue a count of g (which must stay alive until its ticket completes) and
- * return at once with a ticket.  A server thread owned by the context admits
- * queued requests while device memory allows, batches them, and overlaps
- * their work on the device.  TC_ERR_BUSY if the queue is full.
+ * return at once with a ticket (*ticket, host).  No counterpart in the paper
+ * (the served form of the counter); every result is Algorithm 4's exact T,
+ * as tc_count gives it.  Server threads owned by the context admit queued
+ * requests while free device memory allows, batch them, and overlap their
+ * work on the device; large graphs go to a lane of their own so that they
+ * do not hold up small ones.  TC_ERR_BUSY if the queue is full.
  */
 tc_status tc_submit(tc_ctx *ctx, const tc_graph *g, uint64_t *ticket);
 
 /*
- * Non-blocking: TC_OK with *triangles set when the ticket is done (the ticket
- * is then released), TC_NOT_READY while it is queued or running, another
- * status if it failed or the ticket is unknown.
+ * Non-blocking: TC_OK with *triangles (host) set to T when the ticket is done
+ * (the ticket is then released), TC_NOT_READY while it is queued or running,
+ * another status if it failed or the ticket is unknown.  No counterpart in
+ * the paper (served form).
  */
 tc_status tc_poll(tc_ctx *ctx, uint64_t ticket, uint64_t *triangles);
 
 /*
- * tc_poll that also returns the request's latency in nanoseconds, from its
- * tc_submit to the moment the server published its result (the library's
- * steady clock), so a client that polls late does not inflate it.
+ * tc_poll that also returns the request's latency in nanoseconds
+ * (*latency_ns, host, nullable), from its tc_submit to the moment the server
+ * published its result (the library's steady clock), so a client that polls
+ * late does not inflate it.  No counterpart in the paper (served form).
  */
 tc_status tc_poll_ex(tc_ctx *ctx, uint64_t ticket, uint64_t *triangles, uint64_t *latency_ns);
 

@@ -91,3 +91,18 @@ def test_every_declaration_is_documented():
     assert len(decls) >= 20
     undocumented = [m.group(1) for m in decls if not text[:m.start()].rstrip().endswith("*/")]
     assert undocumented == []
+
+
+def test_every_declaration_cites_the_paper_or_says_it_has_no_counterpart():
+    """The comment of each entry point names the passage of the paper that defines
+    the operation (a section or an algorithm), or states that the paper has none."""
+    text = open(os.path.join(ROOT, "include", "tc.h")).read()
+    decls = list(re.finditer(r"^(?:tc_status|const char \*|void|int)\s*\*?\s*(tc_[a-z0-9_]+)\s*\(", text, flags=re.M))
+    missing = []
+    for m in decls:
+        head = text[:m.start()].rstrip()
+        comment = head[head.rfind("/*"):]
+        if not re.search(r"Sec\. [IVX]+|Algorithm [1-4]|no counterpart in\s+(?:\*\s*)?the\s+(?:\*\s*)?paper",
+                         comment, flags=re.I):
+            missing.append(m.group(1))
+    assert missing == []
