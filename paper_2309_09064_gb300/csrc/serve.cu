@@ -1,13 +1,19 @@
 // serve.cu -- tc_submit / tc_poll: a continuous-batching request server.
 //
-// Two worker threads, each with a private sub-context (own stream, arenas and
-// control block), take requests from one queue.  A worker admits queued
-// requests into its next round while their estimated scratch fits its memory
-// budget (a share of the device memory free when serving started), counts
-// the round with the batched union pipeline, publishes the results, and
-// immediately admits whatever arrived meanwhile.  While one worker's round
-// runs on the device the other admits and launches the next, so rounds
-// overlap on the GPU and a request never waits for a full batch to form.
+// Requests go to one of two lanes by size.  The small lane has two worker
+// threads, the large lane one; every worker has a private sub-context (own
+// stream, arenas and control block).  A worker takes queued requests of its
+// lane into its next round while (a) their estimated scratch fits the device
+// memory free at that moment (cudaMemGetInfo, read before every round, split
+// across the workers) plus what the worker's arenas already hold, and (b) the
+// round stays below a work bound (undirected edges), so that no round -- and
+// no request queued behind one -- waits for an unbounded batch.  It counts the
+// round with the batched union pipeline (one graph: tc_count directly),
+// publishes every request of the round with its latency, and immediately
+// admits whatever arrived meanwhile.  While one worker's round runs on the
+// device the others admit and launch theirs, so rounds overlap on the GPU,
+// and a large graph (the large lane) never holds up the small requests
+// behind it.
 #include <chrono>
 
 #include "pipeline.cuh"
@@ -22,15 +28,19 @@ struct ServeRequest {
 
 struct ServeState {
     std::mutex mu;
-    std::condition_variable cv;
-    std::deque<uint64_t> queue;
+    std::condition_variable cv[2];
+    std::deque<uint64_t> queue[2];  // lane 0: small requests, lane 1: large ones
     std::unordered_map<uint64_t, ServeRequest> reqs;
     uint64_t next_ticket = 1;
     bool stop = false;
-    size_t budget = 0;          // scratch bytes per round and worker
-    uint32_t max_batch = 4096;  // graphs per round
+    uint32_t max_batch = 4096;           // graphs per round
+    uint64_t round_edges = 1ull << 25;   // small lane: undirected edges per round (the first request always fits)
+    uint64_t large_slots = 1ull << 23;   // a graph with more CSR slots goes to the large lane
+    double mem_fraction = 0.8;           // share of the free device memory the workers may grow into
     std::vector<tc_ctx *> subs;
+    std::vector<int> lane;
     std::vector<std::thread> workers;
+    size_t queued() const { return queue[0].size() + queue[1].size(); }
 };
 
 namespace tc {
@@ -42,7 +52,10 @@ static size_t request_bytes(const tc_ctx *sub, const tc_graph *g) {
     return pipeline_bytes(sub, g->n, g->slots, 0, true, &hs, &hb) + 8ull * (g->n + 1) + 4ull * (g->slots + 1);
 }
 
-static void worker_loop(ServeState *S, tc_ctx *sub) {
+static size_t arena_held(const tc_ctx *sub) { return sub->arena.cap + sub->batch_arena.cap; }
+
+static void worker_loop(ServeState *S, tc_ctx *sub, int lane, int nworkers) {
+    cudaSetDevice(sub->device);
     std::vector<uint64_t> tickets;
     std::vector<const tc_graph *> graphs;
     std::vector<uint64_t> out;
@@ -51,23 +64,41 @@ static void worker_loop(ServeState *S, tc_ctx *sub) {
         graphs.clear();
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            S->cv.wait(lk, [&] { return S->stop || !S->queue.empty(); });
-            if (S->stop && S->queue.empty()) return;
+            S->cv[lane].wait(lk, [&] { return S->stop || !S->queue[lane].empty(); });
+            if (S->stop && S->queue[lane].empty()) return;
+        }
+        // memory for this round: what the worker's arenas hold plus its share of
+        // what is free on the device right now
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+            cudaGetLastError();
+            free_b = 0;
+        }
+        const size_t budget = arena_held(sub) + (size_t)(free_b * S->mem_fraction) / (size_t)nworkers;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            std::deque<uint64_t> &q = S->queue[lane];
             size_t used = 0;
-            while (!S->queue.empty() && tickets.size() < S->max_batch) {
-                const uint64_t t = S->queue.front();
+            uint64_t edges = 0;
+            while (!q.empty() && tickets.size() < S->max_batch) {
+                const uint64_t t = q.front();
                 ServeRequest &rq = S->reqs[t];
                 const size_t b = request_bytes(sub, rq.g);
-                if (!tickets.empty() && used + b > S->budget) break;  // admit when memory frees up
+                const uint64_t e = rq.g->slots / 2;
+                if (!tickets.empty() && (used + b > budget || (lane == 0 && edges + e > S->round_edges))) break;
                 used += b;
-                S->queue.pop_front();
+                edges += e;
+                q.pop_front();
                 rq.state = 1;
                 tickets.push_back(t);
                 graphs.push_back(rq.g);
             }
         }
+        if (tickets.empty()) continue;
         out.assign(tickets.size(), 0);
-        tc_status st = tc_count_batch(sub, (uint32_t)graphs.size(), graphs.data(), out.data());
+        tc_status st;
+        if (graphs.size() == 1) st = tc_count(sub, graphs[0], &out[0], nullptr);
+        else st = tc_count_batch(sub, (uint32_t)graphs.size(), graphs.data(), out.data());
         {
             const auto now = std::chrono::steady_clock::now();
             std::lock_guard<std::mutex> lk(S->mu);
@@ -85,19 +116,8 @@ static void worker_loop(ServeState *S, tc_ctx *sub) {
 
 static tc_status serve_start(tc_ctx *ctx) {
     ServeState *S = new ServeState();
-    size_t free_b = 0, total_b = 0;
-    int prev = -1;
-    cudaGetDevice(&prev);
-    cudaSetDevice(ctx->device);
-    const cudaError_t mem_e = cudaMemGetInfo(&free_b, &total_b);
-    if (prev >= 0) cudaSetDevice(prev);
-    if (mem_e != cudaSuccess) {
-        cudaGetLastError();
-        delete S;
-        return set_error(ctx, TC_ERR_CUDA, "cudaMemGetInfo failed");
-    }
-    const int nworkers = 2;
-    S->budget = (size_t)(free_b * 0.6) / nworkers;
+    const int lanes[] = {0, 0, 1};  // two small-lane workers, one large-lane worker
+    const int nworkers = 3;
     for (int i = 0; i < nworkers; ++i) {
         tc_options o = ctx->opt;
         o.stream = nullptr;
@@ -109,8 +129,9 @@ static tc_status serve_start(tc_ctx *ctx) {
         }
         sub->tune = ctx->tune;
         S->subs.push_back(sub);
+        S->lane.push_back(lanes[i]);
     }
-    for (tc_ctx *sub : S->subs) S->workers.emplace_back(worker_loop, S, sub);
+    for (size_t i = 0; i < S->subs.size(); ++i) S->workers.emplace_back(worker_loop, S, S->subs[i], S->lane[i], nworkers);
     ctx->serve = S;
     return TC_OK;
 }
@@ -122,7 +143,8 @@ void serve_shutdown(tc_ctx *ctx) {
         std::lock_guard<std::mutex> lk(S->mu);
         S->stop = true;
     }
-    S->cv.notify_all();
+    S->cv[0].notify_all();
+    S->cv[1].notify_all();
     for (auto &t : S->workers) t.join();
     for (tc_ctx *c : S->subs) tc_destroy(c);
     delete S;
@@ -147,18 +169,20 @@ tc_status tc_submit(tc_ctx *ctx, const tc_graph *g, uint64_t *ticket) {
         }
     }
     ServeState *S = ctx->serve;
+    int lane = 0;
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        if (S->queue.size() >= ctx->opt.max_queue) return TC_ERR_BUSY;
+        if (S->queued() >= ctx->opt.max_queue) return TC_ERR_BUSY;
         const uint64_t t = S->next_ticket++;
         ServeRequest rq;
         rq.g = g;
         rq.t_submit = std::chrono::steady_clock::now();
         S->reqs.emplace(t, rq);
-        S->queue.push_back(t);
+        lane = g->slots > S->large_slots ? 1 : 0;
+        S->queue[lane].push_back(t);
         *ticket = t;
     }
-    S->cv.notify_one();
+    S->cv[lane].notify_one();
     return TC_OK;
 }
 

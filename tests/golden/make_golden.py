@@ -48,6 +48,19 @@ def sha(*arrays):
     return h.hexdigest()
 
 
+def host():
+    """Where the oracle times were taken: machine, CPU model, cores (the oracle is serial: one thread)."""
+    import platform
+    model = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.split(":")[0].strip().lower() in ("model name", "cpu part") and not model:
+                model = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return {"machine": platform.machine(), "cpu_model": model, "cpus": os.cpu_count(), "threads_used": 1}
+
+
 def run(name):
     t0 = time.time()
     g = WORKLOADS[name]()
@@ -64,6 +77,7 @@ def run(name):
         "level_hist": [int(x) for x in np.bincount(L.astype(np.int64))],
         "levels_sha256": sha(L.astype("<u4")),
         "oracle_seconds": {"build_csr": round(t1 - t0, 2), "alg4": round(t2 - t1, 2)},
+        "oracle_host": host(),
     }
     if len(g) == 4:
         rec["grid_diagonals"] = int(g[3])
