@@ -134,7 +134,11 @@ typedef struct tc_tuning {
                                    tables (block_cap up to 16384) */
     uint32_t flat_cap;          /* warp class: probe ranges shorter than this are concatenated so that every
                                    lane of a warp has work; longer ones are walked range by range (0..4096) */
-    uint32_t reserved[2];
+    uint32_t block_bits_log2;   /* block class with cuckoo tables: the set's ranks below 2^k live in a direct
+                                   bitmap in shared memory (one bit per rank, 2^k / 8 bytes), only the others
+                                   in the cuckoo table; the rows stage puts every level-spanning part's ranks
+                                   below 2^k first.  0 turns it off; else 10..19 */
+    uint32_t reserved;
 } tc_tuning;
 
 /* ------------------------------------------------------------------ context */

@@ -177,6 +177,7 @@ tc_status tc_get_tuning(const tc_ctx *ctx, tc_tuning *out) {
     out->tiny_cap = t.tiny_cap;
     out->table_kind = t.table_kind;
     out->flat_cap = t.flat_cap;
+    out->block_bits_log2 = t.block_bits_log2;
     return TC_OK;
 }
 
@@ -197,13 +198,15 @@ tc_status tc_set_tuning(tc_ctx *ctx, const tc_tuning *t) {
     nt.tiny_cap = t->tiny_cap;
     nt.table_kind = t->table_kind;
     nt.flat_cap = t->flat_cap;
+    nt.block_bits_log2 = t->block_bits_log2;
     const size_t smem_limit = 227 * 1024;
     auto threads_ok = [](uint32_t x) { return x >= 64 && x <= 1024 && x % 32 == 0; };
     if (nt.warp_cap < 1 || nt.warp_cap > 4096 || nt.block_cap < nt.warp_cap || nt.block_cap > 16384 ||
         nt.task_work < 1 || nt.warp_task_work < 1 || nt.hub_task_work < 1 || nt.warps_per_block < 1 ||
         nt.warps_per_block > 8 || !threads_ok(nt.block_threads) || !threads_ok(nt.hub_threads) || nt.max_v < 64 ||
         nt.max_v > 4096 || nt.hub_group < 1 || nt.hub_group > 64 || nt.hub_filter_log2 < 10 ||
-        nt.hub_filter_log2 > 20 || nt.tiny_cap > 64 || nt.table_kind > 1 || nt.flat_cap > 4096 || warp_kernel_smem(nt) > smem_limit || block_kernel_smem(nt) > smem_limit ||
+        nt.hub_filter_log2 > 20 || nt.tiny_cap > 64 || nt.table_kind > 1 || nt.flat_cap > 4096 ||
+        (nt.block_bits_log2 != 0 && (nt.block_bits_log2 < 10 || nt.block_bits_log2 > 19)) || warp_kernel_smem(nt) > smem_limit || block_kernel_smem(nt) > smem_limit ||
         hub_kernel_smem(nt) > smem_limit)
         return set_error(ctx, TC_ERR_INVALID, "tuning out of range");
     ctx->tune = nt;

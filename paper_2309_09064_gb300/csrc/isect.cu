@@ -426,6 +426,35 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
 
 __device__ __forceinline__ uint32_t shared_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// 32-bit load from the shared window at byte address addr when p holds;
+// otherwise `other` (no shared-memory access: the lane takes no part in it).
+__device__ __forceinline__ uint32_t lds_u32_if(bool p, uint32_t addr, uint32_t other) {
+    uint32_t v = other;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q ld.shared.u32 %0, [%1];\n\t}"
+        : "+r"(v)
+        : "r"(addr), "r"((uint32_t)p));
+    return v;
+}
+
+// Block rows with a split set: the ranks of the set below R sit in a direct
+// bitmap (bit w of R / 32 shared words), the others in the cuckoo table.
+// The probed ids are mostly low ranks (high-degree vertices appear in many
+// rows), so most lookups read one bitmap word -- one shared load, and lanes
+// whose ranks share a word read it together -- instead of two random table
+// slots.  The rows stage puts the low ranks of every level-spanning part
+// first, so a warp step mostly lies wholly below R (bitmap only) or wholly
+// above it (table only); a step that straddles R does both, lane by lane.
+struct SplitSet {
+    static constexpr int kUnroll = 8;
+    static constexpr int kBatch = 8;
+    static constexpr uint32_t kPad = kNone;  // probe padding: a "low" lane in the vote, never a hit
+    static constexpr bool kFineTail = false;
+    CuckooTable C;  // ranks >= R
+    uint32_t bm;    // shared-window byte address of the bitmap
+    uint32_t R;     // ranks below R are in the bitmap (a power of two, or 0: none)
+};
+
 // Hub rows: shared prefilter (2^hub_filter_log2 bits) in front of the exact
 // n-bit bitmap (by rank) in global memory.
 struct HubSet {
@@ -532,6 +561,51 @@ __device__ __forceinline__ void lookup_step(const Set &set, const uint32_t (&w)[
         lookup_batch(set, ww, hh);
 #pragma unroll
         for (int i = 0; i < B; ++i) hit[half + i] = hh[i];
+    }
+}
+
+// One warp step against a split set: a vote picks the bitmap alone (every
+// lane's ids below R, padding included), the table alone (every id at or
+// above R), or both, lane by lane.  The stash holds only ranks >= R.
+template <int U>
+__device__ __forceinline__ void lookup_step(const SplitSet &S, const uint32_t (&w)[U], bool (&hit)[U]) {
+    bool lo_all = true, hi_all = true;
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+        const bool lo = w[i] < S.R;
+        lo_all = lo_all && (lo || w[i] == SplitSet::kPad);
+        hi_all = hi_all && !lo;
+    }
+    lo_all = __all_sync(0xFFFFFFFFu, lo_all);
+    hi_all = __all_sync(0xFFFFFFFFu, hi_all);
+    if (lo_all) {
+        uint32_t x[U];
+#pragma unroll
+        for (int i = 0; i < U; ++i) x[i] = lds_u32(S.bm + (((w[i] < S.R ? w[i] : 0u) >> 5) << 2));
+#pragma unroll
+        for (int i = 0; i < U; ++i) hit[i] = w[i] < S.R && ((x[i] >> (w[i] & 31u)) & 1u);
+        return;
+    }
+    if (hi_all) {
+        lookup_step<U>(S.C, w, hit);
+        return;
+    }
+    uint32_t a[U], c[U];
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+        const bool lo = w[i] < S.R;
+        a[i] = lds_u32(lo ? S.bm + ((w[i] >> 5) << 2) : S.C.a0 + (((w[i] * S.C.k0) >> S.C.shift) << 2));
+        c[i] = lds_u32_if(!lo, S.C.a1 + (((w[i] * S.C.k1) >> S.C.shift) << 2), kEmpty);
+    }
+#pragma unroll
+    for (int i = 0; i < U; ++i)
+        hit[i] = w[i] < S.R ? (((a[i] >> (w[i] & 31u)) & 1u) != 0u) : (a[i] == w[i] || c[i] == w[i]);
+    if (S.C.nstash) {
+        for (uint32_t k = 0; k < S.C.nstash; ++k) {
+            const uint32_t x = S.C.stash[k];
+#pragma unroll
+            for (int i = 0; i < U; ++i) hit[i] = hit[i] || x == w[i];
+        }
     }
 }
 
@@ -706,18 +780,26 @@ __device__ __forceinline__ uint32_t cuckoo_slots_for(uint32_t s, uint32_t m_cap)
     return m;
 }
 
-// Block-wide build (all threads of the block call it).
+// Block-wide build (all threads of the block call it).  With a bitmap bm of
+// R bits (R > 0), keys below R set their bit there instead (the bitmap is
+// cleared first) and only the others enter the table.
 __device__ __forceinline__ CuckooTable cuckoo_build(uint32_t *t, uint32_t m_cap, const uint32_t *__restrict__ row,
-                                                    uint32_t s, CuckooShared *cs, unsigned int *err) {
+                                                    uint32_t s, CuckooShared *cs, unsigned int *err,
+                                                    uint32_t *bm = nullptr, uint32_t R = 0) {
     const uint32_t m = cuckoo_slots_for(s, m_cap);
     CuckooTable C{t, cs->stash, m, (uint32_t)__clz(m) + 1u, 0, 0, 0, shared_addr(t), shared_addr(t + m)};
+    for (uint32_t j = threadIdx.x; j < (R >> 5); j += blockDim.x) bm[j] = 0u;
     for (int attempt = 0; attempt < kCuckooAttempts; ++attempt) {
         C.k0 = kCuckooMul[2 * attempt];
         C.k1 = kCuckooMul[2 * attempt + 1];
         for (uint32_t j = threadIdx.x; j < 2 * m; j += blockDim.x) t[j] = kEmpty;
         if (threadIdx.x == 0) cs->nstash = 0;
         __syncthreads();
-        for (uint32_t j = threadIdx.x; j < s; j += blockDim.x) cuckoo_insert(C, row[j], cs);
+        for (uint32_t j = threadIdx.x; j < s; j += blockDim.x) {
+            const uint32_t key = row[j];
+            if (key < R) atomicOr(bm + (key >> 5), 1u << (key & 31u));
+            else cuckoo_insert(C, key, cs);
+        }
         __syncthreads();
         const unsigned ns = cs->nstash;
         __syncthreads();  // everyone has read it before a rebuild clears it
@@ -1205,8 +1287,9 @@ __device__ __forceinline__ void init_task_smem(TaskSmem *ts) {
 }
 
 // Block class.  The hashed set lives in shared memory: a cuckoo table
-// (table_kind = 0) or the bucketed table (table_kind = 1).
-template <bool kCuckoo, int kM>
+// (kSet = 0), the bucketed table (kSet = 1), or a split set (kSet = 2: ranks
+// below split_R in a bitmap placed after the cuckoo table, the rest in it).
+template <int kSet, int kM>
 __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict__ tasks, const uint32_t *__restrict__ rows,
                                                       const uint32_t *__restrict__ ntask,
                                                       const uint64_t *__restrict__ rp,
@@ -1214,30 +1297,33 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
                                                       const uint32_t *__restrict__ fcnt,
                                                       const uint64_t *__restrict__ eoff,
                                                       const uint4 *__restrict__ erec, Ctl *ctl, uint32_t max_v,
-                                                      uint32_t table_units, unsigned long long chunk,
+                                                      uint32_t table_units, uint32_t split_R,
+                                                      unsigned long long chunk,
                                                       unsigned long long first, unsigned long long last,
                                                       GroupSpec groups, VertexOut vo) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TaskSmem ts;
     __shared__ CuckooShared cs;
     const unsigned lane = lane_id();
+    constexpr bool kCuckoo = kSet != 1;
     const SliceSmem S = carve_slice(smem_raw, max_v);
     unsigned char *tab = smem_raw + slice_smem_bytes(max_v);
+    uint32_t *bmp = reinterpret_cast<uint32_t *>(tab + (kCuckoo ? 8ull : 16ull) * table_units);
+    unsigned char *after = tab + (kCuckoo ? 8ull : 16ull) * table_units + (kSet == 2 ? split_R / 8 : 0u);
     Acc acc;
     unsigned long long build = 0, done = 0, inserts = 0;
     uint32_t cur_row = 0xFFFFFFFFu;
     CuckooTable C{reinterpret_cast<uint32_t *>(tab), cs.stash, 64, 26, 0, 0, 0, 0, 0};
     BucketTable T{reinterpret_cast<uint4 *>(tab), 0, 0, &ctl->error};
     if constexpr (kM == 1) {
-        vo.priv = reinterpret_cast<unsigned long long *>(tab + (kCuckoo ? 8ull : 16ull) * table_units);
+        vo.priv = reinterpret_cast<unsigned long long *>(after);
         priv_begin(vo);
     }
     init_task_smem(&ts);
     ListCtx lc;
     const unsigned long long gw = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if constexpr (kM == 2) {
-        lc.stage = reinterpret_cast<uint32_t *>(tab + (kCuckoo ? 8ull : 16ull) * table_units) +
-                   (size_t)(threadIdx.x >> 5) * kStageSlots;
+        lc.stage = reinterpret_cast<uint32_t *>(after) + (size_t)(threadIdx.x >> 5) * kStageSlots;
         load_list_state(vo, lc, gw);
     }
     const long long t_start = clock64();
@@ -1255,7 +1341,9 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
         __syncthreads();
         scan_segments(S.len, S.seg, k_hi - k_lo);
         if (rebuild) {
-            if constexpr (kCuckoo) {
+            if constexpr (kSet == 2) {
+                C = cuckoo_build(C.t, table_units, adj2 + hb, su, &cs, &ctl->error, bmp, split_R);
+            } else if constexpr (kCuckoo) {
                 C = cuckoo_build(C.t, table_units, adj2 + hb, su, &cs, &ctl->error);
             } else {
                 fill_table(T, adj2 + hb, su, threadIdx.x, blockDim.x);
@@ -1270,7 +1358,9 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
         }
         const unsigned long long before = acc.same + acc.cross;
         lc.u = u;
-        if constexpr (kCuckoo) probe_slice<kM>(C, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);
+        if constexpr (kSet == 2)
+            probe_slice<kM>(SplitSet{C, shared_addr(bmp), split_R}, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);
+        else if constexpr (kCuckoo) probe_slice<kM>(C, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);
         else probe_slice<kM>(T, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);
         finish_task<kM>(acc.same + acc.cross - before, groups, vo, ts, u);
     }
@@ -1391,7 +1481,8 @@ size_t warp_kernel_smem(const Tuning &tu) {
     return (size_t)tu.warps_per_block * (warp_set_bytes(tu.table_kind == 0, warp_table_units(tu)) + kWarpMetaBytes);
 }
 size_t block_kernel_smem(const Tuning &tu) {
-    return slice_smem_bytes(tu.max_v) + (tu.table_kind == 0 ? 8ull : 16ull) * block_table_units(tu);
+    return slice_smem_bytes(tu.max_v) + (tu.table_kind == 0 ? 8ull : 16ull) * block_table_units(tu) +
+           g1_split_rank(tu) / 8;
 }
 size_t hub_kernel_smem(const Tuning &tu) { return slice_smem_bytes(tu.max_v) + (1ull << tu.hub_filter_log2) / 8; }
 
@@ -1486,14 +1577,23 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[5], s));
     if (hi1 > lo1) {
-        const size_t smem = block_kernel_smem(tu) + priv + (mode == 2 ? 4ull * kStageSlots * (tu.block_threads / 32) : 0);
+        // split set: the bitmap shrinks (halves) where the mode's own shared memory needs the room
+        const size_t extra = priv + (mode == 2 ? 4ull * kStageSlots * (tu.block_threads / 32) : 0);
+        uint32_t split_R = g1_split_rank(tu);
+        const size_t base_smem = block_kernel_smem(tu) - split_R / 8;
+        while (split_R >= 1024 && base_smem + split_R / 8 + extra > kSmemLimit) split_R >>= 1;
+        if (split_R < 1024) split_R = 0;
+        const size_t smem = base_smem + split_R / 8 + extra;
         if (smem > kSmemLimit) return set_error(ctx, TC_ERR_INVALID, "tuning leaves no shared memory for this mode");
-        auto kern = tu.table_kind == 0 ? (mode == 0   ? k_isect_block<true, 0>
-                                          : mode == 1 ? k_isect_block<true, 1>
-                                                      : k_isect_block<true, 2>)
-                                       : (mode == 0   ? k_isect_block<false, 0>
-                                          : mode == 1 ? k_isect_block<false, 1>
-                                                      : k_isect_block<false, 2>);
+        auto kern = tu.table_kind == 1 ? (mode == 0   ? k_isect_block<1, 0>
+                                          : mode == 1 ? k_isect_block<1, 1>
+                                                      : k_isect_block<1, 2>)
+                    : split_R         ? (mode == 0   ? k_isect_block<2, 0>
+                                          : mode == 1 ? k_isect_block<2, 1>
+                                                      : k_isect_block<2, 2>)
+                                      : (mode == 0   ? k_isect_block<0, 0>
+                                          : mode == 1 ? k_isect_block<0, 1>
+                                                      : k_isect_block<0, 2>);
         TC_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
         TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tu.block_threads, smem));
@@ -1504,7 +1604,7 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         const unsigned long long chunk = std::max<unsigned long long>(1, (hi1 - lo1) / (grid * 8));
         kern<<<(unsigned)grid, tu.block_threads, smem, s>>>(b.tasks[1], b.rows[1], b.ntask[1], b.rp, b.adj2, b.fcnt,
                                                             b.eoff, b.erec, ctx->d_ctl, tu.max_v, block_table_units(tu),
-                                                            chunk, lo1, hi1, b.groups, vo);
+                                                            split_R, chunk, lo1, hi1, b.groups, vo);
         note_launch(ctx);
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[6], s));

@@ -78,6 +78,12 @@ struct PipeBufs {
     uint32_t *inv = nullptr;                  // [n] rank -> id (null under the id order)
 };
 
+// Ranks below this value are kept in the block class's shared bitmap, and
+// the rows stage puts them first in every level-spanning part (0: no split).
+inline uint32_t g1_split_rank(const Tuning &tu) {
+    return (tu.table_kind == 0 && tu.block_bits_log2) ? (1u << tu.block_bits_log2) : 0u;
+}
+
 tc_status compute_levels(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t slots);
 // levels supplied by the caller (device uint32[n]): copied into b.L after the
 // check that they differ by at most one across every edge (TC_ERR_INVALID if not)

@@ -6,7 +6,14 @@
 //   F(x)  = { y ~ x : L(y) == L(x), x precedes y }  horizontal out-neighbours, as vertex ids
 //   A(x)  = { y ~ x : L(y) == L(x), y precedes x }  horizontal in-neighbours, as ranks, descending
 //   G1(x) = { y ~ x : L(y) != L(x) }                level-spanning neighbours, as ranks
-// (rank = position in the working order).  A(x) is the set Algorithm 2 has
+// (rank = position in the working order).  G1(x) holds its ranks below
+// g1_lo first (g1_lo = 2^block_bits_log2, 0: no split): the block class keeps
+// those ranks of its sets in a direct bitmap, so a probe range whose steps lie
+// wholly below (or wholly above) g1_lo takes one kind of lookup per step.
+// The split is kept where it is cheap -- rows of up to 32 neighbours (a lane's
+// buffer column), level-spanning parts of up to kWarpA ranks (the warp's
+// buffer) and the block-filled rows -- and otherwise left out (the lookups do
+// not depend on it).  A(x) is the set Algorithm 2 has
 // built for x once every row before x's is done.  For a horizontal edge u -> v
 // the intersections hash A(u) and G1(u) and probe the elements of A(v) ranked
 // below u -- which in descending order are the last ones of A(v) -- and all of
@@ -77,7 +84,7 @@ __global__ void __launch_bounds__(kFillThreads) k_row_fill(uint32_t n, const uin
                                                            const uint32_t *__restrict__ lvp, uint32_t *__restrict__ adj2,
                                                            uint32_t *__restrict__ fcnt, uint32_t *__restrict__ gcnt,
                                                            uint4 *__restrict__ vmeta, uint32_t *__restrict__ big,
-                                                           uint32_t *__restrict__ huge, Ctl *ctl) {
+                                                           uint32_t *__restrict__ huge, Ctl *ctl, uint32_t g1_lo) {
     __shared__ uint32_t sbuf[kFillThreads / 32][kWarpA];
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
@@ -90,7 +97,7 @@ __global__ void __launch_bounds__(kFillThreads) k_row_fill(uint32_t n, const uin
         const uint32_t dx = valid ? (uint32_t)(rp[x + 1] - b) : 0;
         const uint2 me = valid ? rank_level<kPacked>(lv, lvp, (uint32_t)x) : make_uint2(0, 0);
         if (valid && dx <= kSmallRow) {
-            uint32_t fp = 0, gp = 0, ap = 0;
+            uint32_t fp = 0, gp = 0, ap = 0, gl = 0;  // gl: level-spanning ranks below g1_lo (column top)
             for (uint32_t j0 = 0; j0 < dx; j0 += kFillAhead) {
                 // the ids and their rank/level words of kFillAhead neighbours in
                 // flight together, then the neighbours in order
@@ -105,7 +112,10 @@ __global__ void __launch_bounds__(kFillThreads) k_row_fill(uint32_t n, const uin
                 for (uint32_t t = 0; t < kFillAhead; ++t) {
                     if (j0 + t >= dx) break;
                     if (q[t].y != me.y) {
-                        adj2[b + dx - 1 - gp++] = q[t].x;
+                        // below g1_lo: kept at the top of the column (A fills it from the
+                        // bottom; together they hold at most dx <= 32 ranks)
+                        if (q[t].x < g1_lo) buf[(kSmallRow - 1 - gl++) * 32 + lane] = q[t].x;
+                        else adj2[b + dx - 1 - gp++] = q[t].x;
                     } else if (me.x < q[t].x) {
                         adj2[b + fp++] = y[t];
                     } else {  // insert into the lane's column, descending
@@ -119,6 +129,8 @@ __global__ void __launch_bounds__(kFillThreads) k_row_fill(uint32_t n, const uin
                 }
             }
             for (uint32_t i = 0; i < ap; ++i) adj2[b + fp + i] = buf[i * 32 + lane];
+            for (uint32_t i = 0; i < gl; ++i) adj2[b + fp + ap + i] = buf[(kSmallRow - 1 - i) * 32 + lane];
+            gp += gl;
             fcnt[x] = fp;
             gcnt[x] = gp;
             const uint64_t as = b + fp;
@@ -188,6 +200,31 @@ __global__ void __launch_bounds__(kFillThreads) k_row_fill(uint32_t n, const uin
                 if (lane == 0 && ap <= kSortCap) big[atomicAdd(&ctl->n_big, 1u)] = bx;
             }
             __syncwarp();
+            if (g1_lo && gp > 1 && gp <= kWarpA) {
+                // G1 (written from the back) through the warp's buffer, back in place
+                // with its ranks below g1_lo first
+                const uint64_t gb = bb + bd - gp;
+                uint32_t nlo = 0;
+                for (uint32_t i = lane; i < gp; i += 32) {
+                    const uint32_t r = adj2[gb + i];
+                    buf[i] = r;
+                    nlo += r < g1_lo;
+                }
+                nlo = warp_sum(nlo);
+                __syncwarp();
+                uint32_t lp = 0, hp = 0;
+                for (uint32_t i0 = 0; i0 < gp; i0 += 32) {
+                    const uint32_t i = i0 + lane;
+                    const uint32_t r = i < gp ? buf[i] : 0u;
+                    const bool lo = i < gp && r < g1_lo, hi = i < gp && r >= g1_lo;
+                    const unsigned ml = __ballot_sync(0xFFFFFFFFu, lo), mh = __ballot_sync(0xFFFFFFFFu, hi);
+                    if (lo) adj2[gb + lp + __popc(ml & lt)] = r;
+                    if (hi) adj2[gb + nlo + hp + __popc(mh & lt)] = r;
+                    lp += __popc(ml);
+                    hp += __popc(mh);
+                }
+                __syncwarp();
+            }
             if (lane == 0) {
                 fcnt[bx] = fp;
                 gcnt[bx] = gp;
@@ -210,8 +247,9 @@ __global__ void __launch_bounds__(1024) k_row_fill_huge(const uint32_t *__restri
                                                         const uint2 *__restrict__ lv,
                                                         const uint32_t *__restrict__ lvp, uint32_t *__restrict__ adj2,
                                                         uint32_t *__restrict__ fcnt, uint32_t *__restrict__ gcnt,
-                                                        uint4 *__restrict__ vmeta, uint32_t *__restrict__ big) {
-    __shared__ unsigned int cnt[3], pos[3];
+                                                        uint4 *__restrict__ vmeta, uint32_t *__restrict__ big,
+                                                        uint32_t g1_lo) {
+    __shared__ unsigned int cnt[4], pos[4];
     const unsigned lane = lane_id();
     const unsigned lt = (1u << lane) - 1u;
     const uint32_t nh = ctl->n_huge;
@@ -220,19 +258,25 @@ __global__ void __launch_bounds__(1024) k_row_fill_huge(const uint32_t *__restri
         const uint64_t b = rp[x];
         const uint32_t d = (uint32_t)(rp[x + 1] - b);
         const uint2 me = rank_level<kPacked>(lv, lvp, x);
-        if (threadIdx.x < 3) cnt[threadIdx.x] = pos[threadIdx.x] = 0;
+        if (threadIdx.x < 4) cnt[threadIdx.x] = pos[threadIdx.x] = 0;
         __syncthreads();
-        uint32_t f = 0, g = 0;
+        uint32_t f = 0, g = 0, gl = 0;
         for (uint32_t j = threadIdx.x; j < d; j += blockDim.x) {
             const uint2 q = rank_level<kPacked>(lv, lvp, col[b + j]);
-            if (q.y != me.y) ++g;
-            else if (me.x < q.x) ++f;
+            if (q.y != me.y) {
+                ++g;
+                gl += q.x < g1_lo;
+            } else if (me.x < q.x) {
+                ++f;
+            }
         }
         f = warp_sum(f);
         g = warp_sum(g);
+        gl = warp_sum(gl);
         if (lane == 0) {
             atomicAdd(&cnt[0], f);
             atomicAdd(&cnt[1], g);
+            atomicAdd(&cnt[3], gl);
         }
         __syncthreads();
         const uint32_t F = cnt[0], G = cnt[1], A = d - F - G;
@@ -248,20 +292,26 @@ __global__ void __launch_bounds__(1024) k_row_fill_huge(const uint32_t *__restri
                 else if (me.x < ry) isF = true;
                 else isA = true;
             }
+            const bool isL = isG && ry < g1_lo;  // level-spanning, below g1_lo: right after A
+            isG = isG && !isL;
             const unsigned mF = __ballot_sync(0xFFFFFFFFu, isF);
             const unsigned mG = __ballot_sync(0xFFFFFFFFu, isG);
             const unsigned mA = __ballot_sync(0xFFFFFFFFu, isA);
-            uint32_t bF = 0, bG = 0, bA = 0;
+            const unsigned mL = __ballot_sync(0xFFFFFFFFu, isL);
+            uint32_t bF = 0, bG = 0, bA = 0, bL = 0;
             if (lane == 0) {
                 if (mF) bF = atomicAdd(&pos[0], __popc(mF));
                 if (mG) bG = atomicAdd(&pos[1], __popc(mG));
                 if (mA) bA = atomicAdd(&pos[2], __popc(mA));
+                if (mL) bL = atomicAdd(&pos[3], __popc(mL));
             }
             bF = __shfl_sync(0xFFFFFFFFu, bF, 0);
             bG = __shfl_sync(0xFFFFFFFFu, bG, 0);
             bA = __shfl_sync(0xFFFFFFFFu, bA, 0);
+            bL = __shfl_sync(0xFFFFFFFFu, bL, 0);
             if (isF) adj2[b + bF + __popc(mF & lt)] = y;
             if (isA) adj2[b + F + bA + __popc(mA & lt)] = ry;
+            if (isL) adj2[b + F + A + bL + __popc(mL & lt)] = ry;
             if (isG) adj2[b + d - 1 - (bG + __popc(mG & lt))] = ry;
         }
         if (threadIdx.x == 0) {
@@ -528,19 +578,21 @@ tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_de
     const Tuning &tu = ctx->tune;
     if (n == 0) return TC_OK;
     uint32_t launches = 1;
+    const uint32_t g1_lo = g1_split_rank(tu);
     if (b.lvp)
         k_row_fill<true><<<grid_for(n, kFillThreads, cap), kFillThreads, 0, s>>>(
-            n, b.rp, b.col, b.lv, b.lvp, b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big, b.huge, ctx->d_ctl);
+            n, b.rp, b.col, b.lv, b.lvp, b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big, b.huge, ctx->d_ctl, g1_lo);
     else
         k_row_fill<false><<<grid_for(n, kFillThreads, cap), kFillThreads, 0, s>>>(
-            n, b.rp, b.col, b.lv, b.lvp, b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big, b.huge, ctx->d_ctl);
+            n, b.rp, b.col, b.lv, b.lvp, b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big, b.huge, ctx->d_ctl, g1_lo);
     if (max_deg > kHugeRow) {
         if (b.lvp)
             k_row_fill_huge<true><<<(unsigned)ctx->num_sms, 1024, 0, s>>>(b.huge, ctx->d_ctl, b.rp, b.col, b.lv, b.lvp,
-                                                                         b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big);
+                                                                         b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big, g1_lo);
         else
             k_row_fill_huge<false><<<(unsigned)ctx->num_sms, 1024, 0, s>>>(b.huge, ctx->d_ctl, b.rp, b.col, b.lv, b.lvp,
-                                                                          b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big);
+                                                                          b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big,
+                                                                          g1_lo);
         ++launches;
     }
     if (max_deg > kWarpA) {

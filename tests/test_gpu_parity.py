@@ -114,6 +114,25 @@ def test_every_intersection_class(tc, name, caps):
         tc.tc_destroy(c)
 
 
+@pytest.mark.parametrize("bits", [0, 10, 11, 12, 18])
+@pytest.mark.parametrize("name", ["rmat10", "rmat12_ef32", "union", "K40", "chung_lu4096", "er4096"])
+def test_block_class_split_set(tc, name, bits):
+    """Block-class sets split at rank 2^bits (a shared bitmap below, the cuckoo
+    table above; the rows stage puts the low ranks of every level-spanning part
+    first): with 2^bits below, inside and above the rank range of the graph,
+    warp steps take the bitmap alone, the table alone and both; every row with a
+    horizontal out-edge goes to the block class."""
+    c = tc.tc_create(0)
+    try:
+        tc.tc_set_tuning(c, warp_cap=1, block_cap=13107, task_work=256, tiny_cap=0, block_bits_log2=bits)
+        g = SMALL[name]
+        T, st, L, rp, col = gpu_count(tc, c, g)
+        assert st["class_probes"][2] == 0 and st["class_probes"][1] > st["class_probes"][0]
+        assert_parity(T, st, L, rp, col, g)
+    finally:
+        tc.tc_destroy(c)
+
+
 @pytest.mark.parametrize("tiny", [1, 8, 64])
 @pytest.mark.parametrize("name", ["rmat10", "grid33x47", "union", "wheel101", "er4096"])
 def test_tiny_merge_class(tc, name, tiny):

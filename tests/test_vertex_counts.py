@@ -34,6 +34,7 @@ TUNINGS = {
     "all_hub": {"warp_cap": 1, "block_cap": 1, "task_work": 1, "tiny_cap": 0},
     "tiny64": {"tiny_cap": 64},
     "buckets": {"table_kind": 1, "warp_cap": 8, "block_cap": 64, "tiny_cap": 0},
+    "split_block": {"warp_cap": 1, "block_cap": 13107, "task_work": 256, "tiny_cap": 0, "block_bits_log2": 10},
 }
 
 
