@@ -138,7 +138,10 @@ typedef struct tc_tuning {
                                    bitmap in shared memory (one bit per rank, 2^k / 8 bytes), only the others
                                    in the cuckoo table; the rows stage puts every level-spanning part's ranks
                                    below 2^k first.  0 turns it off; else 10..19 */
-    uint32_t reserved;
+    uint32_t batch_small_slots; /* tc_count_batch / serving: graphs of at most 65536 vertices and at most this
+                                   many CSR slots are counted one thread block each, all in one launch; the
+                                   others as one disjoint union through the pipeline (0: all of them) */
+    uint32_t reserved[2];
 } tc_tuning;
 
 /* ------------------------------------------------------------------ context */

@@ -62,7 +62,7 @@ class tc_tuning(ctypes.Structure):
     _fields_ = [(k, ctypes.c_uint32) for k in (
         "warp_cap", "block_cap", "task_work", "warps_per_block", "block_threads", "warp_task_work",
         "hub_task_work", "max_v", "hub_group", "hub_filter_log2", "hub_threads", "tiny_cap",
-        "table_kind", "flat_cap", "block_bits_log2")] + [("reserved", ctypes.c_uint32)]
+        "table_kind", "flat_cap", "block_bits_log2", "batch_small_slots")] + [("reserved", ctypes.c_uint32 * 2)]
 
     def to_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

@@ -20,7 +20,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libtc.so")
 
 SOURCES = ["api.cu", "count.cu", "levels.cu", "rank.cu", "rows.cu", "isect.cu", "scan.cu", "csr.cu", "batch.cu", "serve.cu", "alg3.cu", "list.cu",
-           "noalloc.cu"]
+           "noalloc.cu", "graphs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

@@ -38,6 +38,9 @@ CANDIDATES = [
     {"block_cap": 13107},
     {"flat_cap": 0},
     {"flat_cap": 256},
+    {"batch_small_slots": 16384},
+    {"batch_small_slots": 65536},
+    {"batch_small_slots": 262144},
 ]
 
 

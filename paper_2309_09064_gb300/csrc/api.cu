@@ -178,6 +178,7 @@ tc_status tc_get_tuning(const tc_ctx *ctx, tc_tuning *out) {
     out->table_kind = t.table_kind;
     out->flat_cap = t.flat_cap;
     out->block_bits_log2 = t.block_bits_log2;
+    out->batch_small_slots = t.batch_small_slots;
     return TC_OK;
 }
 
@@ -199,6 +200,7 @@ tc_status tc_set_tuning(tc_ctx *ctx, const tc_tuning *t) {
     nt.table_kind = t->table_kind;
     nt.flat_cap = t->flat_cap;
     nt.block_bits_log2 = t->block_bits_log2;
+    nt.batch_small_slots = t->batch_small_slots;
     const size_t smem_limit = 227 * 1024;
     auto threads_ok = [](uint32_t x) { return x >= 64 && x <= 1024 && x % 32 == 0; };
     if (nt.warp_cap < 1 || nt.warp_cap > 4096 || nt.block_cap < nt.warp_cap || nt.block_cap > 16384 ||

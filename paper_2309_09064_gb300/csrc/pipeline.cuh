@@ -84,6 +84,19 @@ inline uint32_t g1_split_rank(const Tuning &tu) {
     return (tu.table_kind == 0 && tu.block_bits_log2) ? (1u << tu.block_bits_log2) : 0u;
 }
 
+// Batched form, one thread block per graph (graphs.cu): graphs of at most
+// kSmallN vertices and max_slots CSR slots.
+constexpr uint32_t kSmallN = 65536;
+bool small_graph_fits(const tc_graph *g, uint64_t max_slots);
+// Scratch bytes for G such graphs of at most nmax vertices and smax slots;
+// *blocks gets the grid.
+size_t small_graphs_bytes(const tc_ctx *ctx, uint32_t nmax, uint64_t smax, uint32_t G, uint32_t *blocks);
+// Count graphs[i], i in idx, into d_counts[i] (device) on the context's
+// stream, one launch, no synchronisation.
+tc_status count_small_graphs(tc_ctx *ctx, const tc_graph *const *graphs, const std::vector<uint32_t> &idx,
+                             unsigned long long *d_counts, char *scratch, size_t scratch_bytes,
+                             unsigned int **d_err);
+
 tc_status compute_levels(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t slots);
 // levels supplied by the caller (device uint32[n]): copied into b.L after the
 // check that they differ by at most one across every edge (TC_ERR_INVALID if not)

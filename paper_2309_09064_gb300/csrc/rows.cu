@@ -236,10 +236,12 @@ __global__ void __launch_bounds__(kFillThreads) k_row_fill(uint32_t n, const uin
 }
 
 // Rows of degree above kHugeRow, one block each (persistent over the list the
-// fill kernel built): a counting pass, then a writing pass with warp-
-// aggregated slot counters.  F and G1 come out in no particular order (the
-// intersections need none); A is written unsorted and listed for k_sort_big
-// (or left unsorted beyond kSortCap).
+// fill kernel built): a counting pass, then a writing pass over chunks of
+// blockDim neighbours whose positions come from the warps' ballots and a
+// prefix over the warps in order, so every part keeps CSR order and every
+// run writes the same rows (a count split into shards recomputes the rows
+// on each shard, and its tasks are slices of F(u): the shards must agree on
+// its order).  A is listed for k_sort_big (or left unsorted beyond kSortCap).
 template <bool kPacked>
 __global__ void __launch_bounds__(1024) k_row_fill_huge(const uint32_t *__restrict__ huge, Ctl *ctl,
                                                         const uint64_t *__restrict__ rp,
@@ -249,8 +251,9 @@ __global__ void __launch_bounds__(1024) k_row_fill_huge(const uint32_t *__restri
                                                         uint32_t *__restrict__ fcnt, uint32_t *__restrict__ gcnt,
                                                         uint4 *__restrict__ vmeta, uint32_t *__restrict__ big,
                                                         uint32_t g1_lo) {
-    __shared__ unsigned int cnt[4], pos[4];
-    const unsigned lane = lane_id();
+    __shared__ unsigned int cnt[4], base[4];
+    __shared__ unsigned int wcnt[32][4];  // this chunk's F, G1 (high), A, G1 (low) per warp
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const uint32_t nh = ctl->n_huge;
     for (uint32_t i = blockIdx.x; i < nh; i += gridDim.x) {
@@ -258,7 +261,7 @@ __global__ void __launch_bounds__(1024) k_row_fill_huge(const uint32_t *__restri
         const uint64_t b = rp[x];
         const uint32_t d = (uint32_t)(rp[x + 1] - b);
         const uint2 me = rank_level<kPacked>(lv, lvp, x);
-        if (threadIdx.x < 4) cnt[threadIdx.x] = pos[threadIdx.x] = 0;
+        if (threadIdx.x < 4) cnt[threadIdx.x] = base[threadIdx.x] = 0;
         __syncthreads();
         uint32_t f = 0, g = 0, gl = 0;
         for (uint32_t j = threadIdx.x; j < d; j += blockDim.x) {
@@ -280,39 +283,52 @@ __global__ void __launch_bounds__(1024) k_row_fill_huge(const uint32_t *__restri
         }
         __syncthreads();
         const uint32_t F = cnt[0], G = cnt[1], A = d - F - G;
-        const uint32_t j_end = (d + 31) & ~31u;
-        for (uint32_t j = threadIdx.x; j < j_end; j += blockDim.x) {  // whole warps take part
-            bool isF = false, isG = false, isA = false;
+        for (uint32_t j0 = 0; j0 < d; j0 += blockDim.x) {  // every thread takes part in every chunk
+            const uint32_t j = j0 + threadIdx.x;
+            bool isF = false, isG = false, isA = false, isL = false;
             uint32_t y = 0, ry = 0;
             if (j < d) {
                 y = col[b + j];
                 const uint2 q = rank_level<kPacked>(lv, lvp, y);
                 ry = q.x;
-                if (q.y != me.y) isG = true;
-                else if (me.x < ry) isF = true;
-                else isA = true;
+                if (q.y != me.y) {
+                    isL = ry < g1_lo;  // level-spanning, below g1_lo: right after A
+                    isG = !isL;
+                } else if (me.x < ry) {
+                    isF = true;
+                } else {
+                    isA = true;
+                }
             }
-            const bool isL = isG && ry < g1_lo;  // level-spanning, below g1_lo: right after A
-            isG = isG && !isL;
             const unsigned mF = __ballot_sync(0xFFFFFFFFu, isF);
             const unsigned mG = __ballot_sync(0xFFFFFFFFu, isG);
             const unsigned mA = __ballot_sync(0xFFFFFFFFu, isA);
             const unsigned mL = __ballot_sync(0xFFFFFFFFu, isL);
-            uint32_t bF = 0, bG = 0, bA = 0, bL = 0;
             if (lane == 0) {
-                if (mF) bF = atomicAdd(&pos[0], __popc(mF));
-                if (mG) bG = atomicAdd(&pos[1], __popc(mG));
-                if (mA) bA = atomicAdd(&pos[2], __popc(mA));
-                if (mL) bL = atomicAdd(&pos[3], __popc(mL));
+                wcnt[warp][0] = __popc(mF);
+                wcnt[warp][1] = __popc(mG);
+                wcnt[warp][2] = __popc(mA);
+                wcnt[warp][3] = __popc(mL);
             }
-            bF = __shfl_sync(0xFFFFFFFFu, bF, 0);
-            bG = __shfl_sync(0xFFFFFFFFu, bG, 0);
-            bA = __shfl_sync(0xFFFFFFFFu, bA, 0);
-            bL = __shfl_sync(0xFFFFFFFFu, bL, 0);
-            if (isF) adj2[b + bF + __popc(mF & lt)] = y;
-            if (isA) adj2[b + F + bA + __popc(mA & lt)] = ry;
-            if (isL) adj2[b + F + A + bL + __popc(mL & lt)] = ry;
-            if (isG) adj2[b + d - 1 - (bG + __popc(mG & lt))] = ry;
+            __syncthreads();
+            uint32_t pF = base[0], pG = base[1], pA = base[2], pL = base[3];
+            for (unsigned w = 0; w < warp; ++w) {
+                pF += wcnt[w][0];
+                pG += wcnt[w][1];
+                pA += wcnt[w][2];
+                pL += wcnt[w][3];
+            }
+            if (isF) adj2[b + pF + __popc(mF & lt)] = y;
+            if (isA) adj2[b + F + pA + __popc(mA & lt)] = ry;
+            if (isL) adj2[b + F + A + pL + __popc(mL & lt)] = ry;
+            if (isG) adj2[b + d - 1 - (pG + __popc(mG & lt))] = ry;
+            __syncthreads();
+            if (threadIdx.x < 4) {
+                uint32_t t = 0;
+                for (unsigned w = 0; w < nwarps; ++w) t += wcnt[w][threadIdx.x];
+                base[threadIdx.x] += t;
+            }
+            __syncthreads();
         }
         if (threadIdx.x == 0) {
             fcnt[x] = F;

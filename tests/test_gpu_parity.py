@@ -247,15 +247,28 @@ def batch_graphs(count, seed, n_hi=4096):
     return [spec.make() for spec in gg.batch_specs(count, seed=seed, n_hi=n_hi)]
 
 
-def test_batch_equals_loop_and_oracle(tc, ctx):
-    graphs = batch_graphs(96, seed=5) + [SMALL["empty0"], SMALL["isolated5"], SMALL["K40"]]
-    gs = [tc.tc_build_csr(ctx, *g[:3]) for g in graphs]
-    batched = tc.tc_count_batch(ctx, gs)
-    looped = [tc.tc_count(ctx, g)[0] for g in gs]
-    ref = [oracle.count_definition(*oracle.build_csr(*g[:3])) for g in graphs]
-    for g in gs:
-        tc.tc_graph_free(g)
-    assert list(batched) == looped == ref
+@pytest.mark.parametrize("small_slots", [0, 1 << 10, 1 << 22])
+@pytest.mark.parametrize("order_name", ["degree", "id"])
+def test_batch_equals_loop_and_oracle(tc, small_slots, order_name):
+    """Graphs up to small_slots CSR slots take the one-launch kernel (a block per
+    graph), the others the union pipeline (0: all of them), in one batch."""
+    order = tc.TC_ORDER_DEGREE if order_name == "degree" else tc.TC_ORDER_ID
+    c = tc.tc_create(0, order=order)
+    try:
+        tc.tc_set_tuning(c, batch_small_slots=small_slots)
+        graphs = batch_graphs(96, seed=5) + [SMALL[k] for k in ("empty0", "isolated5", "K40", "union", "wheel101",
+                                                                  "grid33x47", "tree300", "friendship50")]
+        gs = [tc.tc_build_csr(c, *g[:3]) for g in graphs]
+        batched = tc.tc_count_batch(c, gs)
+        again = tc.tc_count_batch(c, gs[::-1])
+        looped = [tc.tc_count(c, g)[0] for g in gs]
+        ref = [oracle.count_definition(*oracle.build_csr(*g[:3])) for g in graphs]
+        for g in gs:
+            tc.tc_graph_free(g)
+        assert list(batched) == looped == ref
+        assert list(again) == ref[::-1]
+    finally:
+        tc.tc_destroy(c)
 
 
 def test_served_results_alone_and_in_the_mix(tc):
@@ -361,6 +374,27 @@ def test_shards_sum_to_the_count(tc, ctx, nshards):
         parts = [tc.tc_count_shard(ctx, g, k, nshards)[0] for k in range(nshards)]
         tc.tc_graph_free(g)
         assert sum(parts) == T
+
+
+@pytest.mark.parametrize("nshards", [2, 3, 5, 8])
+def test_shards_agree_on_rows_of_degree_above_8192(tc, nshards):
+    """Every shard recomputes the rows, and its tasks are slices of F(u): the
+    block-filled rows (degree above 8192) must come out in the same order on
+    every run, or shards would cut a row's slices from different orders."""
+    c = tc.tc_create(0)
+    try:
+        tc.tc_set_tuning(c, warp_cap=64, block_cap=1024, task_work=4096, hub_task_work=4096, max_v=64)
+        n, s, d = gg.rmat(17, 16, seed=3)
+        g = tc.tc_build_csr(c, n, s, d)
+        assert tc.tc_graph_info(g)[1] > 0
+        T, st = tc.tc_count(c, g)
+        assert st["class_rows"][2] > nshards  # hub rows, split into many tasks
+        for _ in range(3):
+            parts = [tc.tc_count_shard(c, g, k, nshards)[0] for k in range(nshards)]
+            assert sum(parts) == T
+        tc.tc_graph_free(g)
+    finally:
+        tc.tc_destroy(c)
 
 
 def test_bounded_device_wait_times_out_and_context_survives(tc):
