@@ -134,10 +134,12 @@ typedef struct tc_tuning {
                                    tables (block_cap up to 16384) */
     uint32_t flat_cap;          /* warp class: probe ranges shorter than this are concatenated so that every
                                    lane of a warp has work; longer ones are walked range by range (0..4096) */
-    uint32_t block_bits_log2;   /* block class with cuckoo tables: the set's ranks below 2^k live in a direct
-                                   bitmap in shared memory (one bit per rank, 2^k / 8 bytes), only the others
-                                   in the cuckoo table; the rows stage puts every level-spanning part's ranks
-                                   below 2^k first.  0 turns it off; else 10..19 */
+    uint32_t block_bits_log2;   /* plain counts, block class with cuckoo tables: the set's ranks below 2^k
+                                   live in a direct bitmap in shared memory (one bit per rank, 2^k / 8 bytes),
+                                   only the others in the cuckoo table, which shrinks to fit beside it (rows
+                                   whose other ranks do not fit go to the hub class); the rows stage puts
+                                   every level-spanning part's ranks below 2^k first, and probe pieces below
+                                   and above 2^k take one kind of lookup each.  0 turns it off; else 10..20 */
     uint32_t batch_small_slots; /* tc_count_batch / serving: graphs of at most 65536 vertices and at most this
                                    many CSR slots are counted one thread block each, all in one launch; the
                                    others as one disjoint union through the pipeline (0: all of them) */

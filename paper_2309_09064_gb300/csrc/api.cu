@@ -208,7 +208,7 @@ tc_status tc_set_tuning(tc_ctx *ctx, const tc_tuning *t) {
         nt.warps_per_block > 8 || !threads_ok(nt.block_threads) || !threads_ok(nt.hub_threads) || nt.max_v < 64 ||
         nt.max_v > 4096 || nt.hub_group < 1 || nt.hub_group > 64 || nt.hub_filter_log2 < 10 ||
         nt.hub_filter_log2 > 20 || nt.tiny_cap > 64 || nt.table_kind > 1 || nt.flat_cap > 4096 ||
-        (nt.block_bits_log2 != 0 && (nt.block_bits_log2 < 10 || nt.block_bits_log2 > 19)) || warp_kernel_smem(nt) > smem_limit || block_kernel_smem(nt) > smem_limit ||
+        (nt.block_bits_log2 != 0 && (nt.block_bits_log2 < 10 || nt.block_bits_log2 > 20)) || warp_kernel_smem(nt) > smem_limit || block_kernel_smem(nt) > smem_limit ||
         hub_kernel_smem(nt) > smem_limit)
         return set_error(ctx, TC_ERR_INVALID, "tuning out of range");
     ctx->tune = nt;

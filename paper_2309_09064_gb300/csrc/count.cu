@@ -40,7 +40,7 @@ size_t pipeline_bytes(const tc_ctx *ctx, uint32_t n, uint64_t slots, uint32_t ma
     const size_t n1 = (size_t)n + 1;
     const uint64_t rtiles = radix_tiles(n1);
     size_t bytes = 0;
-    bytes += 19 * r(4 * n1);                       // deg q0 q1 fdeg R parent fcnt gcnt rank big huge lvp rows[4] ntask[3]
+    bytes += 21 * r(4 * n1);                       // deg q0 q1 fdeg R parent fcnt gcnt rank big huge lvp glo part rows[4] ntask[3]
     bytes += r(16 * n1);                           // vmeta
     bytes += r(4 * (slots / 2 / 256 + 2));         // chunk_row
     if (own_levels) bytes += r(4 * n1);            // L
@@ -114,11 +114,16 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     b.rank = a.take<uint32_t>(n1);
     b.big = a.take<uint32_t>(n1);
     b.huge = a.take<uint32_t>(n1);
+    b.glo = a.take<uint32_t>(n1);
+    b.part = a.take<uint32_t>(n1);
     uint32_t *lvp = a.take<uint32_t>(n1);
     b.vmeta = a.take<uint4>(n1);
     b.chunk_row = a.take<uint32_t>(g.slots / 2 / 256 + 2);
     bool ok = b.deg && b.L && b.q0 && b.q1 && b.fdeg && b.R && b.parent && b.fcnt && b.gcnt && b.rank && b.big &&
-              b.huge && lvp && b.vmeta && b.chunk_row;
+              b.huge && b.glo && b.part && lvp && b.vmeta && b.chunk_row;
+    // the split set serves the plain count; the per-vertex counts, the listing
+    // and Algorithm 3 keep their shared memory for their own use
+    ctx->split_R = (vertex_counts || list || alg3) ? 0u : g1_split_rank(ctx->tune);
     b.rows[3] = a.take<uint32_t>(n1);
     ok = ok && b.rows[3];
     for (int c = 0; c < 3; ++c) {

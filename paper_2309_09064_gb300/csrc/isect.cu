@@ -455,6 +455,18 @@ struct SplitSet {
     uint32_t R;     // ranks below R are in the bitmap (a power of two, or 0: none)
 };
 
+// The bitmap part of a split set alone: probe pieces whose ids are all below
+// R (the low part of a range the rows stage split) need one shared load per
+// id.  Tail steps clamp the padding's word index and reject it.
+struct BitmapSet {
+    static constexpr int kUnroll = 8;
+    static constexpr int kBatch = 8;
+    static constexpr uint32_t kPad = kNone;
+    static constexpr bool kFineTail = false;
+    uint32_t bm;  // shared-window byte address of the bitmap
+    uint32_t R;   // its size in bits
+};
+
 // Hub rows: shared prefilter (2^hub_filter_log2 bits) in front of the exact
 // n-bit bitmap (by rank) in global memory.
 struct HubSet {
@@ -548,7 +560,7 @@ __device__ __forceinline__ void count_step(const bool (&hit)[U], uint32_t j0, ui
     }
 }
 
-template <int U, class Set>
+template <int U, bool kTail = false, class Set>
 __device__ __forceinline__ void lookup_step(const Set &set, const uint32_t (&w)[U], bool (&hit)[U]) {
     constexpr int B = Set::kBatch < U ? Set::kBatch : U;
     static_assert(U % B == 0, "the unroll must be a multiple of the lookup batch");
@@ -567,7 +579,23 @@ __device__ __forceinline__ void lookup_step(const Set &set, const uint32_t (&w)[
 // One warp step against a split set: a vote picks the bitmap alone (every
 // lane's ids below R, padding included), the table alone (every id at or
 // above R), or both, lane by lane.  The stash holds only ranks >= R.
-template <int U>
+template <int U, bool kTail = false>
+__device__ __forceinline__ void lookup_step(const BitmapSet &B, const uint32_t (&w)[U], bool (&hit)[U]) {
+    uint32_t x[U];
+    if constexpr (kTail) {
+#pragma unroll
+        for (int i = 0; i < U; ++i) x[i] = lds_u32(B.bm + (((w[i] < B.R ? w[i] : 0u) >> 5) << 2));
+#pragma unroll
+        for (int i = 0; i < U; ++i) hit[i] = w[i] < B.R && ((x[i] >> (w[i] & 31u)) & 1u);
+    } else {
+#pragma unroll
+        for (int i = 0; i < U; ++i) x[i] = lds_u32(B.bm + ((w[i] >> 5) << 2));
+#pragma unroll
+        for (int i = 0; i < U; ++i) hit[i] = (x[i] >> (w[i] & 31u)) & 1u;
+    }
+}
+
+template <int U, bool kTail = false>
 __device__ __forceinline__ void lookup_step(const SplitSet &S, const uint32_t (&w)[U], bool (&hit)[U]) {
     bool lo_all = true, hi_all = true;
 #pragma unroll
@@ -641,7 +669,7 @@ __device__ __forceinline__ uint32_t probe_row(const Set &set, const uint32_t *__
             const uint32_t j = j0 + (uint32_t)i * 32u;
             w[i] = j + lane < j_hi ? __ldg(row + j) : Set::kPad;
         }
-        lookup_step<T>(set, w, hit);
+        lookup_step<T, true>(set, w, hit);
         if constexpr (kM == 1) credit_third<T>(hit, w, vo);
         if constexpr (kM == 2) emit_step<T, false, kStage>(hit, w, w, vo, *lc);
         count_step<T>(hit, j0, split, lane, same, cross);
@@ -785,8 +813,8 @@ __device__ __forceinline__ uint32_t cuckoo_slots_for(uint32_t s, uint32_t m_cap)
 // cleared first) and only the others enter the table.
 __device__ __forceinline__ CuckooTable cuckoo_build(uint32_t *t, uint32_t m_cap, const uint32_t *__restrict__ row,
                                                     uint32_t s, CuckooShared *cs, unsigned int *err,
-                                                    uint32_t *bm = nullptr, uint32_t R = 0) {
-    const uint32_t m = cuckoo_slots_for(s, m_cap);
+                                                    uint32_t *bm = nullptr, uint32_t R = 0, uint32_t table_keys = 0) {
+    const uint32_t m = cuckoo_slots_for(R ? table_keys : s, m_cap);
     CuckooTable C{t, cs->stash, m, (uint32_t)__clz(m) + 1u, 0, 0, 0, shared_addr(t), shared_addr(t + m)};
     for (uint32_t j = threadIdx.x; j < (R >> 5); j += blockDim.x) bm[j] = 0u;
     for (int attempt = 0; attempt < kCuckooAttempts; ++attempt) {
@@ -1109,6 +1137,7 @@ __global__ void __launch_bounds__(256) k_isect_tiny(const uint32_t *__restrict__
 struct SliceSmem {
     unsigned long long *b;
     uint32_t *len, *h, *seg, *v;  // v: probed vertex of each range (per-vertex counts and listing only)
+    uint32_t *q;                  // split sets: end of the range's ids below the split rank (kNoSplit: unknown)
 };
 
 __device__ __forceinline__ SliceSmem carve_slice(unsigned char *p, uint32_t max_v) {
@@ -1118,21 +1147,30 @@ __device__ __forceinline__ SliceSmem carve_slice(unsigned char *p, uint32_t max_
     s.h = s.len + max_v;
     s.seg = s.h + max_v;
     s.v = s.seg + max_v + 1;
+    s.q = s.v + max_v;
     return s;
 }
 
-__host__ __device__ constexpr size_t slice_smem_bytes(uint32_t max_v) { return (24ull * max_v + 4 + 15) & ~15ull; }
+__host__ __device__ constexpr size_t slice_smem_bytes(uint32_t max_v) { return (28ull * max_v + 4 + 15) & ~15ull; }
+
+// Pieces of one probe range: kSeg positions each; a split range (q known) is
+// cut into its low part [0, q) and its high part [q, len) separately.
+__device__ __forceinline__ uint32_t range_pieces(uint32_t len, uint32_t q) {
+    if (q == kNoSplit) return (len + kSeg - 1) / kSeg;
+    return (q + kSeg - 1) / kSeg + (len - q + kSeg - 1) / kSeg;
+}
 
 // Block-wide exclusive scan of the piece counts of ranges 0..nv-1 into
 // seg[0..nv]; all threads of the block call it; ends with a barrier.
-__device__ __forceinline__ void scan_segments(const uint32_t *len, uint32_t *seg, uint32_t nv) {
+__device__ __forceinline__ void scan_segments(const uint32_t *len, uint32_t *seg, uint32_t nv,
+                                              const uint32_t *q = nullptr) {
     __shared__ uint32_t warp_tot[32];
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const uint32_t per = (nv + blockDim.x - 1) / blockDim.x;  // ranges per thread (contiguous)
     const uint32_t beg = threadIdx.x * per;
     uint32_t sum = 0;
     for (uint32_t i = 0; i < per; ++i)
-        if (beg + i < nv) sum += (len[beg + i] + kSeg - 1) / kSeg;
+        if (beg + i < nv) sum += q ? range_pieces(len[beg + i], q[beg + i]) : (len[beg + i] + kSeg - 1) / kSeg;
     uint32_t x = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -1155,7 +1193,7 @@ __device__ __forceinline__ void scan_segments(const uint32_t *len, uint32_t *seg
     for (uint32_t i = 0; i < per; ++i) {
         if (beg + i < nv) {
             seg[beg + i] = run;
-            run += (len[beg + i] + kSeg - 1) / kSeg;
+            run += q ? range_pieces(len[beg + i], q[beg + i]) : (len[beg + i] + kSeg - 1) / kSeg;
         }
     }
     if (threadIdx.x == 0) seg[nv] = warp_tot[nwarps - 1];
@@ -1165,15 +1203,25 @@ __device__ __forceinline__ void scan_segments(const uint32_t *len, uint32_t *seg
 // Load the probe records of edges k in [k_lo, k_hi) of one row (no barrier),
 // and with per-vertex counts or listing the probed vertices (F of the row, at
 // frow).
-template <int kM>
+template <int kM, bool kSplit = false>
 __device__ __forceinline__ void load_slice(const SliceSmem &S, const uint4 *__restrict__ rec, uint32_t k_lo,
-                                           uint32_t k_hi, const uint32_t *__restrict__ frow) {
+                                           uint32_t k_hi, const uint32_t *__restrict__ frow,
+                                           const uint32_t *__restrict__ glo = nullptr, bool tail_lo = false) {
     for (uint32_t i = threadIdx.x; i < k_hi - k_lo; i += blockDim.x) {
         const uint4 r = rec[k_lo + i];
         S.b[i] = rec_start(r);
         S.len[i] = r.z;
         S.h[i] = r.w;
-        if constexpr (kM != 0) S.v[i] = frow[k_lo + i];
+        if constexpr (kM != 0 || kSplit) {
+            const uint32_t v = frow[k_lo + i];
+            if constexpr (kM != 0) S.v[i] = v;
+            if constexpr (kSplit) {
+                // the range is [A tail | G1 low | G1 high]: its ids below the split rank
+                // end after G1's low part when the A tail (ranks below u's) is low too
+                const uint32_t gl = glo[v];
+                S.q[i] = (tail_lo && gl != kNoSplit) ? r.w + gl : kNoSplit;
+            }
+        }
     }
 }
 
@@ -1219,6 +1267,77 @@ __device__ __forceinline__ void probe_slice(const Set &set, const SliceSmem &S, 
             const uint32_t ht = __shfl_sync(0xFFFFFFFFu, h, t);
             if constexpr (kM == 2) lc.v = __shfl_sync(0xFFFFFFFFu, vid, t);
             uint32_t got = probe_row<Set::kUnroll, Set::kFineTail, kM, true>(set, adj2, bt, lo, hi, ht, acc, vo, &lc);
+            if constexpr (kM == 1) {
+                got = warp_sum(got);
+                const uint32_t vt = __shfl_sync(0xFFFFFFFFu, vid, t);
+                if (lane == 0 && got) atomicAdd(vo.tid + vt, (unsigned long long)got);
+            }
+        }
+    }
+}
+
+// probe_slice for a split set: a piece of a split range lies wholly in its
+// low part (bitmap lookups only) or wholly in its high part (cuckoo table
+// only); pieces of ranges whose split is unknown take both, lane by lane.
+template <int kM = 0>
+__device__ __forceinline__ void probe_slice_split(const SplitSet &set, const SliceSmem &S, uint32_t nv,
+                                                  const uint32_t *__restrict__ adj2, unsigned int *next, Acc &acc,
+                                                  const VertexOut &vo, ListCtx &lc) {
+    const unsigned lane = lane_id();
+    const uint32_t total = S.seg[nv];
+    const uint32_t nwarps = blockDim.x >> 5;
+    uint32_t batch = total / (4 * nwarps);
+    batch = batch < 1 ? 1 : (batch > 32 ? 32 : batch);
+    const BitmapSet B{set.bm, set.R};
+    for (;;) {
+        uint32_t g0 = 0;
+        if (lane == 0) g0 = atomicAdd(next, batch);
+        g0 = __shfl_sync(0xFFFFFFFFu, g0, 0);
+        if (g0 >= total) break;
+        const uint32_t cnt = min(batch, total - g0);
+        unsigned long long b = 0;
+        uint32_t j_lo = 0, j_hi = 0, h = 0, vid = 0, kind = 0;  // kind: 0 both, 1 low part, 2 high part
+        if (lane < cnt) {
+            const uint32_t g = g0 + lane;
+            uint32_t a = 0, e = nv;  // range of piece g: largest t with seg[t] <= g
+            while (e - a > 1) {
+                const uint32_t m = (a + e) >> 1;
+                if (S.seg[m] <= g) a = m; else e = m;
+            }
+            uint32_t l = g - S.seg[a];
+            const uint32_t len = S.len[a], q = S.q[a];
+            if (q == kNoSplit) {
+                j_lo = l * kSeg;
+                j_hi = min(len, j_lo + kSeg);
+            } else {
+                const uint32_t nlo = (q + kSeg - 1) / kSeg;
+                if (l < nlo) {
+                    j_lo = l * kSeg;
+                    j_hi = min(q, j_lo + kSeg);
+                    kind = 1;
+                } else {
+                    l -= nlo;
+                    j_lo = q + l * kSeg;
+                    j_hi = min(len, j_lo + kSeg);
+                    kind = 2;
+                }
+            }
+            b = S.b[a];
+            h = S.h[a];
+            if constexpr (kM != 0) vid = S.v[a];
+            acc.probes += j_hi - j_lo;
+        }
+        for (uint32_t t = 0; t < cnt; ++t) {
+            const unsigned long long bt = __shfl_sync(0xFFFFFFFFu, b, t);
+            const uint32_t lo = __shfl_sync(0xFFFFFFFFu, j_lo, t);
+            const uint32_t hi = __shfl_sync(0xFFFFFFFFu, j_hi, t);
+            const uint32_t ht = __shfl_sync(0xFFFFFFFFu, h, t);
+            const uint32_t kt = __shfl_sync(0xFFFFFFFFu, kind, t);
+            if constexpr (kM == 2) lc.v = __shfl_sync(0xFFFFFFFFu, vid, t);
+            uint32_t got;
+            if (kt == 1) got = probe_row<BitmapSet::kUnroll, false, kM, true>(B, adj2, bt, lo, hi, ht, acc, vo, &lc);
+            else if (kt == 2) got = probe_row<CuckooTable::kUnroll, false, kM, true>(set.C, adj2, bt, lo, hi, ht, acc, vo, &lc);
+            else got = probe_row<SplitSet::kUnroll, false, kM, true>(set, adj2, bt, lo, hi, ht, acc, vo, &lc);
             if constexpr (kM == 1) {
                 got = warp_sum(got);
                 const uint32_t vt = __shfl_sync(0xFFFFFFFFu, vid, t);
@@ -1298,7 +1417,9 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
                                                       const uint64_t *__restrict__ eoff,
                                                       const uint4 *__restrict__ erec, Ctl *ctl, uint32_t max_v,
                                                       uint32_t table_units, uint32_t split_R,
-                                                      unsigned long long chunk,
+                                                      const uint32_t *__restrict__ glo,
+                                                      const uint32_t *__restrict__ gcnt,
+                                                      const uint2 *__restrict__ lv, unsigned long long chunk,
                                                       unsigned long long first, unsigned long long last,
                                                       GroupSpec groups, VertexOut vo) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1337,12 +1458,16 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
         const bool rebuild = task.x != cur_row;
         if constexpr (!kCuckoo)
             if (rebuild) T = clear_table(T.bk, su, table_units, threadIdx.x, blockDim.x, &ctl->error);
-        load_slice<kM>(S, erec + eoff[u], k_lo, k_hi, adj2 + (hb - fu));
+        // split set: u's own A part holds ranks below u's, all low when u is ranked below split_R
+        const bool tail_lo = kSet == 2 && lv[u].x <= split_R;
+        load_slice<kM, kSet == 2>(S, erec + eoff[u], k_lo, k_hi, adj2 + (hb - fu), glo, tail_lo);
         __syncthreads();
-        scan_segments(S.len, S.seg, k_hi - k_lo);
+        scan_segments(S.len, S.seg, k_hi - k_lo, kSet == 2 ? S.q : nullptr);
         if (rebuild) {
             if constexpr (kSet == 2) {
-                C = cuckoo_build(C.t, table_units, adj2 + hb, su, &cs, &ctl->error, bmp, split_R);
+                const uint32_t g = gcnt[u], gl = glo[u];
+                const uint32_t hi_keys = (gl == kNoSplit ? g : g - gl) + (tail_lo ? 0u : su - g);
+                C = cuckoo_build(C.t, table_units, adj2 + hb, su, &cs, &ctl->error, bmp, split_R, hi_keys);
             } else if constexpr (kCuckoo) {
                 C = cuckoo_build(C.t, table_units, adj2 + hb, su, &cs, &ctl->error);
             } else {
@@ -1359,7 +1484,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
         const unsigned long long before = acc.same + acc.cross;
         lc.u = u;
         if constexpr (kSet == 2)
-            probe_slice<kM>(SplitSet{C, shared_addr(bmp), split_R}, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);
+            probe_slice_split<kM>(SplitSet{C, shared_addr(bmp), split_R}, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);
         else if constexpr (kCuckoo) probe_slice<kM>(C, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);
         else probe_slice<kM>(T, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);
         finish_task<kM>(acc.same + acc.cross - before, groups, vo, ts, u);
@@ -1480,14 +1605,29 @@ uint32_t block_table_units(const Tuning &tu) {
 size_t warp_kernel_smem(const Tuning &tu) {
     return (size_t)tu.warps_per_block * (warp_set_bytes(tu.table_kind == 0, warp_table_units(tu)) + kWarpMetaBytes);
 }
+// With a split rank R the cuckoo table shares shared memory with the R-bit
+// bitmap: the largest power-of-two table that fits beside it (and the task
+// metadata), at most the size the class cap needs.
+uint32_t block_units_for(const Tuning &tu, uint32_t R) {
+    const uint32_t full = block_table_units(tu);
+    if (!R || tu.table_kind != 0) return full;
+    const size_t fixed = slice_smem_bytes(tu.max_v) + R / 8 + 2048;  // 2 KB: static shared memory and margin
+    uint32_t m = full;
+    while (m > 64 && fixed + 8ull * m > kSmemLimitBytes) m >>= 1;
+    return m;
+}
+uint32_t block_hi_cap(const Tuning &tu, uint32_t R) {
+    const uint32_t m = block_units_for(tu, R);
+    return R ? (uint32_t)((uint64_t)m * 4 / 5) : tu.block_cap;
+}
 size_t block_kernel_smem(const Tuning &tu) {
-    return slice_smem_bytes(tu.max_v) + (tu.table_kind == 0 ? 8ull : 16ull) * block_table_units(tu) +
-           g1_split_rank(tu) / 8;
+    const uint32_t R = g1_split_rank(tu);
+    return slice_smem_bytes(tu.max_v) + (tu.table_kind == 0 ? 8ull : 16ull) * block_units_for(tu, R) + R / 8;
 }
 size_t hub_kernel_smem(const Tuning &tu) { return slice_smem_bytes(tu.max_v) + (1ull << tu.hub_filter_log2) / 8; }
 
 // Shared memory one block may opt into on sm_103a.
-constexpr size_t kSmemLimit = 227 * 1024;
+constexpr size_t kSmemLimit = kSmemLimitBytes;
 
 tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
     (void)n;
@@ -1577,20 +1717,17 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[5], s));
     if (hi1 > lo1) {
-        // split set: the bitmap shrinks (halves) where the mode's own shared memory needs the room
+        // split set (plain counts only): the bitmap sits after the cuckoo table
         const size_t extra = priv + (mode == 2 ? 4ull * kStageSlots * (tu.block_threads / 32) : 0);
-        uint32_t split_R = g1_split_rank(tu);
-        const size_t base_smem = block_kernel_smem(tu) - split_R / 8;
-        while (split_R >= 1024 && base_smem + split_R / 8 + extra > kSmemLimit) split_R >>= 1;
-        if (split_R < 1024) split_R = 0;
-        const size_t smem = base_smem + split_R / 8 + extra;
+        const uint32_t split_R = ctx->split_R;
+        const uint32_t units = block_units_for(tu, split_R);
+        const size_t smem =
+            slice_smem_bytes(tu.max_v) + (tu.table_kind == 0 ? 8ull : 16ull) * units + split_R / 8 + extra;
         if (smem > kSmemLimit) return set_error(ctx, TC_ERR_INVALID, "tuning leaves no shared memory for this mode");
         auto kern = tu.table_kind == 1 ? (mode == 0   ? k_isect_block<1, 0>
                                           : mode == 1 ? k_isect_block<1, 1>
                                                       : k_isect_block<1, 2>)
-                    : split_R         ? (mode == 0   ? k_isect_block<2, 0>
-                                          : mode == 1 ? k_isect_block<2, 1>
-                                                      : k_isect_block<2, 2>)
+                    : split_R         ? k_isect_block<2, 0>  // split sets serve plain counts only
                                       : (mode == 0   ? k_isect_block<0, 0>
                                           : mode == 1 ? k_isect_block<0, 1>
                                                       : k_isect_block<0, 2>);
@@ -1603,8 +1740,8 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         grid = list_grid(grid, tu.block_threads / 32);
         const unsigned long long chunk = std::max<unsigned long long>(1, (hi1 - lo1) / (grid * 8));
         kern<<<(unsigned)grid, tu.block_threads, smem, s>>>(b.tasks[1], b.rows[1], b.ntask[1], b.rp, b.adj2, b.fcnt,
-                                                            b.eoff, b.erec, ctx->d_ctl, tu.max_v, block_table_units(tu),
-                                                            split_R, chunk, lo1, hi1, b.groups, vo);
+                                                            b.eoff, b.erec, ctx->d_ctl, tu.max_v, units, split_R,
+                                                            b.glo, b.gcnt, b.lv, chunk, lo1, hi1, b.groups, vo);
         note_launch(ctx);
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[6], s));

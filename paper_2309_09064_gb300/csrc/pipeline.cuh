@@ -38,6 +38,8 @@ struct PipeBufs {
     uint32_t *big = nullptr;        // [n]   rows whose A part the block sorter sorts
     uint32_t *huge = nullptr;       // [n]   rows of very high degree (filled by a block each)
     uint4 *vmeta = nullptr;         // [n]   {A start lo, A start hi, |A(x)|, |G1(x)|}
+    uint32_t *glo = nullptr;        // [n]   ranks of G1(x) below the split rank, placed first (kNoSplit: not split)
+    uint32_t *part = nullptr;       // [n]   rows whose G1 part k_g1_split splits
     uint32_t *chunk_row = nullptr;  // first row of every chunk of kRecChunk probe records
     uint64_t *eoff = nullptr;       // [n+1] exclusive prefix of fcnt: first probe record of x
     uint4 *erec = nullptr;          // [|E0|] probe record per oriented horizontal edge u -> v:
@@ -80,9 +82,17 @@ struct PipeBufs {
 
 // Ranks below this value are kept in the block class's shared bitmap, and
 // the rows stage puts them first in every level-spanning part (0: no split).
+// A count uses it for the plain count only (ctx->split_R); the per-vertex
+// counts and the listing keep their shared memory for their own staging.
 inline uint32_t g1_split_rank(const Tuning &tu) {
     return (tu.table_kind == 0 && tu.block_bits_log2) ? (1u << tu.block_bits_log2) : 0u;
 }
+constexpr uint32_t kNoSplit = 0xFFFFFFFFu;  // glo[x]: G1(x) was not split
+constexpr size_t kSmemLimitBytes = 227 * 1024;  // shared memory one block may opt into on sm_103a
+// Cuckoo slots per table of the block class and the most ranks at or above
+// R one block-class set may hold (R = 0: no split, the whole set).
+uint32_t block_units_for(const Tuning &tu, uint32_t R);
+uint32_t block_hi_cap(const Tuning &tu, uint32_t R);
 
 // Batched form, one thread block per graph (graphs.cu): graphs of at most
 // kSmallN vertices and max_slots CSR slots.

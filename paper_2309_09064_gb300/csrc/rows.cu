@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(kFillThreads) k_row_fill(uint32_t n, const uin
                                                            const uint32_t *__restrict__ lvp, uint32_t *__restrict__ adj2,
                                                            uint32_t *__restrict__ fcnt, uint32_t *__restrict__ gcnt,
                                                            uint4 *__restrict__ vmeta, uint32_t *__restrict__ big,
-                                                           uint32_t *__restrict__ huge, Ctl *ctl, uint32_t g1_lo) {
+                                                           uint32_t *__restrict__ huge, Ctl *ctl, uint32_t g1_lo,
+                                                           uint32_t *__restrict__ glo, uint32_t *__restrict__ part) {
     __shared__ uint32_t sbuf[kFillThreads / 32][kWarpA];
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(kFillThreads) k_row_fill(uint32_t n, const uin
             gp += gl;
             fcnt[x] = fp;
             gcnt[x] = gp;
+            glo[x] = gl;
             const uint64_t as = b + fp;
             vmeta[x] = make_uint4((uint32_t)as, (uint32_t)(as >> 32), ap, gp);
         }
@@ -200,7 +202,11 @@ __global__ void __launch_bounds__(kFillThreads) k_row_fill(uint32_t n, const uin
                 if (lane == 0 && ap <= kSortCap) big[atomicAdd(&ctl->n_big, 1u)] = bx;
             }
             __syncwarp();
-            if (g1_lo && gp > 1 && gp <= kWarpA) {
+            uint32_t row_glo = 0;
+            if (g1_lo && gp > kWarpA) {  // split by k_g1_split (a block each)
+                if (lane == 0) part[atomicAdd(&ctl->n_part, 1u)] = bx;
+                row_glo = kNoSplit;
+            } else if (g1_lo && gp > 0) {
                 // G1 (written from the back) through the warp's buffer, back in place
                 // with its ranks below g1_lo first
                 const uint64_t gb = bb + bd - gp;
@@ -224,10 +230,12 @@ __global__ void __launch_bounds__(kFillThreads) k_row_fill(uint32_t n, const uin
                     hp += __popc(mh);
                 }
                 __syncwarp();
+                row_glo = nlo;
             }
             if (lane == 0) {
                 fcnt[bx] = fp;
                 gcnt[bx] = gp;
+                glo[bx] = row_glo;
                 const uint64_t as = bb + fp;
                 vmeta[bx] = make_uint4((uint32_t)as, (uint32_t)(as >> 32), ap, gp);
             }
@@ -250,7 +258,7 @@ __global__ void __launch_bounds__(1024) k_row_fill_huge(const uint32_t *__restri
                                                         const uint32_t *__restrict__ lvp, uint32_t *__restrict__ adj2,
                                                         uint32_t *__restrict__ fcnt, uint32_t *__restrict__ gcnt,
                                                         uint4 *__restrict__ vmeta, uint32_t *__restrict__ big,
-                                                        uint32_t g1_lo) {
+                                                        uint32_t g1_lo, uint32_t *__restrict__ glo) {
     __shared__ unsigned int cnt[4], base[4];
     __shared__ unsigned int wcnt[32][4];  // this chunk's F, G1 (high), A, G1 (low) per warp
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -333,10 +341,77 @@ __global__ void __launch_bounds__(1024) k_row_fill_huge(const uint32_t *__restri
         if (threadIdx.x == 0) {
             fcnt[x] = F;
             gcnt[x] = G;
+            glo[x] = cnt[3];
             const uint64_t as = b + F;
             vmeta[x] = make_uint4((uint32_t)as, (uint32_t)(as >> 32), A, G);
             if (A > 1 && A <= kSortCap) big[atomicAdd(&ctl->n_big, 1u)] = x;
         }
+        __syncthreads();
+    }
+}
+
+// Level-spanning parts of more than kWarpA ranks in warp-filled rows (at most
+// kHugeRow): one block per listed row stages the part in shared memory and
+// writes it back with its ranks below g1_lo first, each side in its former
+// order (positions from the warps' ballots and a prefix over the warps).
+__global__ void __launch_bounds__(1024) k_g1_split(const uint32_t *__restrict__ part, const Ctl *ctl,
+                                                   const uint64_t *__restrict__ rp, const uint32_t *__restrict__ gcnt,
+                                                   uint32_t *__restrict__ adj2, uint32_t g1_lo,
+                                                   uint32_t *__restrict__ glo) {
+    extern __shared__ uint32_t sg[];  // kHugeRow ranks
+    __shared__ unsigned int wcnt[32][2], base[2], nlo;
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t np = ctl->n_part;
+    for (uint32_t i = blockIdx.x; i < np; i += gridDim.x) {
+        const uint32_t x = part[i];
+        const uint32_t g = gcnt[x];
+        if (threadIdx.x == 0) {
+            base[0] = base[1] = 0;
+            nlo = 0;
+        }
+        __syncthreads();
+        if (g > kHugeRow) {  // not a row the fill kernel listed: leave it unsplit
+            if (threadIdx.x == 0) glo[x] = kNoSplit;
+            continue;
+        }
+        const uint64_t gb = rp[x + 1] - g;
+        uint32_t c = 0;
+        for (uint32_t j = threadIdx.x; j < g; j += blockDim.x) {
+            const uint32_t r = adj2[gb + j];
+            sg[j] = r;
+            c += r < g1_lo;
+        }
+        c = warp_sum(c);
+        if (lane == 0) atomicAdd(&nlo, c);
+        __syncthreads();
+        const uint32_t L = nlo;
+        for (uint32_t j0 = 0; j0 < g; j0 += blockDim.x) {
+            const uint32_t j = j0 + threadIdx.x;
+            const uint32_t r = j < g ? sg[j] : 0u;
+            const bool lo = j < g && r < g1_lo, hi = j < g && r >= g1_lo;
+            const unsigned ml = __ballot_sync(0xFFFFFFFFu, lo), mh = __ballot_sync(0xFFFFFFFFu, hi);
+            if (lane == 0) {
+                wcnt[warp][0] = __popc(ml);
+                wcnt[warp][1] = __popc(mh);
+            }
+            __syncthreads();
+            uint32_t pl = base[0], ph = base[1];
+            for (unsigned w = 0; w < warp; ++w) {
+                pl += wcnt[w][0];
+                ph += wcnt[w][1];
+            }
+            if (lo) adj2[gb + pl + __popc(ml & lt)] = r;
+            if (hi) adj2[gb + L + ph + __popc(mh & lt)] = r;
+            __syncthreads();
+            if (threadIdx.x < 2) {
+                uint32_t t = 0;
+                for (unsigned w = 0; w < nwarps; ++w) t += wcnt[w][threadIdx.x];
+                base[threadIdx.x] += t;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) glo[x] = L;
         __syncthreads();
     }
 }
@@ -390,9 +465,14 @@ __global__ void __launch_bounds__(1024) k_sort_big(const uint32_t *__restrict__ 
 // |G1(v)| per edge), so it takes only rows whose G1 part is short.
 constexpr uint32_t kTinyG = 8;
 
+// With a split rank R the block class also needs the set's ranks at or above
+// R (the ones its cuckoo table holds) to number at most hi_cap: G1's high part,
+// and all of A(x) when x itself is ranked at or above R (A holds ranks below
+// x's); a G1 part left unsplit counts whole.
 __global__ void k_class_flags(uint32_t n, const uint32_t *__restrict__ fcnt, const uint32_t *__restrict__ gcnt,
                               const uint32_t *__restrict__ deg, uint32_t *__restrict__ cls, Ctl *ctl,
-                              uint32_t warp_cap, uint32_t block_cap, uint32_t tiny_cap) {
+                              uint32_t warp_cap, uint32_t block_cap, uint32_t tiny_cap, uint32_t R, uint32_t hi_cap,
+                              const uint32_t *__restrict__ glo, const uint2 *__restrict__ lv) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     unsigned my_max = 0;
     for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
@@ -400,7 +480,13 @@ __global__ void k_class_flags(uint32_t n, const uint32_t *__restrict__ fcnt, con
         const uint32_t f = fcnt[x];
         if (f > 0) {
             const uint32_t s = deg[x] - f;
-            c = s <= warp_cap ? 0u : (s <= block_cap ? 1u : 2u);
+            bool fits = s <= block_cap;
+            if (R && fits && s > warp_cap) {
+                const uint32_t g = gcnt[x], gl = glo[x];
+                const uint32_t hi = (gl == kNoSplit ? g : g - gl) + (lv[x].x >= R ? s - g : 0u);
+                fits = hi <= hi_cap;
+            }
+            c = s <= warp_cap ? 0u : (fits ? 1u : 2u);
             if (s <= tiny_cap && deg[x] <= 4 * tiny_cap && gcnt[x] <= kTinyG) c = 3;
             if (c == 1 || c == 2) my_max = s > my_max ? s : my_max;
         }
@@ -594,21 +680,30 @@ tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_de
     const Tuning &tu = ctx->tune;
     if (n == 0) return TC_OK;
     uint32_t launches = 1;
-    const uint32_t g1_lo = g1_split_rank(tu);
+    const uint32_t g1_lo = ctx->split_R;
     if (b.lvp)
         k_row_fill<true><<<grid_for(n, kFillThreads, cap), kFillThreads, 0, s>>>(
-            n, b.rp, b.col, b.lv, b.lvp, b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big, b.huge, ctx->d_ctl, g1_lo);
+            n, b.rp, b.col, b.lv, b.lvp, b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big, b.huge, ctx->d_ctl, g1_lo, b.glo,
+            b.part);
     else
         k_row_fill<false><<<grid_for(n, kFillThreads, cap), kFillThreads, 0, s>>>(
-            n, b.rp, b.col, b.lv, b.lvp, b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big, b.huge, ctx->d_ctl, g1_lo);
+            n, b.rp, b.col, b.lv, b.lvp, b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big, b.huge, ctx->d_ctl, g1_lo, b.glo,
+            b.part);
     if (max_deg > kHugeRow) {
         if (b.lvp)
             k_row_fill_huge<true><<<(unsigned)ctx->num_sms, 1024, 0, s>>>(b.huge, ctx->d_ctl, b.rp, b.col, b.lv, b.lvp,
-                                                                         b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big, g1_lo);
+                                                                         b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big, g1_lo,
+                                                                         b.glo);
         else
             k_row_fill_huge<false><<<(unsigned)ctx->num_sms, 1024, 0, s>>>(b.huge, ctx->d_ctl, b.rp, b.col, b.lv, b.lvp,
                                                                           b.adj2, b.fcnt, b.gcnt, b.vmeta, b.big,
-                                                                          g1_lo);
+                                                                          g1_lo, b.glo);
+        ++launches;
+    }
+    if (g1_lo && max_deg > kWarpA) {
+        const int smem = (int)(4 * kHugeRow);
+        TC_CUDA(ctx, cudaFuncSetAttribute(k_g1_split, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        k_g1_split<<<(unsigned)ctx->num_sms, 1024, smem, s>>>(b.part, ctx->d_ctl, b.rp, b.gcnt, b.adj2, g1_lo, b.glo);
         ++launches;
     }
     if (max_deg > kWarpA) {
@@ -622,7 +717,8 @@ tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_de
     k_records<<<cap, 256, 0, s>>>(n, b.eoff, b.chunk_row, b.rp, b.adj2, b.lv, b.vmeta, b.erec, ctx->d_ctl);
     // fdeg and R are free after the levels: class of every vertex, 0/1 indicator
     k_class_flags<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.fcnt, b.gcnt, b.deg, b.fdeg, ctx->d_ctl, tu.warp_cap,
-                                                        tu.block_cap, tu.tiny_cap);
+                                                        tu.block_cap, tu.tiny_cap, g1_lo, block_hi_cap(tu, g1_lo),
+                                                        b.glo, b.lv);
     launches += 3;
     for (uint32_t c = 0; c < 4; ++c) {
         k_class_indicator<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.fdeg, c, b.R);

@@ -38,7 +38,7 @@ struct Tuning {
     uint32_t tiny_cap = 16;          // s(u) <= tiny_cap and deg(u) <= 4 tiny_cap: thread-per-row merges (0: off)
     uint32_t table_kind = 0;         // warp/block-class sets: 0 two-choice cuckoo tables, 1 bucketed tables
     uint32_t flat_cap = 128;         // warp class: probe ranges shorter than this are concatenated across lanes
-    uint32_t block_bits_log2 = 0;    // block class (cuckoo): ranks below 2^k in a shared bitmap (0: off)
+    uint32_t block_bits_log2 = 19;   // block class (cuckoo): ranks below 2^k in a shared bitmap (0: off)
     uint32_t batch_small_slots = 0;  // batches: graphs this small counted a block each in one launch (0: off)
 };
 
@@ -71,6 +71,7 @@ struct Ctl {
     unsigned int bar_count, bar_spare;      // arrivals at the persistent BFS's grid barriers (this launch)
     unsigned int n_big;              // rows whose A part the block sorter sorts
     unsigned int n_huge;             // rows of very high degree filled by a block each
+    unsigned int n_part;             // rows whose level-spanning part k_g1_split splits
     unsigned int pad[2];
     unsigned long long list_cursor;  // listing: next free chunk position
 };
@@ -120,6 +121,7 @@ struct tc_ctx {
     uint32_t launches = 0;    // kernels launched on this context so far (a call reports its own difference)
     uint32_t isect_flags = 0; // which intersection kernels the last count launched (1 warp, 2 block, 4 hub)
     uint32_t shard = 0, nshards = 1;  // intersection tasks of this count: share `shard` of `nshards`
+    uint32_t split_R = 0;             // this count's split rank (block-class bitmap; 0: none)
     uint64_t alloc_calls = 0;         // device allocations made by this context
     uint64_t fail_alloc_at = 0;       // fault injection: fail this allocation (1-based; 0 = never)
     std::string err;

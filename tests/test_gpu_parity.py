@@ -114,8 +114,9 @@ def test_every_intersection_class(tc, name, caps):
         tc.tc_destroy(c)
 
 
-@pytest.mark.parametrize("bits", [0, 10, 11, 12, 18])
-@pytest.mark.parametrize("name", ["rmat10", "rmat12_ef32", "union", "K40", "chung_lu4096", "er4096"])
+@pytest.mark.parametrize("bits", [0, 10, 11, 12, 14, 18, 20])
+@pytest.mark.parametrize("name", ["rmat10", "rmat12_ef32", "union", "K40", "chung_lu4096", "er4096", "rmat15",
+                                  "two_hubs"])
 def test_block_class_split_set(tc, name, bits):
     """Block-class sets split at rank 2^bits (a shared bitmap below, the cuckoo
     table above; the rows stage puts the low ranks of every level-spanning part
@@ -125,9 +126,10 @@ def test_block_class_split_set(tc, name, bits):
     c = tc.tc_create(0)
     try:
         tc.tc_set_tuning(c, warp_cap=1, block_cap=13107, task_work=256, tiny_cap=0, block_bits_log2=bits)
-        g = SMALL[name]
+        g = {"rmat15": lambda: gg.rmat(15, 16, seed=2), "two_hubs": two_hub_graph}.get(name, lambda: SMALL[name])()
         T, st, L, rp, col = gpu_count(tc, c, g)
-        assert st["class_probes"][2] == 0 and st["class_probes"][1] > st["class_probes"][0]
+        if name != "two_hubs":  # its hub rows stay in the hub class
+            assert st["class_probes"][2] == 0 and st["class_probes"][1] > st["class_probes"][0]
         assert_parity(T, st, L, rp, col, g)
     finally:
         tc.tc_destroy(c)
