@@ -1279,16 +1279,17 @@ __device__ __forceinline__ void probe_slice(const Set &set, const SliceSmem &S, 
 // probe_slice for a split set: a piece of a split range lies wholly in its
 // low part (bitmap lookups only) or wholly in its high part (cuckoo table
 // only); pieces of ranges whose split is unknown take both, lane by lane.
-template <int kM = 0>
-__device__ __forceinline__ void probe_slice_split(const SplitSet &set, const SliceSmem &S, uint32_t nv,
-                                                  const uint32_t *__restrict__ adj2, unsigned int *next, Acc &acc,
-                                                  const VertexOut &vo, ListCtx &lc) {
+// Low pieces go to `low` (the bitmap), high pieces to `high`, pieces of
+// ranges with no known split to `mix` (a set that answers for any id).
+template <int kM = 0, class LowSet, class HighSet, class MixSet>
+__device__ __forceinline__ void probe_slice_split(const LowSet &low, const HighSet &high, const MixSet &mix,
+                                                  const SliceSmem &S, uint32_t nv, const uint32_t *__restrict__ adj2,
+                                                  unsigned int *next, Acc &acc, const VertexOut &vo, ListCtx &lc) {
     const unsigned lane = lane_id();
     const uint32_t total = S.seg[nv];
     const uint32_t nwarps = blockDim.x >> 5;
     uint32_t batch = total / (4 * nwarps);
     batch = batch < 1 ? 1 : (batch > 32 ? 32 : batch);
-    const BitmapSet B{set.bm, set.R};
     for (;;) {
         uint32_t g0 = 0;
         if (lane == 0) g0 = atomicAdd(next, batch);
@@ -1335,9 +1336,12 @@ __device__ __forceinline__ void probe_slice_split(const SplitSet &set, const Sli
             const uint32_t kt = __shfl_sync(0xFFFFFFFFu, kind, t);
             if constexpr (kM == 2) lc.v = __shfl_sync(0xFFFFFFFFu, vid, t);
             uint32_t got;
-            if (kt == 1) got = probe_row<BitmapSet::kUnroll, false, kM, true>(B, adj2, bt, lo, hi, ht, acc, vo, &lc);
-            else if (kt == 2) got = probe_row<CuckooTable::kUnroll, false, kM, true>(set.C, adj2, bt, lo, hi, ht, acc, vo, &lc);
-            else got = probe_row<SplitSet::kUnroll, false, kM, true>(set, adj2, bt, lo, hi, ht, acc, vo, &lc);
+            if (kt == 1)
+                got = probe_row<LowSet::kUnroll, LowSet::kFineTail, kM, true>(low, adj2, bt, lo, hi, ht, acc, vo, &lc);
+            else if (kt == 2)
+                got = probe_row<HighSet::kUnroll, HighSet::kFineTail, kM, true>(high, adj2, bt, lo, hi, ht, acc, vo, &lc);
+            else
+                got = probe_row<MixSet::kUnroll, MixSet::kFineTail, kM, true>(mix, adj2, bt, lo, hi, ht, acc, vo, &lc);
             if constexpr (kM == 1) {
                 got = warp_sum(got);
                 const uint32_t vt = __shfl_sync(0xFFFFFFFFu, vid, t);
@@ -1483,8 +1487,10 @@ __global__ void __launch_bounds__(1024, 1) k_isect_block(const uint2 *__restrict
         }
         const unsigned long long before = acc.same + acc.cross;
         lc.u = u;
-        if constexpr (kSet == 2)
-            probe_slice_split<kM>(SplitSet{C, shared_addr(bmp), split_R}, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);
+        if constexpr (kSet == 2) {
+            const SplitSet SS{C, shared_addr(bmp), split_R};
+            probe_slice_split<kM>(BitmapSet{SS.bm, split_R}, C, SS, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);
+        }
         else if constexpr (kCuckoo) probe_slice<kM>(C, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);
         else probe_slice<kM>(T, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);
         finish_task<kM>(acc.same + acc.cross - before, groups, vo, ts, u);
@@ -1514,7 +1520,12 @@ __global__ void k_hub_set(const uint32_t *__restrict__ rows, uint32_t i0, uint32
 
 // Probe the tasks [first, last) of the hub rows with row index in
 // [i0, i0 + hub_group) against their bitmaps.
-template <int kM>
+// With kSplit (split_R > 0), the ranks of the set below split_R also sit in
+// an exact shared bitmap after the prefilter: the low pieces of split probe
+// ranges are answered there, without the prefilter or L2; high pieces and
+// pieces of unsplit ranges take the prefilter and the L2 bitmap (the
+// prefilter holds the whole set).
+template <int kM, bool kSplit = false>
 __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__ tasks, unsigned long long first,
                                                     unsigned long long last, const uint32_t *__restrict__ rows,
                                                     const uint32_t *__restrict__ ntask, uint32_t i0,
@@ -1523,7 +1534,8 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
                                                     const uint64_t *__restrict__ eoff, const uint4 *__restrict__ erec,
                                                     Ctl *ctl, const uint32_t *bits, uint64_t words, uint32_t max_v,
                                                     unsigned long long chunk, uint32_t filter_log2, GroupSpec groups,
-                                                    VertexOut vo) {
+                                                    VertexOut vo, uint32_t split_R = 0, const uint32_t *__restrict__ glo = nullptr,
+                                                    const uint2 *__restrict__ lv = nullptr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TaskSmem ts;
     const unsigned lane = lane_id();
@@ -1531,6 +1543,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
     uint32_t *filter = reinterpret_cast<uint32_t *>(smem_raw + slice_smem_bytes(max_v));
     const uint32_t filter_words = 1u << (filter_log2 - 5);
     const uint32_t fshift = 32u - filter_log2;
+    uint32_t *lowbm = filter + filter_words;  // kSplit: split_R bits
     if constexpr (kM == 1) {
         vo.priv = reinterpret_cast<unsigned long long *>(filter + filter_words);
         priv_begin(vo);
@@ -1554,15 +1567,23 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
         const uint32_t su = (uint32_t)(rp[u + 1] - hb);
         const uint32_t k_lo = (uint32_t)((uint64_t)task.y * fu / nt), k_hi = (uint32_t)((uint64_t)(task.y + 1) * fu / nt);
         const bool rebuild = task.x != cur_row;
-        if (rebuild)
+        if (rebuild) {
             for (uint32_t j = threadIdx.x; j < filter_words; j += blockDim.x) filter[j] = 0u;
-        load_slice<kM>(S, erec + eoff[u], k_lo, k_hi, adj2 + (hb - fu));
+            if constexpr (kSplit)
+                for (uint32_t j = threadIdx.x; j < (split_R >> 5); j += blockDim.x) lowbm[j] = 0u;
+        }
+        bool tail_lo = false;
+        if constexpr (kSplit) tail_lo = lv[u].x <= split_R;
+        load_slice<kM, kSplit>(S, erec + eoff[u], k_lo, k_hi, adj2 + (hb - fu), glo, tail_lo);
         __syncthreads();
-        scan_segments(S.len, S.seg, k_hi - k_lo);
+        scan_segments(S.len, S.seg, k_hi - k_lo, kSplit ? S.q : nullptr);
         if (rebuild) {
             for (uint32_t j = threadIdx.x; j < su; j += blockDim.x) {
-                const uint32_t f = filter_bit(adj2[hb + j], fshift);
+                const uint32_t w = adj2[hb + j];
+                const uint32_t f = filter_bit(w, fshift);
                 atomicOr(filter + (f >> 5), 1u << (f & 31));
+                if constexpr (kSplit)
+                    if (w < split_R) atomicOr(lowbm + (w >> 5), 1u << (w & 31u));
             }
             __syncthreads();
             cur_row = task.x;
@@ -1575,7 +1596,11 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
         const HubSet H{filter, bits + (uint64_t)(task.x - i0) * words, fshift};
         const unsigned long long before = acc.same + acc.cross;
         lc.u = u;
-        probe_slice<kM>(H, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);
+        if constexpr (kSplit)
+            probe_slice_split<kM>(BitmapSet{shared_addr(lowbm), split_R}, H, H, S, k_hi - k_lo, adj2, &ts.next, acc,
+                                  vo, lc);
+        else
+            probe_slice<kM>(H, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);
         finish_task<kM>(acc.same + acc.cross - before, groups, vo, ts, u);
     }
     flush(acc, ctl, 2, threadIdx.x == 0 ? build : 0, threadIdx.x == 0 ? done : 0);
@@ -1751,9 +1776,17 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         std::vector<unsigned long long> pref(nh + 1);
         TC_CUDA(ctx, cudaMemcpyAsync(pref.data(), b.tpref[2], 8ull * (nh + 1), cudaMemcpyDeviceToHost, s));
         TC_CUDA(ctx, cudaStreamSynchronize(s));
-        const size_t smem = hub_kernel_smem(tu) + priv + (mode == 2 ? 4ull * kStageSlots * (tu.hub_threads / 32) : 0);
+        // split (plain counts): the prefilter shrinks to make room for the low-rank bitmap
+        const uint32_t split_R = ctx->split_R;
+        uint32_t filter_log2 = tu.hub_filter_log2;
+        while (split_R && filter_log2 > 10 &&
+               slice_smem_bytes(tu.max_v) + (1ull << filter_log2) / 8 + split_R / 8 + 2048 > kSmemLimit)
+            --filter_log2;
+        const size_t smem = slice_smem_bytes(tu.max_v) + (1ull << filter_log2) / 8 + split_R / 8 + priv +
+                            (mode == 2 ? 4ull * kStageSlots * (tu.hub_threads / 32) : 0);
         if (smem > kSmemLimit) return set_error(ctx, TC_ERR_INVALID, "tuning leaves no shared memory for this mode");
-        auto hub = mode == 0 ? k_isect_hub<0> : mode == 1 ? k_isect_hub<1> : k_isect_hub<2>;
+        auto hub = split_R ? k_isect_hub<0, true>
+                           : mode == 0 ? k_isect_hub<0> : mode == 1 ? k_isect_hub<1> : k_isect_hub<2>;
         TC_CUDA(ctx, cudaFuncSetAttribute(hub, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int per_sm = 0;
         TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hub, tu.hub_threads, smem));
@@ -1774,8 +1807,8 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
             hub<<<(unsigned)grid, tu.hub_threads, smem, s>>>(b.tasks[2], first, last, b.rows[2], b.ntask[2], i0,
                                                                      b.rp, b.adj2, b.fcnt, b.eoff, b.erec, ctx->d_ctl,
                                                                      b.hub_bits,
-                                                                     b.hub_words, tu.max_v, chunk, tu.hub_filter_log2,
-                                                                     b.groups, vo);
+                                                                     b.hub_words, tu.max_v, chunk, filter_log2,
+                                                                     b.groups, vo, split_R, b.glo, b.lv);
             note_launch(ctx, 2);
         }
     }
