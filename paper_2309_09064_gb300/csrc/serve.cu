@@ -85,7 +85,8 @@ static void worker_loop(ServeState *S, tc_ctx *sub, int lane, int nworkers) {
                 ServeRequest &rq = S->reqs[t];
                 const size_t b = request_bytes(sub, rq.g);
                 const uint64_t e = rq.g->slots / 2;
-                if (!tickets.empty() && (used + b > budget || (lane == 0 && edges + e > S->round_edges))) break;
+                // a large-lane round is one graph; a small-lane round stops at round_edges
+                if (!tickets.empty() && (lane == 1 || used + b > budget || edges + e > S->round_edges)) break;
                 used += b;
                 edges += e;
                 q.pop_front();
@@ -128,6 +129,25 @@ static tc_status serve_start(tc_ctx *ctx) {
             return set_error(ctx, TC_ERR_CUDA, "serving sub-context creation failed");
         }
         sub->tune = ctx->tune;
+        if (lanes[i] == 1) {
+            // the large lane's kernels get the device's highest stream priority: its
+            // blocks are scheduled first whenever the small rounds' kernels leave room,
+            // so a large count is not spread thin between many small rounds
+            int least = 0, greatest = 0;
+            cudaStream_t hs = nullptr;
+            int prev = -1;
+            cudaGetDevice(&prev);
+            cudaSetDevice(ctx->device);
+            if (cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+                cudaStreamCreateWithPriority(&hs, cudaStreamNonBlocking, greatest) == cudaSuccess) {
+                cudaStreamDestroy(sub->own_stream);
+                sub->own_stream = hs;
+                sub->stream = hs;
+            } else {
+                cudaGetLastError();
+            }
+            if (prev >= 0) cudaSetDevice(prev);
+        }
         S->subs.push_back(sub);
         S->lane.push_back(lanes[i]);
     }
