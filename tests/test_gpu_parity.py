@@ -378,19 +378,21 @@ def test_shards_sum_to_the_count(tc, ctx, nshards):
         assert sum(parts) == T
 
 
+@pytest.mark.parametrize("bits", [0, 19])
 @pytest.mark.parametrize("nshards", [2, 3, 5, 8])
-def test_shards_agree_on_rows_of_degree_above_8192(tc, nshards):
+def test_shards_agree_on_rows_of_degree_above_8192(tc, nshards, bits):
     """Every shard recomputes the rows, and its tasks are slices of F(u): the
     block-filled rows (degree above 8192) must come out in the same order on
     every run, or shards would cut a row's slices from different orders."""
     c = tc.tc_create(0)
     try:
-        tc.tc_set_tuning(c, warp_cap=64, block_cap=1024, task_work=4096, hub_task_work=4096, max_v=64)
+        tc.tc_set_tuning(c, warp_cap=64, block_cap=1024, task_work=4096, hub_task_work=4096, max_v=64,
+                         block_bits_log2=bits)
         n, s, d = gg.rmat(17, 16, seed=3)
         g = tc.tc_build_csr(c, n, s, d)
         assert tc.tc_graph_info(g)[1] > 0
         T, st = tc.tc_count(c, g)
-        assert st["class_rows"][2] > nshards  # hub rows, split into many tasks
+        assert st["class_rows"][2 if bits == 0 else 1] > nshards  # hub (or split block) rows, many tasks
         for _ in range(3):
             parts = [tc.tc_count_shard(c, g, k, nshards)[0] for k in range(nshards)]
             assert sum(parts) == T
