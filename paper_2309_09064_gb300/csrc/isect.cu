@@ -1244,6 +1244,10 @@ __device__ __forceinline__ void probe_slice(const Set &set, const SliceSmem &S, 
         g0 = __shfl_sync(0xFFFFFFFFu, g0, 0);
         if (g0 >= total) break;
         const uint32_t cnt = min(batch, total - g0);
+        {   // guided: later grabs take fewer pieces, so the warps finish the task together
+            uint32_t nb = (total - g0 - cnt) / (4 * nwarps);
+            batch = nb < 1 ? 1 : (nb < batch ? nb : batch);
+        }
         unsigned long long b = 0;
         uint32_t j_lo = 0, j_hi = 0, h = 0, vid = 0;
         if (lane < cnt) {
@@ -1296,6 +1300,10 @@ __device__ __forceinline__ void probe_slice_split(const LowSet &low, const HighS
         g0 = __shfl_sync(0xFFFFFFFFu, g0, 0);
         if (g0 >= total) break;
         const uint32_t cnt = min(batch, total - g0);
+        {   // guided: later grabs take fewer pieces, so the warps finish the task together
+            uint32_t nb = (total - g0 - cnt) / (4 * nwarps);
+            batch = nb < 1 ? 1 : (nb < batch ? nb : batch);
+        }
         unsigned long long b = 0;
         uint32_t j_lo = 0, j_hi = 0, h = 0, vid = 0, kind = 0;  // kind: 0 both, 1 low part, 2 high part
         if (lane < cnt) {
