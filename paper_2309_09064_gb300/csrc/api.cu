@@ -27,6 +27,25 @@ cudaError_t device_alloc(tc_ctx *ctx, void **p, size_t bytes) {
     return cudaMalloc(p, bytes);
 }
 
+cudaError_t graph_alloc(tc_ctx *ctx, void **p, size_t bytes, bool *pooled) {
+    *pooled = false;
+    if (!ctx->graph_pool) return device_alloc(ctx, p, bytes);
+    ++ctx->alloc_calls;
+    if (ctx->fail_alloc_at && ctx->alloc_calls == ctx->fail_alloc_at) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;  // injected: nothing was allocated
+    }
+    const cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->graph_pool, ctx->stream);
+    *pooled = e == cudaSuccess;
+    return e;
+}
+
+void graph_free(tc_ctx *ctx, void *p, bool pooled) {
+    if (!p) return;
+    if (pooled) cudaFreeAsync(p, ctx->stream);
+    else cudaFree(p);
+}
+
 // Grow-only device arena owned by the context.  Growing waits for the stream
 // (earlier work may still read the old buffer), then replaces the buffer.
 static tc_status reserve_in(tc_ctx *ctx, Arena &a, size_t bytes) {
@@ -119,6 +138,21 @@ tc_status tc_create(tc_ctx **out, int device, const tc_options *opt) {
     ok = ok && cudaMalloc(&ctx->d_ctl, sizeof(Ctl)) == cudaSuccess;
     ok = ok && cudaMallocHost(&ctx->h_ctl, sizeof(Ctl)) == cudaSuccess;
     for (int i = 0; ok && i < 10; ++i) ok = cudaEventCreate(&ctx->ev[i]) == cudaSuccess;
+    if (ok) {
+        // graph arrays come from a pool that keeps freed memory, so a user who makes
+        // and frees a graph per request does not pay cudaMalloc / cudaFree each time
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        if (cudaMemPoolCreate(&ctx->graph_pool, &props) == cudaSuccess) {
+            uint64_t keep = ~0ull;
+            cudaMemPoolSetAttribute(ctx->graph_pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        } else {
+            cudaGetLastError();
+            ctx->graph_pool = nullptr;  // fall back to cudaMalloc
+        }
+    }
     if (!ok) {
         cudaGetLastError();
         tc_destroy(ctx);
@@ -139,6 +173,7 @@ tc_status tc_destroy(tc_ctx *ctx) {
     if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
     for (int i = 0; i < 10; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    if (ctx->graph_pool) cudaMemPoolDestroy(ctx->graph_pool);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
     return TC_OK;
@@ -246,8 +281,12 @@ tc_status tc_graph_from_csr(tc_ctx *ctx, uint32_t n, const uint64_t *row_ptr, co
         g->owned = false;
     } else {
         g->owned = true;
-        if (device_alloc(ctx, (void **)&g->rp, sizeof(uint64_t) * ((size_t)n + 1)) != cudaSuccess ||
-            device_alloc(ctx, (void **)&g->col, sizeof(uint32_t) * (size_t)(slots + 1)) != cudaSuccess) {
+        bool p1 = false, p2 = false;
+        const cudaError_t e1 = graph_alloc(ctx, (void **)&g->rp, sizeof(uint64_t) * ((size_t)n + 1), &p1);
+        const cudaError_t e2 =
+            e1 == cudaSuccess ? graph_alloc(ctx, (void **)&g->col, sizeof(uint32_t) * (size_t)(slots + 1), &p2) : e1;
+        g->pooled = p1;  // both come from the same source
+        if (e1 != cudaSuccess || e2 != cudaSuccess) {
             cudaGetLastError();
             tc_graph_free(g);
             return set_error(ctx, TC_ERR_OOM, "graph allocation failed");
@@ -286,7 +325,8 @@ tc_status tc_build_csr(tc_ctx *ctx, uint32_t n, uint64_t n_tuples, const uint32_
     uint64_t *rp = nullptr;
     uint32_t *col = nullptr;
     uint64_t slots = 0;
-    tc_status st = build_csr_device(ctx, n, n_tuples, ds, dd, &rp, &col, &slots);
+    bool pooled = false;
+    tc_status st = build_csr_device(ctx, n, n_tuples, ds, dd, &rp, &col, &slots, &pooled);
     if (tmp) {
         cudaStreamSynchronize(ctx->stream);
         cudaFree(tmp);
@@ -298,6 +338,7 @@ tc_status tc_build_csr(tc_ctx *ctx, uint32_t n, uint64_t n_tuples, const uint32_
     g->slots = slots;
     g->rp = rp;
     g->col = col;
+    g->pooled = pooled;
     g->owned = true;
     return finish_graph(ctx, g, 0, out);
 }
@@ -333,9 +374,9 @@ tc_status tc_graph_free(tc_graph *g) {
     if (!g) return TC_ERR_INVALID;
     if (g->owned) {
         DeviceGuard guard(g->ctx->device);
-        if (g->ctx->stream) cudaStreamSynchronize(g->ctx->stream);
-        if (g->rp) cudaFree(g->rp);
-        if (g->col) cudaFree(g->col);
+        if (g->ctx->stream) cudaStreamSynchronize(g->ctx->stream);  // its last use on the context is done
+        graph_free(g->ctx, g->rp, g->pooled);
+        graph_free(g->ctx, g->col, g->pooled);
     }
     delete g;
     return TC_OK;

@@ -238,7 +238,7 @@ uint32_t radix_sort_u64(unsigned long long **cur, unsigned long long **alt, uint
 }
 
 tc_status build_csr_device(tc_ctx *ctx, uint32_t n, uint64_t t, const uint32_t *d_src, const uint32_t *d_dst,
-                           uint64_t **rp_out, uint32_t **col_out, uint64_t *slots_out) {
+                           uint64_t **rp_out, uint32_t **col_out, uint64_t *slots_out, bool *pooled_out) {
     cudaStream_t s = ctx->stream;
     const unsigned cap = (unsigned)ctx->num_sms * 16u;
     const uint64_t K = 2 * t;  // upper bound on keys
@@ -287,15 +287,17 @@ tc_status build_csr_device(tc_ctx *ctx, uint32_t n, uint64_t t, const uint32_t *
         TC_CUDA(ctx, cudaMemcpyAsync(&U, pos + nk, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
         TC_CUDA(ctx, cudaStreamSynchronize(s));
     }
-    if (device_alloc(ctx, (void **)&rp, sizeof(uint64_t) * ((size_t)n + 1)) != cudaSuccess) {
+    bool pooled = false, pooled2 = false;
+    if (graph_alloc(ctx, (void **)&rp, sizeof(uint64_t) * ((size_t)n + 1), &pooled) != cudaSuccess) {
         cudaGetLastError();
         return set_error(ctx, TC_ERR_OOM, "tc_build_csr: row_ptr allocation failed");
     }
-    if (device_alloc(ctx, (void **)&col, sizeof(uint32_t) * (size_t)(U + 1)) != cudaSuccess) {
+    if (graph_alloc(ctx, (void **)&col, sizeof(uint32_t) * (size_t)(U + 1), &pooled2) != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(rp);
+        graph_free(ctx, rp, pooled);
         return set_error(ctx, TC_ERR_OOM, "tc_build_csr: col allocation failed");
     }
+    *pooled_out = pooled;
     if (U) {
         k_compact<<<grid_for(nk, 256, cap), 256, 0, s>>>(cur, nk, flag, reinterpret_cast<const unsigned long long *>(pos),
                                                         col, src32);
@@ -306,8 +308,8 @@ tc_status build_csr_device(tc_ctx *ctx, uint32_t n, uint64_t t, const uint32_t *
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
-        cudaFree(rp);
-        cudaFree(col);
+        graph_free(ctx, rp, pooled);
+        graph_free(ctx, col, pooled2);
         return cuda_error(ctx, e, "tc_build_csr kernels");
     }
     *rp_out = rp;

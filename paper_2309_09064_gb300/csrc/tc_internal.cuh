@@ -102,6 +102,7 @@ struct tc_graph {
     uint32_t *col;     // device
     uint32_t max_deg;
     bool owned;
+    bool pooled = false;  // rp/col come from the context's graph pool (stream-ordered free)
 };
 
 struct ServeState;  // serve.cu
@@ -115,6 +116,7 @@ struct tc_ctx {
     tc::Tuning tune{};
     tc::Arena arena;
     tc::Arena batch_arena;   // union CSR of tc_count_batch
+    cudaMemPool_t graph_pool = nullptr;  // graph arrays: freed memory stays in the pool for the next graph
     tc::Ctl *d_ctl = nullptr;
     tc::Ctl *h_ctl = nullptr;   // pinned
     cudaEvent_t ev[10] = {};
@@ -136,6 +138,10 @@ tc_status cuda_error(tc_ctx *ctx, cudaError_t e, const char *what);
 tc_status arena_reserve(tc_ctx *ctx, size_t bytes);
 // cudaMalloc through the context (counts calls; honours the injected failure).
 cudaError_t device_alloc(tc_ctx *ctx, void **p, size_t bytes);
+// Graph arrays: from the context's memory pool, stream-ordered on its stream
+// (plain cudaMalloc when the pool could not be made); *pooled says which.
+cudaError_t graph_alloc(tc_ctx *ctx, void **p, size_t bytes, bool *pooled);
+void graph_free(tc_ctx *ctx, void *p, bool pooled);
 
 // Launch bookkeeping: every kernel launch site calls this once per launch.
 inline void note_launch(tc_ctx *ctx, uint32_t k = 1) { ctx->launches += k; }
@@ -193,7 +199,7 @@ size_t pipeline_bytes(const tc_ctx *ctx, uint32_t n, uint64_t slots, uint32_t ma
 // CSR construction / validation (csr.cu)
 tc_status build_csr_device(tc_ctx *ctx, uint32_t n, uint64_t t, const uint32_t *d_src,
                            const uint32_t *d_dst, uint64_t **rp_out, uint32_t **col_out,
-                           uint64_t *slots_out);
+                           uint64_t *slots_out, bool *pooled_out);
 tc_status validate_csr_device(tc_ctx *ctx, uint32_t n, const uint64_t *rp, const uint32_t *col,
                               uint64_t slots, int *ok);
 tc_status max_degree_device(tc_ctx *ctx, uint32_t n, const uint64_t *rp, uint32_t *max_deg);
