@@ -90,9 +90,14 @@ __global__ void __launch_bounds__(kFillThreads) k_row_fill(uint32_t n, const uin
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     uint32_t *buf = sbuf[warp];
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t n_round = ((uint64_t)n + 31) & ~uint64_t(31);
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_round; x += stride) {
+    // warps take chunks of 32 vertices from a counter: rows of very different lengths even out
+    const uint64_t chunks = ((uint64_t)n + 31) / 32;
+    for (;;) {
+        unsigned int c = 0;
+        if (lane == 0) c = atomicAdd(&ctl->fill_next, 1u);
+        c = __shfl_sync(0xFFFFFFFFu, c, 0);
+        if (c >= chunks) break;
+        const uint64_t x = (uint64_t)c * 32 + lane;
         const bool valid = x < n;
         const uint64_t b = valid ? rp[x] : 0;
         const uint32_t dx = valid ? (uint32_t)(rp[x + 1] - b) : 0;
@@ -261,10 +266,16 @@ __global__ void __launch_bounds__(1024) k_row_fill_huge(const uint32_t *__restri
                                                         uint32_t g1_lo, uint32_t *__restrict__ glo) {
     __shared__ unsigned int cnt[4], base[4];
     __shared__ unsigned int wcnt[32][4];  // this chunk's F, G1 (high), A, G1 (low) per warp
+    __shared__ unsigned int s_i;
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const uint32_t nh = ctl->n_huge;
-    for (uint32_t i = blockIdx.x; i < nh; i += gridDim.x) {
+    for (;;) {  // blocks take rows from a counter (their degrees differ by orders of magnitude)
+        if (threadIdx.x == 0) s_i = atomicAdd(&ctl->huge_next, 1u);
+        __syncthreads();
+        const uint32_t i = s_i;
+        __syncthreads();
+        if (i >= nh) break;
         const uint32_t x = huge[i];
         const uint64_t b = rp[x];
         const uint32_t d = (uint32_t)(rp[x + 1] - b);

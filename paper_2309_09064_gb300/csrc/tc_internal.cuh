@@ -72,6 +72,8 @@ struct Ctl {
     unsigned int n_big;              // rows whose A part the block sorter sorts
     unsigned int n_huge;             // rows of very high degree filled by a block each
     unsigned int n_part;             // rows whose level-spanning part k_g1_split splits
+    unsigned int fill_next;          // k_row_fill: next chunk of 32 vertices a warp takes
+    unsigned int huge_next;          // k_row_fill_huge: next listed row a block takes
     unsigned int pad[2];
     unsigned long long list_cursor;  // listing: next free chunk position
 };
