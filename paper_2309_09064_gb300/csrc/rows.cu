@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(1024) k_row_fill_huge(const uint32_t *__restri
 // kHugeRow): one block per listed row stages the part in shared memory and
 // writes it back with its ranks below g1_lo first, each side in its former
 // order (positions from the warps' ballots and a prefix over the warps).
-__global__ void __launch_bounds__(1024) k_g1_split(const uint32_t *__restrict__ part, const Ctl *ctl,
+__global__ void __launch_bounds__(1024) k_g1_split(const uint32_t *__restrict__ part, Ctl *ctl,
                                                    const uint64_t *__restrict__ rp, const uint32_t *__restrict__ gcnt,
                                                    uint32_t *__restrict__ adj2, uint32_t g1_lo,
                                                    uint32_t *__restrict__ glo) {
@@ -373,8 +373,14 @@ __global__ void __launch_bounds__(1024) k_g1_split(const uint32_t *__restrict__ 
     __shared__ unsigned int wcnt[32][2], base[2], nlo;
     const unsigned lane = lane_id(), warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
+    __shared__ unsigned int s_i;
     const uint32_t np = ctl->n_part;
-    for (uint32_t i = blockIdx.x; i < np; i += gridDim.x) {
+    for (;;) {  // blocks take rows from a counter
+        if (threadIdx.x == 0) s_i = atomicAdd(&ctl->split_next, 1u);
+        __syncthreads();
+        const uint32_t i = s_i;
+        __syncthreads();
+        if (i >= np) break;
         const uint32_t x = part[i];
         const uint32_t g = gcnt[x];
         if (threadIdx.x == 0) {
@@ -434,8 +440,14 @@ __global__ void __launch_bounds__(1024) k_sort_big(const uint32_t *__restrict__ 
                                                    const uint64_t *__restrict__ rp, const uint32_t *__restrict__ fcnt,
                                                    const uint32_t *__restrict__ gcnt, uint32_t *__restrict__ adj2) {
     extern __shared__ uint32_t sb[];  // kSortCap words
+    __shared__ unsigned int s_i;
     const uint32_t nb = ctl->n_big;
-    for (uint32_t i = blockIdx.x; i < nb; i += gridDim.x) {
+    for (;;) {  // blocks take rows from a counter (the parts differ in length by 32x)
+        if (threadIdx.x == 0) s_i = atomicAdd(&ctl->sort_next, 1u);
+        __syncthreads();
+        const uint32_t i = s_i;
+        __syncthreads();
+        if (i >= nb) break;
         const uint32_t x = big[i];
         const uint64_t b = rp[x] + fcnt[x];
         const uint32_t a = (uint32_t)(rp[x + 1] - b) - gcnt[x];

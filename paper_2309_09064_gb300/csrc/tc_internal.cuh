@@ -74,6 +74,8 @@ struct Ctl {
     unsigned int n_part;             // rows whose level-spanning part k_g1_split splits
     unsigned int fill_next;          // k_row_fill: next chunk of 32 vertices a warp takes
     unsigned int huge_next;          // k_row_fill_huge: next listed row a block takes
+    unsigned int sort_next;          // k_sort_big: next listed row a block takes
+    unsigned int split_next;         // k_g1_split: next listed row a block takes
     unsigned int pad[2];
     unsigned long long list_cursor;  // listing: next free chunk position
 };
