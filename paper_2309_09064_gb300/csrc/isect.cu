@@ -1280,12 +1280,24 @@ __device__ __forceinline__ void probe_slice(const Set &set, const SliceSmem &S, 
     }
 }
 
+// Ask L2 for the lines of positions [lo, hi) of the range at adj2[b]: one
+// 128-byte line per lane (at most 32 lines, i.e. a whole 512-position piece
+// with room to spare).  No registers wait on it; the walk's loads then find
+// the lines in L2 instead of DRAM.
+__device__ __forceinline__ void prefetch_piece(const uint32_t *adj2, unsigned long long b, uint32_t lo, uint32_t hi) {
+    const unsigned lane = lane_id();
+    const uint32_t *p0 = adj2 + b + lo;
+    const uint32_t *line = reinterpret_cast<const uint32_t *>(reinterpret_cast<uintptr_t>(p0) & ~uintptr_t(127)) +
+                           32u * lane;
+    if (hi > lo && line < adj2 + b + hi) asm volatile("prefetch.global.L2 [%0];" ::"l"(line));
+}
+
 // probe_slice for a split set: a piece of a split range lies wholly in its
 // low part (bitmap lookups only) or wholly in its high part (cuckoo table
 // only); pieces of ranges whose split is unknown take both, lane by lane.
 // Low pieces go to `low` (the bitmap), high pieces to `high`, pieces of
 // ranges with no known split to `mix` (a set that answers for any id).
-template <int kM = 0, class LowSet, class HighSet, class MixSet>
+template <int kM = 0, bool kPrefetch = false, class LowSet, class HighSet, class MixSet>
 __device__ __forceinline__ void probe_slice_split(const LowSet &low, const HighSet &high, const MixSet &mix,
                                                   const SliceSmem &S, uint32_t nv, const uint32_t *__restrict__ adj2,
                                                   unsigned int *next, Acc &acc, const VertexOut &vo, ListCtx &lc) {
@@ -1342,6 +1354,12 @@ __device__ __forceinline__ void probe_slice_split(const LowSet &low, const HighS
             const uint32_t hi = __shfl_sync(0xFFFFFFFFu, j_hi, t);
             const uint32_t ht = __shfl_sync(0xFFFFFFFFu, h, t);
             const uint32_t kt = __shfl_sync(0xFFFFFFFFu, kind, t);
+            if constexpr (kPrefetch) {  // the next piece of the batch to L2 while this one is walked
+                const uint32_t tn = t + 1 < cnt ? t + 1 : t;
+                const unsigned long long bn = __shfl_sync(0xFFFFFFFFu, b, tn);
+                const uint32_t ln = __shfl_sync(0xFFFFFFFFu, j_lo, tn), hn = __shfl_sync(0xFFFFFFFFu, j_hi, tn);
+                if (t + 1 < cnt) prefetch_piece(adj2, bn, ln, hn);
+            }
             if constexpr (kM == 2) lc.v = __shfl_sync(0xFFFFFFFFu, vid, t);
             uint32_t got;
             if (kt == 1)
@@ -1605,8 +1623,9 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
         const unsigned long long before = acc.same + acc.cross;
         lc.u = u;
         if constexpr (kSplit)
-            probe_slice_split<kM>(BitmapSet{shared_addr(lowbm), split_R}, H, H, S, k_hi - k_lo, adj2, &ts.next, acc,
-                                  vo, lc);
+            // the hub's probe ranges mostly come from DRAM: their next piece is prefetched into L2
+            probe_slice_split<kM, true>(BitmapSet{shared_addr(lowbm), split_R}, H, H, S, k_hi - k_lo, adj2, &ts.next,
+                                        acc, vo, lc);
         else
             probe_slice<kM>(H, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);
         finish_task<kM>(acc.same + acc.cross - before, groups, vo, ts, u);
