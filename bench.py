@@ -286,6 +286,10 @@ def run_batched_forms(args):
         specs = gg.batch_specs(args.batch_graphs, seed=5)
         graphs, m_total = _build_graphs(tc, ctx, specs)
         torch.cuda.synchronize()
+        tuned = None
+        if args.autotune:  # class caps, table kind, task sizes and the one-launch threshold, timed on this batch
+            from paper_2309_09064_gb300 import autotune
+            tuned, _ = autotune.autotune(ctx, graphs, reps=2)
         for _ in range(max(args.warmup, 1)):
             batched = tc.tc_count_batch(ctx, graphs)
         t0 = time.perf_counter()
@@ -301,7 +305,8 @@ def run_batched_forms(args):
                     "ms_per_step": t_batch * 1e3,
                     "config": {"workload": "batch", "graphs": len(graphs), "m_total": int(m_total),
                                "mix": "n log-uniform in [64, 65536]; R-MAT (ef U[8,32]) or G(n,m) (mean degree "
-                                      "U[4,64]) by coin; seed 5"},
+                                      "U[4,64]) by coin; seed 5",
+                               "tuning": tuned or tc.tc_get_tuning(ctx), "autotuned": bool(tuned)},
                     "looped": {"value": m_total / t_loop, "ms": t_loop * 1e3},
                     "speedup_vs_loop": t_loop / t_batch, "triangles_total": int(sum(int(x) for x in batched))})
     else:

@@ -38,6 +38,10 @@ CANDIDATES = [
     {"block_cap": 13107},
     {"flat_cap": 0},
     {"flat_cap": 256},
+    {"block_bits_log2": 0},
+    {"block_bits_log2": 18},
+    {"block_bits_log2": 20},
+    {"hub_task_work": 2097152},
     {"batch_small_slots": 16384},
     {"batch_small_slots": 65536},
     {"batch_small_slots": 262144},
