@@ -212,6 +212,10 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
         if (st != TC_OK) return st;
         st = emit_tasks(ctx, b);
         if (st != TC_OK) return st;
+        if (ctx->nshards > 1) {
+            st = records_for_shard(ctx, b);
+            if (st != TC_OK) return st;
+        }
         TC_CUDA(ctx, cudaEventRecord(ctx->ev[2], s));
         b.list_phase = list ? 1 : 0;
         st = intersect(ctx, b, n);

@@ -128,6 +128,8 @@ tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_de
 tc_status plan_scans(tc_ctx *ctx, const PipeBufs &b);
 // task emission (after the host knows the task totals)
 tc_status emit_tasks(tc_ctx *ctx, PipeBufs &b);
+// a count split into shards: the probe records of this shard's tasks only
+tc_status records_for_shard(tc_ctx *ctx, const PipeBufs &b);
 tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n);
 
 }  // namespace tc

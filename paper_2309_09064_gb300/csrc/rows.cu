@@ -636,10 +636,15 @@ __global__ void k_records(uint32_t n, const uint64_t *__restrict__ eoff, const u
 // record lengths, ntask = ceil(work(u) / max(task_work, min_mult * s(u))), at
 // least ceil(|F(u)| / max_v) (shared-memory metadata of one task), at most
 // |F(u)|.
+// With est (a count split into shards), the work of an edge u -> v is taken
+// as |A(v)| + |G1(v)| (the probe range at most), read from v's descriptor:
+// the plan then needs no probe record, and every shard builds the records of
+// its own tasks only.
 __global__ void k_plan(const uint32_t *__restrict__ rows, const unsigned int *__restrict__ n_rows,
                        const uint64_t *__restrict__ rp, const uint32_t *__restrict__ fcnt,
                        const uint64_t *__restrict__ eoff, const uint4 *__restrict__ erec,
-                       uint32_t *__restrict__ ntask, uint32_t task_work, uint32_t min_mult, uint32_t max_v) {
+                       uint32_t *__restrict__ ntask, uint32_t task_work, uint32_t min_mult, uint32_t max_v,
+                       bool est, const uint32_t *__restrict__ adj2, const uint4 *__restrict__ vmeta) {
     const unsigned lane = lane_id();
     const uint32_t nr = *n_rows;
     const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
@@ -649,13 +654,21 @@ __global__ void k_plan(const uint32_t *__restrict__ rows, const unsigned int *__
         const uint4 *rec = erec + eoff[u];
         unsigned long long w0 = 0, w1 = 0, w2 = 0, w3 = 0;
         uint32_t k = lane;
-        for (; k + 96 < fu; k += 128) {  // four independent loads in flight
-            w0 += rec[k].z;
-            w1 += rec[k + 32].z;
-            w2 += rec[k + 64].z;
-            w3 += rec[k + 96].z;
+        if (est) {
+            const uint32_t *f = adj2 + rp[u];  // F(u): the probed vertices
+            for (; k < fu; k += 32) {
+                const uint4 m = vmeta[f[k]];
+                w0 += (unsigned long long)m.z + m.w;
+            }
+        } else {
+            for (; k + 96 < fu; k += 128) {  // four independent loads in flight
+                w0 += rec[k].z;
+                w1 += rec[k + 32].z;
+                w2 += rec[k + 64].z;
+                w3 += rec[k + 96].z;
+            }
+            for (; k < fu; k += 32) w0 += rec[k].z;
         }
-        for (; k < fu; k += 32) w0 += rec[k].z;
         const unsigned long long work = warp_sum(w0 + w1 + w2 + w3);
         if (lane == 0) {
             const unsigned long long su = (rp[u + 1] - rp[u]) - fu;
@@ -667,6 +680,47 @@ __global__ void k_plan(const uint32_t *__restrict__ rows, const unsigned int *__
             if (nt < 1) nt = 1;
             if (nt > fu) nt = fu;
             ntask[i] = (uint32_t)nt;
+        }
+    }
+}
+
+__global__ void k_e0(uint32_t n, const uint64_t *__restrict__ eoff, Ctl *ctl) { ctl->e0 = eoff[n]; }
+
+// The probe records of the edges of tasks [first, last) of one class only (a
+// shard's share): one warp per task, one edge per lane, the same record as
+// k_records (p = the elements of the descending A(v) ranked below u, by a
+// binary search; all of A(v) when it was left unsorted).
+__global__ void k_records_tasks(const uint2 *__restrict__ tasks, unsigned long long first, unsigned long long last,
+                                const uint32_t *__restrict__ rows, const uint32_t *__restrict__ ntask,
+                                const uint64_t *__restrict__ rp, const uint32_t *__restrict__ fcnt,
+                                const uint64_t *__restrict__ eoff, const uint32_t *__restrict__ adj2,
+                                const uint2 *__restrict__ lv, const uint4 *__restrict__ vmeta,
+                                uint4 *__restrict__ erec) {
+    const unsigned lane = lane_id();
+    const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    for (unsigned long long t = first + (((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < last;
+         t += warps) {
+        const uint2 task = tasks[t];
+        const uint32_t u = rows[task.x], nt = ntask[task.x], fu = fcnt[u];
+        const uint32_t k_lo = (uint32_t)((uint64_t)task.y * fu / nt), k_hi = (uint32_t)((uint64_t)(task.y + 1) * fu / nt);
+        const uint32_t ru = lv[u].x;
+        const uint64_t fb = rp[u], e_base = eoff[u];
+        for (uint32_t k = k_lo + lane; k < k_hi; k += 32) {
+            const uint32_t v = adj2[fb + k];
+            const uint4 m = vmeta[v];
+            const uint64_t as = ((uint64_t)m.y << 32) | m.x;
+            const uint32_t av = m.z;
+            uint32_t p = av;  // an unsorted A part is probed whole
+            if (av <= kSortCap) {
+                uint32_t lo = 0, hi = av;  // first position holding a rank below u's
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (adj2[as + mid] < ru) hi = mid; else lo = mid + 1;
+                }
+                p = av - lo;
+            }
+            const uint64_t start = as + av - p;
+            erec[e_base + k] = make_uint4((uint32_t)start, (uint32_t)(start >> 32), m.w + p, p);
         }
     }
 }
@@ -736,13 +790,19 @@ tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_de
         ++launches;
     }
     launches += scan_u32_to_u64(b.fcnt, b.eoff, n, b.scan_tmp, s);
-    k_chunk_rows<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.eoff, b.chunk_row);
-    k_records<<<cap, 256, 0, s>>>(n, b.eoff, b.chunk_row, b.rp, b.adj2, b.lv, b.vmeta, b.erec, ctx->d_ctl);
+    // a count split into shards builds each shard's records after planning (records_for_shard)
+    const bool sharded = ctx->nshards > 1;
+    if (sharded) {
+        k_e0<<<1, 1, 0, s>>>(n, b.eoff, ctx->d_ctl);
+    } else {
+        k_chunk_rows<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.eoff, b.chunk_row);
+        k_records<<<cap, 256, 0, s>>>(n, b.eoff, b.chunk_row, b.rp, b.adj2, b.lv, b.vmeta, b.erec, ctx->d_ctl);
+    }
     // fdeg and R are free after the levels: class of every vertex, 0/1 indicator
     k_class_flags<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.fcnt, b.gcnt, b.deg, b.fdeg, ctx->d_ctl, tu.warp_cap,
                                                         tu.block_cap, tu.tiny_cap, g1_lo, block_hi_cap(tu, g1_lo),
                                                         b.glo, b.lv);
-    launches += 3;
+    launches += sharded ? 2 : 3;
     for (uint32_t c = 0; c < 4; ++c) {
         k_class_indicator<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.fdeg, c, b.R);
         launches += 2 + scan_u32_to_u64(b.R, b.fpref, n, b.scan_tmp, s);
@@ -755,7 +815,7 @@ tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_de
     for (int c = 0; c < 3; ++c) {
         k_plan<<<grid_for((uint64_t)n * 32, 256, cap), 256, 0, s>>>(b.rows[c], &ctx->d_ctl->n_rows[c], b.rp, b.fcnt,
                                                                     b.eoff, b.erec, b.ntask[c], work[c], mult[c],
-                                                                    maxv[c]);
+                                                                    maxv[c], sharded, b.adj2, b.vmeta);
         ++launches;
     }
     note_launch(ctx, launches);
@@ -773,6 +833,26 @@ tc_status plan_scans(tc_ctx *ctx, const PipeBufs &b) {
                                   reinterpret_cast<const unsigned long long *>(b.tpref[1]),
                                   reinterpret_cast<const unsigned long long *>(b.tpref[2]));
     note_launch(ctx, launches);
+    TC_CUDA(ctx, cudaGetLastError());
+    return TC_OK;
+}
+
+// A count split into shards: the probe records of this shard's tasks
+// (share ctx->shard of ctx->nshards of every class's task list, as the
+// intersections take them), after the tasks are emitted.
+tc_status records_for_shard(tc_ctx *ctx, const PipeBufs &b) {
+    cudaStream_t s = ctx->stream;
+    const unsigned cap = (unsigned)ctx->num_sms * 16u;
+    for (int c = 0; c < 3; ++c) {
+        const unsigned long long total = ctx->h_ctl->n_tasks[c];
+        const unsigned long long lo = total * ctx->shard / ctx->nshards;
+        const unsigned long long hi = total * (ctx->shard + 1) / ctx->nshards;
+        if (hi <= lo) continue;
+        k_records_tasks<<<grid_for((hi - lo) * 32, 256, cap), 256, 0, s>>>(b.tasks[c], lo, hi, b.rows[c], b.ntask[c],
+                                                                           b.rp, b.fcnt, b.eoff, b.adj2, b.lv,
+                                                                           b.vmeta, b.erec);
+        note_launch(ctx);
+    }
     TC_CUDA(ctx, cudaGetLastError());
     return TC_OK;
 }
