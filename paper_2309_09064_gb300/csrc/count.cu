@@ -121,8 +121,9 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     b.chunk_row = a.take<uint32_t>(g.slots / 2 / 256 + 2);
     bool ok = b.deg && b.L && b.q0 && b.q1 && b.fdeg && b.R && b.parent && b.fcnt && b.gcnt && b.rank && b.big &&
               b.huge && b.glo && b.part && lvp && b.vmeta && b.chunk_row;
-    // the split set serves the plain count; the per-vertex counts, the listing
-    // and Algorithm 3 keep their shared memory for their own use
+    // the split set serves the plain count; the per-vertex counts and the
+    // listing are faster without it (their time goes to counters and output
+    // writes, and the split's extra pieces cost more than its lookups save)
     ctx->split_R = (vertex_counts || list || alg3) ? 0u : g1_split_rank(ctx->tune);
     b.rows[3] = a.take<uint32_t>(n1);
     ok = ok && b.rows[3];

@@ -1569,9 +1569,10 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
     uint32_t *filter = reinterpret_cast<uint32_t *>(smem_raw + slice_smem_bytes(max_v));
     const uint32_t filter_words = 1u << (filter_log2 - 5);
     const uint32_t fshift = 32u - filter_log2;
-    uint32_t *lowbm = filter + filter_words;  // kSplit: split_R bits
+    uint32_t *lowbm = filter + filter_words;                             // kSplit: split_R bits
+    uint32_t *after = lowbm + (kSplit ? (split_R >> 5) : 0u);            // per-vertex counters or listing stage
     if constexpr (kM == 1) {
-        vo.priv = reinterpret_cast<unsigned long long *>(filter + filter_words);
+        vo.priv = reinterpret_cast<unsigned long long *>(after);
         priv_begin(vo);
     }
     Acc acc;
@@ -1581,7 +1582,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
     ListCtx lc;
     const unsigned long long gw = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if constexpr (kM == 2) {
-        lc.stage = filter + filter_words + (size_t)(threadIdx.x >> 5) * kStageSlots;
+        lc.stage = after + (size_t)(threadIdx.x >> 5) * kStageSlots;
         load_list_state(vo, lc, gw);
     }
     const long long t_start = clock64();
