@@ -479,6 +479,19 @@ struct HubSet {
     uint32_t fshift;
 };
 
+// A hub set split at R: ids below R in the shared low bitmap, the others
+// behind the prefilter (which then holds only the set's ids >= R) in the L2
+// bitmap.  For probe pieces of ranges whose split is unknown.
+struct HubMixSet {
+    static constexpr int kUnroll = 4;  // rare pieces: fewer registers held
+    static constexpr int kBatch = 4;
+    static constexpr uint32_t kPad = kEmpty;
+    static constexpr bool kFineTail = true;
+    HubSet H;
+    uint32_t bm;  // shared-window byte address of the low bitmap
+    uint32_t R;
+};
+
 // Probe one batch of N elements against the bucket table: first buckets for
 // all, then the rare continuation for those whose home bucket was full.
 template <int N>
@@ -531,6 +544,26 @@ __device__ __forceinline__ void lookup_batch(const HubSet &H, const uint32_t (&w
     for (int i = 0; i < N; ++i) word[i] = pos[i] ? __ldg(H.bits + (w[i] >> 5)) : 0u;
 #pragma unroll
     for (int i = 0; i < N; ++i) hit[i] = pos[i] && ((word[i] >> (w[i] & 31)) & 1u);
+}
+
+template <int N>
+__device__ __forceinline__ void lookup_batch(const HubMixSet &M, const uint32_t (&w)[N], bool (&hit)[N]) {
+    bool lo[N], pos[N];
+    uint32_t x[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        lo[i] = w[i] < M.R;
+        const uint32_t f = filter_bit(w[i], M.H.fshift);
+        // low ids read their bitmap word, the others their prefilter word
+        x[i] = lds_u32(lo[i] ? M.bm + ((w[i] >> 5) << 2) : shared_addr(M.H.filter) + ((f >> 5) << 2));
+        pos[i] = !lo[i] && w[i] != kEmpty && ((x[i] >> (f & 31u)) & 1u);
+    }
+    uint32_t word[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) word[i] = pos[i] ? __ldg(M.H.bits + (w[i] >> 5)) : 0u;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        hit[i] = lo[i] ? ((x[i] >> (w[i] & 31u)) & 1u) != 0u : (pos[i] && ((word[i] >> (w[i] & 31u)) & 1u));
 }
 
 // ---------------------------------------------------------------------------- probing
@@ -1546,11 +1579,11 @@ __global__ void k_hub_set(const uint32_t *__restrict__ rows, uint32_t i0, uint32
 
 // Probe the tasks [first, last) of the hub rows with row index in
 // [i0, i0 + hub_group) against their bitmaps.
-// With kSplit (split_R > 0), the ranks of the set below split_R also sit in
-// an exact shared bitmap after the prefilter: the low pieces of split probe
-// ranges are answered there, without the prefilter or L2; high pieces and
-// pieces of unsplit ranges take the prefilter and the L2 bitmap (the
-// prefilter holds the whole set).
+// With kSplit (split_R > 0), the ranks of the set below split_R sit in an
+// exact shared bitmap after the prefilter, which then holds only the others:
+// the low pieces of split probe ranges are answered in shared memory, high
+// pieces take the prefilter and the L2 bitmap, pieces of unsplit ranges
+// (HubMixSet) either, id by id.
 template <int kM, bool kSplit = false>
 __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__ tasks, unsigned long long first,
                                                     unsigned long long last, const uint32_t *__restrict__ rows,
@@ -1607,10 +1640,12 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
         if (rebuild) {
             for (uint32_t j = threadIdx.x; j < su; j += blockDim.x) {
                 const uint32_t w = adj2[hb + j];
-                const uint32_t f = filter_bit(w, fshift);
-                atomicOr(filter + (f >> 5), 1u << (f & 31));
-                if constexpr (kSplit)
-                    if (w < split_R) atomicOr(lowbm + (w >> 5), 1u << (w & 31u));
+                if (kSplit && w < split_R) {  // low ids: the exact bitmap only
+                    atomicOr(lowbm + (w >> 5), 1u << (w & 31u));
+                } else {
+                    const uint32_t f = filter_bit(w, fshift);
+                    atomicOr(filter + (f >> 5), 1u << (f & 31));
+                }
             }
             __syncthreads();
             cur_row = task.x;
@@ -1625,7 +1660,8 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
         lc.u = u;
         if constexpr (kSplit)
             // the hub's probe ranges mostly come from DRAM: their next piece is prefetched into L2
-            probe_slice_split<kM, true>(BitmapSet{shared_addr(lowbm), split_R}, H, H, S, k_hi - k_lo, adj2, &ts.next,
+            probe_slice_split<kM, true>(BitmapSet{shared_addr(lowbm), split_R}, H,
+                                        HubMixSet{H, shared_addr(lowbm), split_R}, S, k_hi - k_lo, adj2, &ts.next,
                                         acc, vo, lc);
         else
             probe_slice<kM>(H, S, k_hi - k_lo, adj2, &ts.next, acc, vo, lc);

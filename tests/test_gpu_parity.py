@@ -135,6 +135,25 @@ def test_block_class_split_set(tc, name, bits):
         tc.tc_destroy(c)
 
 
+@pytest.mark.parametrize("bits", [10, 11, 12])
+@pytest.mark.parametrize("name", ["rmat12_ef32", "chung_lu4096", "union", "rmat10"])
+def test_hub_class_split_set(tc, name, bits):
+    """Every row with a set of two or more ranks goes to the hub class, split at
+    rank 2^bits: low pieces in the shared bitmap, high pieces behind the
+    prefilter of the high ranks, and rows ranked at or above 2^bits (whose A
+    tails may hold high ranks) probing both, id by id."""
+    c = tc.tc_create(0)
+    try:
+        tc.tc_set_tuning(c, warp_cap=1, block_cap=1, task_work=64, hub_task_work=64, tiny_cap=0,
+                         block_bits_log2=bits)
+        g = SMALL[name]
+        T, st, L, rp, col = gpu_count(tc, c, g)
+        assert st["class_probes"][2] > st["class_probes"][0] + st["class_probes"][1]
+        assert_parity(T, st, L, rp, col, g)
+    finally:
+        tc.tc_destroy(c)
+
+
 @pytest.mark.parametrize("tiny", [1, 8, 64])
 @pytest.mark.parametrize("name", ["rmat10", "grid33x47", "union", "wheel101", "er4096"])
 def test_tiny_merge_class(tc, name, tiny):
