@@ -675,7 +675,7 @@ __device__ __forceinline__ void lookup_step(const SplitSet &S, const uint32_t (&
 // then the ragged end in one bounds-checked step of U x 32 positions, or in
 // steps of 64 positions (kFineTail: pays where lookups are expensive);
 // positions below `split` are the A part.
-template <int U, bool kFineTail = false, int kM = 0, bool kStage = false, class Set>
+template <int U, bool kFineTail = false, int kM = 0, bool kStage = false, bool kHalfTail = true, class Set>
 __device__ __forceinline__ uint32_t probe_row(const Set &set, const uint32_t *__restrict__ adj2, unsigned long long b,
                                               uint32_t j_lo, uint32_t j_hi, uint32_t split, Acc &acc,
                                               const VertexOut &vo = VertexOut{}, ListCtx *lc = nullptr) {
@@ -694,6 +694,21 @@ __device__ __forceinline__ uint32_t probe_row(const Set &set, const uint32_t *__
         count_step<U>(hit, j0, split, lane, same, cross);
     }
     constexpr int T = kFineTail ? 2 : U;
+    constexpr int H = (kHalfTail && T >= 8) ? T / 2 : T;  // a ragged end of at most half a step takes a half step
+    if (H < T && j0 < j_hi && j_hi - j0 <= 32u * H) {
+        uint32_t w[H];
+        bool hit[H];
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            const uint32_t j = j0 + (uint32_t)i * 32u;
+            w[i] = j + lane < j_hi ? __ldg(row + j) : Set::kPad;
+        }
+        lookup_step<H, true>(set, w, hit);
+        if constexpr (kM == 1) credit_third<H>(hit, w, vo);
+        if constexpr (kM == 2) emit_step<H, false, kStage>(hit, w, w, vo, *lc);
+        count_step<H>(hit, j0, split, lane, same, cross);
+        j0 = j_hi;
+    }
     for (; j0 < j_hi; j0 += 32u * T) {
         uint32_t w[T];
         bool hit[T];
@@ -1004,9 +1019,9 @@ __global__ void __launch_bounds__(256, 3) k_isect_warp(const uint2 *__restrict__
                 uint32_t got;
                 if constexpr (kM == 2) lc.v = __shfl_sync(0xFFFFFFFFu, vid, t);
                 if constexpr (kCuckoo)
-                    got = probe_row<CuckooTable::kUnroll, false, kM>(C, adj2, bt, 0, lt, ht, acc, vo, &lc);
+                    got = probe_row<CuckooTable::kUnroll, false, kM, false, false>(C, adj2, bt, 0, lt, ht, acc, vo, &lc);
                 else
-                    got = probe_row<BucketTable::kUnroll, false, kM>(T, adj2, bt, 0, lt, ht, acc, vo, &lc);
+                    got = probe_row<BucketTable::kUnroll, false, kM, false, false>(T, adj2, bt, 0, lt, ht, acc, vo, &lc);
                 if constexpr (kM == 1) {
                     got = warp_sum(got);
                     const uint32_t vt = __shfl_sync(0xFFFFFFFFu, vid, t);
