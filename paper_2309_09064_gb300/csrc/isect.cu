@@ -695,6 +695,21 @@ __device__ __forceinline__ uint32_t probe_row(const Set &set, const uint32_t *__
     }
     constexpr int T = kFineTail ? 2 : U;
     constexpr int H = (kHalfTail && T >= 8) ? T / 2 : T;  // a ragged end of at most half a step takes a half step
+    constexpr int Q = (kHalfTail && T >= 8) ? T / 4 : T;  // of at most a quarter step, a quarter step
+    if (Q < H && j0 < j_hi && j_hi - j0 <= 32u * Q) {
+        uint32_t w[Q];
+        bool hit[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const uint32_t j = j0 + (uint32_t)i * 32u;
+            w[i] = j + lane < j_hi ? __ldg(row + j) : Set::kPad;
+        }
+        lookup_step<Q, true>(set, w, hit);
+        if constexpr (kM == 1) credit_third<Q>(hit, w, vo);
+        if constexpr (kM == 2) emit_step<Q, false, kStage>(hit, w, w, vo, *lc);
+        count_step<Q>(hit, j0, split, lane, same, cross);
+        j0 = j_hi;
+    }
     if (H < T && j0 < j_hi && j_hi - j0 <= 32u * H) {
         uint32_t w[H];
         bool hit[H];
