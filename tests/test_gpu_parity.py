@@ -117,20 +117,22 @@ def test_every_intersection_class(tc, name, caps):
 @pytest.mark.parametrize("bits", [0, 10, 11, 12, 14, 18, 20])
 @pytest.mark.parametrize("name", ["rmat10", "rmat12_ef32", "union", "K40", "chung_lu4096", "er4096", "rmat15",
                                   "two_hubs"])
-def test_block_class_split_set(tc, name, bits):
+@pytest.mark.parametrize("order_name", ["degree", "id"])
+def test_block_class_split_set(tc, name, bits, order_name):
     """Block-class sets split at rank 2^bits (a shared bitmap below, the cuckoo
     table above; the rows stage puts the low ranks of every level-spanning part
     first): with 2^bits below, inside and above the rank range of the graph,
-    warp steps take the bitmap alone, the table alone and both; every row with a
-    horizontal out-edge goes to the block class."""
-    c = tc.tc_create(0)
+    probe pieces take the bitmap, the table, or both id by id; every row whose
+    set holds two or more ranks goes to the block class.  Under the id order
+    the ranks are the ids."""
+    c = tc.tc_create(0, order=tc.TC_ORDER_DEGREE if order_name == "degree" else tc.TC_ORDER_ID)
     try:
         tc.tc_set_tuning(c, warp_cap=1, block_cap=13107, task_work=256, tiny_cap=0, block_bits_log2=bits)
         g = {"rmat15": lambda: gg.rmat(15, 16, seed=2), "two_hubs": two_hub_graph}.get(name, lambda: SMALL[name])()
         T, st, L, rp, col = gpu_count(tc, c, g)
         if name != "two_hubs":  # its hub rows stay in the hub class
             assert st["class_probes"][2] == 0 and st["class_probes"][1] > st["class_probes"][0]
-        assert_parity(T, st, L, rp, col, g)
+        assert_parity(T, st, L, rp, col, g, degree_order=order_name == "degree")
     finally:
         tc.tc_destroy(c)
 
