@@ -840,7 +840,7 @@ __device__ __forceinline__ unsigned long long rec_start(const uint4 &r) {
 // Long probe ranges are walked in kSeg pieces, one warp each.  In the warp
 // class, ranges shorter than flat_cap (a tuning knob) are concatenated
 // (probe_flat) so that every lane has work.
-constexpr uint32_t kSeg = 512;
+constexpr uint32_t kSeg = 2048;
 
 // Build the cuckoo table of a hashed set row[0..s) (all threads of a block,
 // or of a warp, call it): clear 2m slots, insert every key by displacement, stash the keys
