@@ -1872,11 +1872,12 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         TC_CUDA(ctx, cudaStreamSynchronize(s));
         // split (plain counts): the prefilter shrinks to make room for the low-rank bitmap
         const uint32_t split_R = ctx->split_R;
+        const uint32_t hmax_v = hub_max_v(tu, split_R);
         uint32_t filter_log2 = tu.hub_filter_log2;
         while (split_R && filter_log2 > 10 &&
-               slice_smem_bytes(tu.max_v) + (1ull << filter_log2) / 8 + split_R / 8 + 2048 > kSmemLimit)
+               slice_smem_bytes(hmax_v) + (1ull << filter_log2) / 8 + split_R / 8 + 2048 > kSmemLimit)
             --filter_log2;
-        const size_t smem = slice_smem_bytes(tu.max_v) + (1ull << filter_log2) / 8 + split_R / 8 + priv +
+        const size_t smem = slice_smem_bytes(hmax_v) + (1ull << filter_log2) / 8 + split_R / 8 + priv +
                             (mode == 2 ? 4ull * kStageSlots * (tu.hub_threads / 32) : 0);
         if (smem > kSmemLimit) return set_error(ctx, TC_ERR_INVALID, "tuning leaves no shared memory for this mode");
         auto hub = split_R ? k_isect_hub<0, true>
@@ -1901,7 +1902,7 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
             hub<<<(unsigned)grid, tu.hub_threads, smem, s>>>(b.tasks[2], first, last, b.rows[2], b.ntask[2], i0,
                                                                      b.rp, b.adj2, b.fcnt, b.eoff, b.erec, ctx->d_ctl,
                                                                      b.hub_bits,
-                                                                     b.hub_words, tu.max_v, chunk, filter_log2,
+                                                                     b.hub_words, hmax_v, chunk, filter_log2,
                                                                      b.groups, vo, split_R, b.glo, b.lv);
             note_launch(ctx, 2);
         }

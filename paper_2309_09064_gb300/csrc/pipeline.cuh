@@ -88,6 +88,10 @@ inline uint32_t g1_split_rank(const Tuning &tu) {
     return (tu.table_kind == 0 && tu.block_bits_log2) ? (1u << tu.block_bits_log2) : 0u;
 }
 constexpr uint32_t kNoSplit = 0xFFFFFFFFu;  // glo[x]: G1(x) was not split
+// Out-edges per hub task: with a split rank the hub kernel's shared memory also
+// holds the low-rank bitmap, so its tasks take at most 1024 records to leave
+// room for a larger prefilter (the planner and the kernel use the same value).
+inline uint32_t hub_max_v(const Tuning &tu, uint32_t R) { return (R && tu.max_v > 1024) ? 1024u : tu.max_v; }
 constexpr size_t kSmemLimitBytes = 227 * 1024;  // shared memory one block may opt into on sm_103a
 // Cuckoo slots per table of the block class and the most ranks at or above
 // R one block-class set may hold (R = 0: no split, the whole set).

@@ -811,7 +811,7 @@ tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_de
     }
     const uint32_t work[3] = {tu.warp_task_work, tu.task_work, tu.hub_task_work};
     const uint32_t mult[3] = {1, 2, 2};
-    const uint32_t maxv[3] = {0xFFFFFFFFu, tu.max_v, tu.max_v};
+    const uint32_t maxv[3] = {0xFFFFFFFFu, tu.max_v, hub_max_v(tu, g1_lo)};
     for (int c = 0; c < 3; ++c) {
         k_plan<<<grid_for((uint64_t)n * 32, 256, cap), 256, 0, s>>>(b.rows[c], &ctx->d_ctl->n_rows[c], b.rp, b.fcnt,
                                                                     b.eoff, b.erec, b.ntask[c], work[c], mult[c],

@@ -38,7 +38,7 @@ struct Tuning {
     uint32_t tiny_cap = 16;          // s(u) <= tiny_cap and deg(u) <= 4 tiny_cap: thread-per-row merges (0: off)
     uint32_t table_kind = 0;         // warp/block-class sets: 0 two-choice cuckoo tables, 1 bucketed tables
     uint32_t flat_cap = 128;         // warp class: probe ranges shorter than this are concatenated across lanes
-    uint32_t block_bits_log2 = 19;   // block class (cuckoo): ranks below 2^k in a shared bitmap (0: off)
+    uint32_t block_bits_log2 = 20;   // block class (cuckoo): ranks below 2^k in a shared bitmap (0: off)
     uint32_t batch_small_slots = 0;  // batches: graphs this small counted a block each in one launch (0: off)
 };
 
