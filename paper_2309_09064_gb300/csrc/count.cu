@@ -46,6 +46,7 @@ size_t pipeline_bytes(const tc_ctx *ctx, uint32_t n, uint64_t slots, uint32_t ma
     if (own_levels) bytes += r(4 * n1);            // L
     bytes += 8 * r(8 * n1);                        // fpref eoff tpref[3] lv rkeys0 rkeys1
     bytes += r(4 * (slots + 1));                   // adj2
+    bytes += r(4 * (slots / 32 + 2));              // fence
     bytes += r(16 * (slots / 2 + 1));              // probe records: one per oriented G0 edge
     bytes += r(4 * (256 * rtiles + 1)) + r(8 * (256 * rtiles + 2));  // radix digit counts and offsets
     bytes += r(8 * scan_tmp_elems(std::max<uint64_t>(n1 + 1, 256 * rtiles + 2)));  // scan tiles
@@ -142,6 +143,8 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     b.rcounts = a.take<uint32_t>(256 * rtiles + 1);
     b.roffs = a.take<uint64_t>(256 * rtiles + 2);
     b.adj2 = a.take<uint32_t>(g.slots + 1);
+    b.fence = a.take<uint32_t>(g.slots / 32 + 2);
+    b.slots = g.slots;
     b.erec_cap = g.slots / 2 + 1;
     b.erec = a.take<uint4>(b.erec_cap);
     b.scan_tmp = a.take<uint64_t>(scan_tmp_elems(std::max<uint64_t>(n1 + 1, 256 * rtiles + 2)));
@@ -181,7 +184,7 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
         TC_CUDA(ctx, cudaMemsetAsync(b.hits, 0, 8 * z.tiny, s));
         TC_CUDA(ctx, cudaMemsetAsync(b.wstate, 0, 16 * z.states, s));
     }
-    ok = ok && b.fpref && b.eoff && b.lv && b.rkeys0 && b.rkeys1 && b.rcounts && b.roffs && b.adj2 && b.erec &&
+    ok = ok && b.fpref && b.eoff && b.lv && b.rkeys0 && b.rkeys1 && b.rcounts && b.roffs && b.adj2 && b.fence && b.erec &&
          b.scan_tmp && b.task_pool && (!hub_maps || b.hub_bits);
     if (!ok) return set_error(ctx, TC_ERR_OOM, "arena carve failed");
 

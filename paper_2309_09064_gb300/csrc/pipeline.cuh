@@ -35,6 +35,8 @@ struct PipeBufs {
     uint32_t *fcnt = nullptr;       // [n]   |F(x)|  horizontal out-neighbours (ids)
     uint32_t *gcnt = nullptr;       // [n]   |G1(x)| level-spanning neighbours (ranks)
     uint32_t *adj2 = nullptr;       // [S]   the rewritten rows; A(x) (ranks) is descending
+    uint32_t *fence = nullptr;      // [S/32] every 32nd slot of adj2 (searches in long A parts)
+    uint64_t slots = 0;             // S
     uint32_t *big = nullptr;        // [n]   rows whose A part the block sorter sorts
     uint32_t *huge = nullptr;       // [n]   rows of very high degree (filled by a block each)
     uint4 *vmeta = nullptr;         // [n]   {A start lo, A start hi, |A(x)|, |G1(x)|}

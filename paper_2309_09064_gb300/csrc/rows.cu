@@ -551,9 +551,34 @@ __global__ void k_chunk_rows(uint32_t n, const uint64_t *__restrict__ eoff, uint
     }
 }
 
+// Every 32nd slot of the rewritten rows, kept compact: fence[k] = adj2[32 k].
+// A search in a long sorted A part runs over its fences first (one 128-byte
+// line holds 32 of them, and the array stays in L2), then inside the one
+// 128-byte line of adj2 left.
+__global__ void k_fence(const uint32_t *__restrict__ adj2, uint64_t slots, uint32_t *__restrict__ fence) {
+    const uint64_t nf = (slots + 31) / 32;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nf; k += stride) fence[k] = adj2[32 * k];
+}
+
+// The interval [*lo, *hi) of positions of the descending run adj2[as, as + av)
+// that holds its first element below r, from a binary search over the run's
+// fences: at most 32 positions (all positions when the run holds no fence).
+__device__ __forceinline__ void fence_search(const uint32_t *__restrict__ fence, uint64_t as, uint32_t av, uint32_t r,
+                                             uint32_t *lo, uint32_t *hi) {
+    const uint64_t k0 = (as + 31) / 32, kend = (as + av + 31) / 32;  // fences at 32 k in [as, as + av)
+    uint64_t flo = k0, fhi = kend > k0 ? kend : k0;
+    while (flo < fhi) {
+        const uint64_t mid = (flo + fhi) >> 1;
+        if (fence[mid] < r) fhi = mid; else flo = mid + 1;
+    }
+    *lo = flo > k0 ? (uint32_t)(32 * (flo - 1) - as + 1) : 0u;  // fence flo - 1 holds a rank >= r
+    *hi = flo < kend ? (uint32_t)(32 * flo - as) : av;          // fence flo holds one below r
+}
+
 // For every oriented edge u -> v: the number p of elements of A(v) ranked
-// below u (binary search in the descending A(v); all of A(v) when it was left
-// unsorted), and the probe record {start, length = |G1(v)| + p, split = p}
+// below u (binary search in the descending A(v), over its fences first; all
+// of A(v) when it was left unsorted), and the probe record {start, length = |G1(v)| + p, split = p}
 // of the range at the end of v's slots.  One warp per chunk; every lane walks
 // from the chunk's first row to the rows of its own edges, and runs the
 // binary searches of kRecBatch edges in lockstep (independent loads in
@@ -563,7 +588,7 @@ constexpr int kRecBatch = 2;
 __global__ void k_records(uint32_t n, const uint64_t *__restrict__ eoff, const uint32_t *__restrict__ chunk_row,
                           const uint64_t *__restrict__ rp, const uint32_t *__restrict__ adj2,
                           const uint2 *__restrict__ lv, const uint4 *__restrict__ vmeta, uint4 *__restrict__ erec,
-                          Ctl *ctl) {
+                          Ctl *ctl, const uint32_t *__restrict__ fence) {
     const unsigned lane = lane_id();
     const uint64_t E = eoff[n];
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->e0 = E;
@@ -605,6 +630,37 @@ __global__ void k_records(uint32_t n, const uint64_t *__restrict__ eoff, const u
 #pragma unroll
                     for (uint32_t j = 0; j < kRecLinear; ++j) c += j < av[i] && adj2[as[i] + j] >= r[i];
                     lo[i] = hi[i] = c;
+                }
+            }
+            // long sorted A parts: over the fences first, in lockstep
+            uint64_t flo[kRecBatch], fhi[kRecBatch], fk0[kRecBatch], fend[kRecBatch];
+#pragma unroll
+            for (int i = 0; i < kRecBatch; ++i) {
+                fk0[i] = (as[i] + 31) / 32;
+                fend[i] = (as[i] + av[i] + 31) / 32;
+                const bool use = hi[i] > lo[i] + 32;
+                flo[i] = fk0[i];
+                fhi[i] = use ? fend[i] : fk0[i];
+            }
+            for (int step = 0; step < 17; ++step) {
+                bool any = false;
+#pragma unroll
+                for (int i = 0; i < kRecBatch; ++i) {
+                    if (flo[i] < fhi[i]) {
+                        const uint64_t mid = (flo[i] + fhi[i]) >> 1;
+                        if (fence[mid] < r[i]) fhi[i] = mid; else flo[i] = mid + 1;
+                        any = true;
+                    }
+                }
+                if (!any) break;
+            }
+#pragma unroll
+            for (int i = 0; i < kRecBatch; ++i) {
+                if (hi[i] > lo[i] + 32) {  // the one line left between two fences
+                    const uint32_t l = flo[i] > fk0[i] ? (uint32_t)(32 * (flo[i] - 1) - as[i] + 1) : 0u;
+                    const uint32_t h = flo[i] < fend[i] ? (uint32_t)(32 * flo[i] - as[i]) : av[i];
+                    lo[i] = l;
+                    hi[i] = h;
                 }
             }
             // first position holding a rank below r, all searches in lockstep
@@ -695,7 +751,7 @@ __global__ void k_records_tasks(const uint2 *__restrict__ tasks, unsigned long l
                                 const uint64_t *__restrict__ rp, const uint32_t *__restrict__ fcnt,
                                 const uint64_t *__restrict__ eoff, const uint32_t *__restrict__ adj2,
                                 const uint2 *__restrict__ lv, const uint4 *__restrict__ vmeta,
-                                uint4 *__restrict__ erec) {
+                                uint4 *__restrict__ erec, const uint32_t *__restrict__ fence) {
     const unsigned lane = lane_id();
     const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
     for (unsigned long long t = first + (((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < last;
@@ -713,6 +769,7 @@ __global__ void k_records_tasks(const uint2 *__restrict__ tasks, unsigned long l
             uint32_t p = av;  // an unsorted A part is probed whole
             if (av <= kSortCap) {
                 uint32_t lo = 0, hi = av;  // first position holding a rank below u's
+                if (av > 32) fence_search(fence, as, av, ru, &lo, &hi);
                 while (lo < hi) {
                     const uint32_t mid = (lo + hi) >> 1;
                     if (adj2[as + mid] < ru) hi = mid; else lo = mid + 1;
@@ -789,6 +846,8 @@ tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_de
         k_sort_big<<<(unsigned)ctx->num_sms, 1024, smem, s>>>(b.big, ctx->d_ctl, b.rp, b.fcnt, b.gcnt, b.adj2);
         ++launches;
     }
+    k_fence<<<cap, 256, 0, s>>>(b.adj2, b.slots, b.fence);
+    ++launches;
     launches += scan_u32_to_u64(b.fcnt, b.eoff, n, b.scan_tmp, s);
     // a count split into shards builds each shard's records after planning (records_for_shard)
     const bool sharded = ctx->nshards > 1;
@@ -796,7 +855,8 @@ tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_de
         k_e0<<<1, 1, 0, s>>>(n, b.eoff, ctx->d_ctl);
     } else {
         k_chunk_rows<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.eoff, b.chunk_row);
-        k_records<<<cap, 256, 0, s>>>(n, b.eoff, b.chunk_row, b.rp, b.adj2, b.lv, b.vmeta, b.erec, ctx->d_ctl);
+        k_records<<<cap, 256, 0, s>>>(n, b.eoff, b.chunk_row, b.rp, b.adj2, b.lv, b.vmeta, b.erec, ctx->d_ctl,
+                                      b.fence);
     }
     // fdeg and R are free after the levels: class of every vertex, 0/1 indicator
     k_class_flags<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.fcnt, b.gcnt, b.deg, b.fdeg, ctx->d_ctl, tu.warp_cap,
@@ -850,7 +910,7 @@ tc_status records_for_shard(tc_ctx *ctx, const PipeBufs &b) {
         if (hi <= lo) continue;
         k_records_tasks<<<grid_for((hi - lo) * 32, 256, cap), 256, 0, s>>>(b.tasks[c], lo, hi, b.rows[c], b.ntask[c],
                                                                            b.rp, b.fcnt, b.eoff, b.adj2, b.lv,
-                                                                           b.vmeta, b.erec);
+                                                                           b.vmeta, b.erec, b.fence);
         note_launch(ctx);
     }
     TC_CUDA(ctx, cudaGetLastError());
