@@ -28,6 +28,8 @@ struct PipeBufs {
     uint2 *lv = nullptr;            // [n]   {rank, level}
     uint32_t *lvp = nullptr;        // [n]   rank << 8 | level (only when n <= 2^24 and levels < 255)
     unsigned long long *rkeys0 = nullptr, *rkeys1 = nullptr;  // [n] radix-sort keys
+    const unsigned long long *order = nullptr;  // [n] the sorted keys: the vertex of rank i in their low half
+                                                //       (null under the id order: rank = id)
     uint32_t *rcounts = nullptr;    // radix digit counts per tile
     uint64_t *roffs = nullptr;      // their scan
     // partition / orientation / rows: every vertex keeps its CSR slots
@@ -119,7 +121,7 @@ tc_status compute_levels(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint64_t sl
 tc_status given_levels(tc_ctx *ctx, const PipeBufs &b, uint32_t n, const uint32_t *levels_in);
 tc_status selftest_barrier(tc_ctx *ctx, uint32_t timeout_ms);
 // rank of every vertex in the working order, packed with its level (lv)
-tc_status compute_ranks(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_deg);
+tc_status compute_ranks(tc_ctx *ctx, PipeBufs &b, uint32_t n, uint32_t max_deg);
 // Listing: close the open chunks, then move the triangles written past the
 // first t_big positions into the gaps below it (list.cu).  g_end = the chunk
 // cursor after the listing pass.

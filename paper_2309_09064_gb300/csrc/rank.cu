@@ -58,7 +58,7 @@ unsigned grid_for(uint64_t work, unsigned threads, unsigned cap) {
 
 }  // namespace
 
-tc_status compute_ranks(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_deg) {
+tc_status compute_ranks(tc_ctx *ctx, PipeBufs &b, uint32_t n, uint32_t max_deg) {
     cudaStream_t s = ctx->stream;
     const unsigned cap = (unsigned)ctx->num_sms * 16u;
     if (n == 0) return TC_OK;
@@ -73,6 +73,7 @@ tc_status compute_ranks(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max
         k_rank_scatter<<<grid_for(n, 256, cap), 256, 0, s>>>(n, cur, b.rank, b.inv);
         ++launches;
         rank = b.rank;
+        b.order = cur;
     }
     k_pack_rank_level<<<grid_for(n, 256, cap), 256, 0, s>>>(n, rank, b.L, b.lv, b.lvp);
     note_launch(ctx, launches + 1);

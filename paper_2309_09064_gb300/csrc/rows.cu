@@ -523,17 +523,29 @@ __global__ void k_class_flags(uint32_t n, const uint32_t *__restrict__ fcnt, con
     if (lane_id() == 0 && my_max) atomicMax(&ctl->max_s2, my_max);
 }
 
-__global__ void k_class_indicator(uint32_t n, const uint32_t *__restrict__ cls, uint32_t c, uint32_t *__restrict__ ind) {
+// The rows of every class are listed in the working order (order[i] = the
+// vertex of rank i, the sorted rank keys; null: the identity): the largest
+// hashed sets come first and the task lists end with the smallest tasks, so
+// the blocks that claim the last runs of tasks finish close together.
+__device__ __forceinline__ uint32_t vertex_at(const unsigned long long *order, uint64_t i) {
+    return order ? (uint32_t)(order[i] & 0xFFFFFFFFull) : (uint32_t)i;
+}
+
+__global__ void k_class_indicator(uint32_t n, const uint32_t *__restrict__ cls, uint32_t c, uint32_t *__restrict__ ind,
+                                  const unsigned long long *__restrict__ order) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) ind[x] = cls[x] == c;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        ind[i] = cls[vertex_at(order, i)] == c;
 }
 
 __global__ void k_class_scatter(uint32_t n, const uint32_t *__restrict__ cls, uint32_t c,
                                 const unsigned long long *__restrict__ pos, uint32_t *__restrict__ rows,
-                                unsigned int *__restrict__ n_rows) {
+                                unsigned int *__restrict__ n_rows, const unsigned long long *__restrict__ order) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride)
-        if (cls[x] == c) rows[pos[x]] = (uint32_t)x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t x = vertex_at(order, i);
+        if (cls[x] == c) rows[pos[i]] = x;
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) *n_rows = (unsigned int)pos[n];
 }
 
@@ -864,10 +876,11 @@ tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_de
                                                         b.glo, b.lv);
     launches += sharded ? 2 : 3;
     for (uint32_t c = 0; c < 4; ++c) {
-        k_class_indicator<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.fdeg, c, b.R);
+        k_class_indicator<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.fdeg, c, b.R, b.order);
         launches += 2 + scan_u32_to_u64(b.R, b.fpref, n, b.scan_tmp, s);
         k_class_scatter<<<grid_for(n, 256, cap), 256, 0, s>>>(
-            n, b.fdeg, c, reinterpret_cast<const unsigned long long *>(b.fpref), b.rows[c], &ctx->d_ctl->n_rows[c]);
+            n, b.fdeg, c, reinterpret_cast<const unsigned long long *>(b.fpref), b.rows[c], &ctx->d_ctl->n_rows[c],
+            b.order);
     }
     const uint32_t work[3] = {tu.warp_task_work, tu.task_work, tu.hub_task_work};
     const uint32_t mult[3] = {1, 2, 2};
