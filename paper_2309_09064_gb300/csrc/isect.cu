@@ -1857,7 +1857,9 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         uint64_t grid = (uint64_t)ctx->num_sms * per_sm;
         if (grid > hi1 - lo1) grid = hi1 - lo1;
         grid = list_grid(grid, tu.block_threads / 32);
-        const unsigned long long chunk = std::max<unsigned long long>(1, (hi1 - lo1) / (grid * 8));
+        // runs of about 1/64 of a block's share of the tasks: with the rows in the working order the
+        // last runs hold the smallest tasks, and short runs let the blocks finish close together
+        const unsigned long long chunk = std::max<unsigned long long>(1, (hi1 - lo1) / (grid * 64));
         kern<<<(unsigned)grid, tu.block_threads, smem, s>>>(b.tasks[1], b.rows[1], b.ntask[1], b.rp, b.adj2, b.fcnt,
                                                             b.eoff, b.erec, ctx->d_ctl, tu.max_v, units, split_R,
                                                             b.glo, b.gcnt, b.lv, chunk, lo1, hi1, b.groups, vo);
@@ -1898,7 +1900,7 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
             uint64_t grid = (uint64_t)ctx->num_sms * per_sm;
             if (grid > last - first) grid = last - first;
             grid = list_grid(grid, tu.hub_threads / 32);
-            const unsigned long long chunk = std::max<unsigned long long>(1, (last - first) / (grid * 4));
+            const unsigned long long chunk = std::max<unsigned long long>(1, (last - first) / (grid * 8));
             hub<<<(unsigned)grid, tu.hub_threads, smem, s>>>(b.tasks[2], first, last, b.rows[2], b.ntask[2], i0,
                                                                      b.rp, b.adj2, b.fcnt, b.eoff, b.erec, ctx->d_ctl,
                                                                      b.hub_bits,
