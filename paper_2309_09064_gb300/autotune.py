@@ -42,6 +42,8 @@ CANDIDATES = [
     {"block_bits_log2": 18},
     {"block_bits_log2": 20},
     {"hub_task_work": 2097152},
+    {"task_work": 2097152, "warp_task_work": 16384},
+    {"max_v": 1024},
     {"batch_small_slots": 16384},
     {"batch_small_slots": 65536},
     {"batch_small_slots": 262144},

@@ -26,10 +26,10 @@ constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 struct Tuning {
     uint32_t warp_cap = 768;         // s(u) <= warp_cap: warp tasks, per-warp smem table
     uint32_t block_cap = 13107;      // s(u) <= block_cap: block tasks, smem table; larger: hub tasks
-    uint32_t task_work = 2097152;    // target probes per block task (at least 2 s(u))
+    uint32_t task_work = 4194304;    // target probes per block task (at least 2 s(u))
     uint32_t warps_per_block = 8;    // warp-class kernel: warps per block
     uint32_t block_threads = 1024;   // block-class kernel threads
-    uint32_t warp_task_work = 16384; // target probes per warp task
+    uint32_t warp_task_work = 65536; // target probes per warp task
     uint32_t hub_task_work = 1048576; // target probes per hub task
     uint32_t max_v = 2048;           // out-neighbours per block / hub task (shared-memory metadata)
     uint32_t hub_group = 32;         // hub rows sharing one launch (one L2-resident bitmap each)
