@@ -173,6 +173,12 @@ tc_status tc_destroy(tc_ctx *ctx) {
     if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
     for (int i = 0; i < 10; ++i)
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    for (int i = 0; i < 2; ++i)
+        if (ctx->side_ev[i]) cudaEventDestroy(ctx->side_ev[i]);
+    if (ctx->side_stream) {
+        cudaStreamSynchronize(ctx->side_stream);
+        cudaStreamDestroy(ctx->side_stream);
+    }
     if (ctx->graph_pool) cudaMemPoolDestroy(ctx->graph_pool);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;

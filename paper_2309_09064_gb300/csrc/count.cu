@@ -34,7 +34,7 @@ tc_status pull(tc_ctx *ctx) {
 
 // Bytes of scratch for a graph with n vertices, `slots` CSR slots and the
 // given maximum degree.
-size_t pipeline_bytes(const tc_ctx *ctx, uint32_t n, uint64_t slots, uint32_t max_deg, bool own_levels,
+size_t pipeline_bytes(const tc_ctx *ctx, uint32_t n, uint64_t slots, uint32_t max_deg, bool own_levels, bool plain,
                       uint64_t *hub_words, uint32_t *hub_maps) {
     auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t n1 = (size_t)n + 1;
@@ -55,7 +55,8 @@ size_t pipeline_bytes(const tc_ctx *ctx, uint32_t n, uint64_t slots, uint32_t ma
     *hub_maps = 0;
     if (max_deg > ctx->tune.block_cap) {
         *hub_words = ((((uint64_t)n + 31) / 32) + 31) & ~uint64_t(31);
-        *hub_maps = ctx->tune.hub_group;
+        // plain counts run two hub groups at a time (isect.cu): two sets of bitmaps
+        *hub_maps = ctx->tune.hub_group * (plain ? 2u : 1u);
         bytes += r(4ull * *hub_words * *hub_maps);
     }
     return bytes + 4096;
@@ -93,7 +94,8 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     const uint32_t launches0 = ctx->launches;  // the context's running total before this call
     uint64_t hub_words = 0;
     uint32_t hub_maps = 0;
-    const size_t need = pipeline_bytes(ctx, n, g.slots, g.max_deg, levels_out == nullptr, &hub_words, &hub_maps) +
+    const bool plain = !(vertex_counts || list || alg3);
+    const size_t need = pipeline_bytes(ctx, n, g.slots, g.max_deg, levels_out == nullptr, plain, &hub_words, &hub_maps) +
                         (vertex_counts ? 8ull * ((size_t)n + 1) + 256 : 0) + (list ? list_bytes(ctx, n, list->capacity) : 0);
     tc_status st = arena_reserve(ctx, need);
     if (st != TC_OK) return st;
@@ -125,7 +127,7 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     // the split set serves the plain count; the per-vertex counts and the
     // listing are faster without it (their time goes to counters and output
     // writes, and the split's extra pieces cost more than its lookups save)
-    ctx->split_R = (vertex_counts || list || alg3) ? 0u : g1_split_rank(ctx->tune);
+    ctx->split_R = plain ? g1_split_rank(ctx->tune) : 0u;
     b.rows[3] = a.take<uint32_t>(n1);
     ok = ok && b.rows[3];
     for (int c = 0; c < 3; ++c) {
@@ -151,6 +153,7 @@ tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, 
     b.task_cap = g.slots / 2 + 1;
     b.task_pool = a.take<uint2>(b.task_cap);
     b.hub_words = hub_words;
+    b.hub_sets = hub_maps > ctx->tune.hub_group ? 2u : 1u;
     if (hub_maps) b.hub_bits = a.take<uint32_t>(hub_words * hub_maps);
     b.groups = groups;
     if (vertex_counts) {

@@ -1624,7 +1624,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
                                                     Ctl *ctl, const uint32_t *bits, uint64_t words, uint32_t max_v,
                                                     unsigned long long chunk, uint32_t filter_log2, GroupSpec groups,
                                                     VertexOut vo, uint32_t split_R = 0, const uint32_t *__restrict__ glo = nullptr,
-                                                    const uint2 *__restrict__ lv = nullptr) {
+                                                    const uint2 *__restrict__ lv = nullptr, int ctr = 2) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ TaskSmem ts;
     const unsigned lane = lane_id();
@@ -1649,7 +1649,7 @@ __global__ void __launch_bounds__(1024, 1) k_isect_hub(const uint2 *__restrict__
         load_list_state(vo, lc, gw);
     }
     const long long t_start = clock64();
-    while (next_task(ctl, 2, first, last, chunk, tasks, &ts, t_start)) {
+    while (next_task(ctl, ctr, first, last, chunk, tasks, &ts, t_start)) {
         const uint2 task = ts.task;
         const uint32_t u = rows[task.x], nt = ntask[task.x];
         const uint32_t fu = fcnt[u];
@@ -1888,25 +1888,50 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
         int per_sm = 0;
         TC_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hub, tu.hub_threads, smem));
         if (per_sm < 1) per_sm = 1;
+        // Plain counts with two sets of bitmaps: groups alternate between the
+        // context's stream and a side stream, each with its own bitmaps and task
+        // counter, so that a group's last tasks overlap the next group's start.
+        // (Per-vertex counts and listing keep one stream: their per-warp output
+        // state is indexed by the warp's place in the grid.)
+        const bool two = mode == 0 && b.hub_sets == 2 && nh > tu.hub_group;
+        if (two) {
+            if (!ctx->side_stream) {
+                int prio = 0;
+                TC_CUDA(ctx, cudaStreamGetPriority(s, &prio));
+                TC_CUDA(ctx, cudaStreamCreateWithPriority(&ctx->side_stream, cudaStreamNonBlocking, prio));
+                for (int i = 0; i < 2; ++i)
+                    TC_CUDA(ctx, cudaEventCreateWithFlags(&ctx->side_ev[i], cudaEventDisableTiming));
+            }
+            TC_CUDA(ctx, cudaEventRecord(ctx->side_ev[0], s));
+            TC_CUDA(ctx, cudaStreamWaitEvent(ctx->side_stream, ctx->side_ev[0], 0));
+        }
+        uint32_t gi = 0;
         for (uint32_t i0 = 0; i0 < nh; i0 += tu.hub_group) {
             const uint32_t g = std::min<uint32_t>(tu.hub_group, nh - i0);
             const unsigned long long first = std::max<unsigned long long>(pref[i0], lo2);
             const unsigned long long last = std::min<unsigned long long>(pref[i0 + g], hi2);
             if (first >= last) continue;  // none of this group's tasks is in this shard
-            TC_CUDA(ctx, cudaMemsetAsync(b.hub_bits, 0, 4ull * b.hub_words * g, s));
-            TC_CUDA(ctx, cudaMemsetAsync(&ctx->d_ctl->task_next[2], 0, sizeof(unsigned), s));
-            k_hub_set<<<(unsigned)ctx->num_sms * 4u, 256, 0, s>>>(b.rows[2], i0, g, b.rp, b.fcnt, b.adj2, b.hub_bits,
-                                                                 b.hub_words);
+            const bool side = two && (gi++ & 1u);
+            cudaStream_t gs = side ? ctx->side_stream : s;
+            uint32_t *bits = b.hub_bits + (side ? b.hub_words * tu.hub_group : 0ull);
+            const int ctr = side ? 3 : 2;
+            TC_CUDA(ctx, cudaMemsetAsync(bits, 0, 4ull * b.hub_words * g, gs));
+            TC_CUDA(ctx, cudaMemsetAsync(&ctx->d_ctl->task_next[ctr], 0, sizeof(unsigned), gs));
+            k_hub_set<<<(unsigned)ctx->num_sms * 4u, 256, 0, gs>>>(b.rows[2], i0, g, b.rp, b.fcnt, b.adj2, bits,
+                                                                  b.hub_words);
             uint64_t grid = (uint64_t)ctx->num_sms * per_sm;
             if (grid > last - first) grid = last - first;
             grid = list_grid(grid, tu.hub_threads / 32);
             const unsigned long long chunk = std::max<unsigned long long>(1, (last - first) / (grid * 8));
-            hub<<<(unsigned)grid, tu.hub_threads, smem, s>>>(b.tasks[2], first, last, b.rows[2], b.ntask[2], i0,
-                                                                     b.rp, b.adj2, b.fcnt, b.eoff, b.erec, ctx->d_ctl,
-                                                                     b.hub_bits,
-                                                                     b.hub_words, hmax_v, chunk, filter_log2,
-                                                                     b.groups, vo, split_R, b.glo, b.lv);
+            hub<<<(unsigned)grid, tu.hub_threads, smem, gs>>>(b.tasks[2], first, last, b.rows[2], b.ntask[2], i0,
+                                                                      b.rp, b.adj2, b.fcnt, b.eoff, b.erec, ctx->d_ctl,
+                                                                      bits, b.hub_words, hmax_v, chunk, filter_log2,
+                                                                      b.groups, vo, split_R, b.glo, b.lv, ctr);
             note_launch(ctx, 2);
+        }
+        if (two) {  // the context's stream waits for the side stream's groups
+            TC_CUDA(ctx, cudaEventRecord(ctx->side_ev[1], ctx->side_stream));
+            TC_CUDA(ctx, cudaStreamWaitEvent(s, ctx->side_ev[1], 0));
         }
     }
     TC_CUDA(ctx, cudaEventRecord(ctx->ev[7], s));

@@ -58,6 +58,7 @@ struct PipeBufs {
     uint64_t task_cap = 0;
     uint32_t *hub_bits = nullptr;   // hub_group bitmaps of hub_words words each (indexed by rank)
     uint64_t hub_words = 0;
+    uint32_t hub_sets = 1;          // 2: two groups' bitmaps, hub groups alternate between two streams
     uint64_t *scan_tmp = nullptr;
     // batched counting of a disjoint union
     GroupSpec groups;

@@ -49,7 +49,7 @@ static size_t request_bytes(const tc_ctx *sub, const tc_graph *g) {
     uint64_t hs = 0;
     uint32_t hb = 0;
     // union copy + per-vertex scratch; the hub tables are shared per round
-    return pipeline_bytes(sub, g->n, g->slots, 0, true, &hs, &hb) + 8ull * (g->n + 1) + 4ull * (g->slots + 1);
+    return pipeline_bytes(sub, g->n, g->slots, 0, true, true, &hs, &hb) + 8ull * (g->n + 1) + 4ull * (g->slots + 1);
 }
 
 static size_t arena_held(const tc_ctx *sub) { return sub->arena.cap + sub->batch_arena.cap; }

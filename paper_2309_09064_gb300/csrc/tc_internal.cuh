@@ -63,7 +63,7 @@ struct Ctl {
     unsigned int changed;            // CC hooking made progress
     unsigned int n_residual;
     unsigned int n_rows[4];          // rows per intersection class (warp, block, hub, tiny)
-    unsigned int task_next[3];       // dynamic scheduling counters per class
+    unsigned int task_next[4];       // dynamic scheduling counters per class (3: odd hub groups)
     unsigned long long n_tasks[3];   // tasks per class
     unsigned int error;              // nonzero: a device-side check failed
     unsigned int max_s2;             // largest hashed row among block-class rows / max degree
@@ -124,6 +124,8 @@ struct tc_ctx {
     tc::Ctl *d_ctl = nullptr;
     tc::Ctl *h_ctl = nullptr;   // pinned
     cudaEvent_t ev[10] = {};
+    cudaStream_t side_stream = nullptr;  // hub groups of odd index, beside `stream` (made on first use)
+    cudaEvent_t side_ev[2] = {};         // fork and join of the side stream
     uint32_t launches = 0;    // kernels launched on this context so far (a call reports its own difference)
     uint32_t isect_flags = 0; // which intersection kernels the last count launched (1 warp, 2 block, 4 hub)
     uint32_t shard = 0, nshards = 1;  // intersection tasks of this count: share `shard` of `nshards`
@@ -197,7 +199,7 @@ struct ListSpec {
 tc_status count_pipeline(tc_ctx *ctx, const GraphView &g, uint32_t *levels_out, const GroupSpec &groups,
                          uint64_t *triangles, tc_stats *stats, const uint32_t *levels_in = nullptr,
                          uint64_t *vertex_counts = nullptr, const ListSpec *list = nullptr, bool alg3 = false);
-size_t pipeline_bytes(const tc_ctx *ctx, uint32_t n, uint64_t slots, uint32_t max_deg, bool own_levels,
+size_t pipeline_bytes(const tc_ctx *ctx, uint32_t n, uint64_t slots, uint32_t max_deg, bool own_levels, bool plain,
                       uint64_t *hub_words, uint32_t *hub_maps);
 
 // CSR construction / validation (csr.cu)
