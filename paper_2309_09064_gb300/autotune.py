@@ -41,7 +41,7 @@ CANDIDATES = [
     {"block_bits_log2": 0},
     {"block_bits_log2": 18},
     {"block_bits_log2": 20},
-    {"hub_task_work": 2097152},
+    {"hub_task_work": 1048576},
     {"task_work": 2097152, "warp_task_work": 16384},
     {"max_v": 1024},
     {"batch_small_slots": 16384},

@@ -30,7 +30,7 @@ struct Tuning {
     uint32_t warps_per_block = 8;    // warp-class kernel: warps per block
     uint32_t block_threads = 1024;   // block-class kernel threads
     uint32_t warp_task_work = 65536; // target probes per warp task
-    uint32_t hub_task_work = 1048576; // target probes per hub task
+    uint32_t hub_task_work = 2097152; // target probes per hub task
     uint32_t max_v = 2048;           // out-neighbours per block / hub task (shared-memory metadata)
     uint32_t hub_group = 32;         // hub rows sharing one launch (one L2-resident bitmap each)
     uint32_t hub_threads = 1024;     // hub kernel threads
