@@ -875,12 +875,16 @@ tc_status build_rows(tc_ctx *ctx, const PipeBufs &b, uint32_t n, uint32_t max_de
                                                         tu.block_cap, tu.tiny_cap, g1_lo, block_hi_cap(tu, g1_lo),
                                                         b.glo, b.lv);
     launches += sharded ? 2 : 3;
+    // class lists in the working order; a count split into shards keeps the vertex order, in which
+    // contiguous slices of a task list carry about equal work (in the working order the first
+    // shard would get every large task)
+    const unsigned long long *order = sharded ? nullptr : b.order;
     for (uint32_t c = 0; c < 4; ++c) {
-        k_class_indicator<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.fdeg, c, b.R, b.order);
+        k_class_indicator<<<grid_for(n, 256, cap), 256, 0, s>>>(n, b.fdeg, c, b.R, order);
         launches += 2 + scan_u32_to_u64(b.R, b.fpref, n, b.scan_tmp, s);
         k_class_scatter<<<grid_for(n, 256, cap), 256, 0, s>>>(
             n, b.fdeg, c, reinterpret_cast<const unsigned long long *>(b.fpref), b.rows[c], &ctx->d_ctl->n_rows[c],
-            b.order);
+            order);
     }
     const uint32_t work[3] = {tu.warp_task_work, tu.task_work, tu.hub_task_work};
     const uint32_t mult[3] = {1, 2, 2};
