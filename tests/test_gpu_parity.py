@@ -156,6 +156,30 @@ def test_hub_class_split_set(tc, name, bits):
         tc.tc_destroy(c)
 
 
+@pytest.mark.parametrize("hub_group", [1, 2, 3, 32])
+@pytest.mark.parametrize("name", ["rmat12_ef32", "chung_lu4096", "union"])
+def test_hub_groups_on_two_streams(tc, name, hub_group):
+    """Plain counts run consecutive hub groups on the context's stream and a
+    side stream, each with its own bitmaps and task counter; with one to
+    three rows per group every group boundary is crossed many times, and the
+    per-vertex counts (one stream) must agree with the same tuning."""
+    c = tc.tc_create(0)
+    try:
+        tc.tc_set_tuning(c, warp_cap=1, block_cap=1, task_work=64, hub_task_work=64, tiny_cap=0,
+                         hub_group=hub_group)
+        g = SMALL[name]
+        T, st, L, rp, col = gpu_count(tc, c, g)
+        assert st["class_rows"][2] > 0
+        assert_parity(T, st, L, rp, col, g)
+        gr = tc.tc_build_csr(c, *g[:3])
+        out = torch.zeros(g[0], dtype=torch.int64, device="cuda")
+        Tv, _ = tc.tc_count_vertices(c, gr, out)
+        tc.tc_graph_free(gr)
+        assert Tv == T and int(out.sum()) == 3 * T
+    finally:
+        tc.tc_destroy(c)
+
+
 @pytest.mark.parametrize("tiny", [1, 8, 64])
 @pytest.mark.parametrize("name", ["rmat10", "grid33x47", "union", "wheel101", "er4096"])
 def test_tiny_merge_class(tc, name, tiny):
