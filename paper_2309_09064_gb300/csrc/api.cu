@@ -167,6 +167,7 @@ tc_status tc_destroy(tc_ctx *ctx) {
     serve_shutdown(ctx);
     DeviceGuard guard(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->side_stream) cudaStreamSynchronize(ctx->side_stream);  // hub groups read the arena
     if (ctx->arena.base) cudaFree(ctx->arena.base);
     if (ctx->batch_arena.base) cudaFree(ctx->batch_arena.base);
     if (ctx->d_ctl) cudaFree(ctx->d_ctl);
@@ -175,10 +176,7 @@ tc_status tc_destroy(tc_ctx *ctx) {
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     for (int i = 0; i < 2; ++i)
         if (ctx->side_ev[i]) cudaEventDestroy(ctx->side_ev[i]);
-    if (ctx->side_stream) {
-        cudaStreamSynchronize(ctx->side_stream);
-        cudaStreamDestroy(ctx->side_stream);
-    }
+    if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
     if (ctx->graph_pool) cudaMemPoolDestroy(ctx->graph_pool);
     if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
     delete ctx;
@@ -191,6 +189,11 @@ tc_status tc_set_stream(tc_ctx *ctx, void *stream) {
     if (!ctx) return TC_ERR_INVALID;
     DeviceGuard guard(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    if (ctx->side_stream) {  // made again on first use, with the new stream's priority
+        cudaStreamSynchronize(ctx->side_stream);
+        cudaStreamDestroy(ctx->side_stream);
+        ctx->side_stream = nullptr;
+    }
     ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
     if (!ctx->stream) {
         if (cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess)

@@ -1900,7 +1900,8 @@ tc_status intersect(tc_ctx *ctx, PipeBufs &b, uint32_t n) {
                 TC_CUDA(ctx, cudaStreamGetPriority(s, &prio));
                 TC_CUDA(ctx, cudaStreamCreateWithPriority(&ctx->side_stream, cudaStreamNonBlocking, prio));
                 for (int i = 0; i < 2; ++i)
-                    TC_CUDA(ctx, cudaEventCreateWithFlags(&ctx->side_ev[i], cudaEventDisableTiming));
+                    if (!ctx->side_ev[i])
+                        TC_CUDA(ctx, cudaEventCreateWithFlags(&ctx->side_ev[i], cudaEventDisableTiming));
             }
             TC_CUDA(ctx, cudaEventRecord(ctx->side_ev[0], s));
             TC_CUDA(ctx, cudaStreamWaitEvent(ctx->side_stream, ctx->side_ev[0], 0));

@@ -176,6 +176,12 @@ def test_hub_groups_on_two_streams(tc, name, hub_group):
         Tv, _ = tc.tc_count_vertices(c, gr, out)
         tc.tc_graph_free(gr)
         assert Tv == T and int(out.sum()) == 3 * T
+        # a new stream for the context: the side stream is made again beside it
+        st2 = torch.cuda.Stream()
+        tc.tc_set_stream(c, st2)
+        T2 = gpu_count(tc, c, g)[0]
+        tc.tc_set_stream(c, None)
+        assert T2 == T
     finally:
         tc.tc_destroy(c)
 
