@@ -123,7 +123,8 @@ typedef struct tc_tuning {
     uint32_t warp_task_work;   /* target probes per warp task */
     uint32_t hub_task_work;    /* target probes per hub task */
     uint32_t max_v;            /* out-neighbour rows per block / hub task (64..4096) */
-    uint32_t hub_group;        /* hub rows probed per launch, one n-bit bitmap each (1..64) */
+    uint32_t hub_group;        /* hub rows probed per launch, one n-bit bitmap each (1..64); plain counts
+                                  run two groups at a time on two streams and keep 2 x hub_group bitmaps */
     uint32_t hub_filter_log2;  /* hub prefilter size: 2^k bits of shared memory (10..20) */
     uint32_t hub_threads;      /* hub kernel threads (64..1024, multiple of 32) */
     uint32_t tiny_cap;         /* s(u) <= tiny_cap (and degree <= 4 tiny_cap, |G1(u)| <= 8): one thread per
